@@ -1,0 +1,369 @@
+"""Pins of the oracle's DGSEM operator, RK3, TGV field and diagnostics against
+what the paper and the mathematics fix (no GPU)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dgsem, physics
+from paper_2207_11571_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden_numbers():
+    out = {}
+    with open(os.path.join(GOLDEN, "paper_printed_numbers.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split()[:2]
+            out[k] = float(v)
+    return out
+
+
+def uniform_state(mesh, rho, v, p, gamma=1.4):
+    shape = (mesh.K,) * 3 + (mesh.n,) * 3
+    q = np.empty((5,) + shape)
+    q[0] = rho
+    for i in range(3):
+        q[1 + i] = rho * v[i]
+    q[4] = p / (gamma - 1) + 0.5 * rho * sum(c * c for c in v)
+    return q
+
+
+# ----------------------------------------------------------------------------- structural invariants
+
+@pytest.mark.parametrize("les", [False, True])
+@pytest.mark.parametrize("K,P", [(2, 3), (3, 2), (2, 5)])
+def test_free_stream_preservation(K, P, les):
+    mesh = dgsem.Mesh(K, P)
+    flow = physics.Flow(Re=100.0, Mach=0.1, les=les)
+    q = uniform_state(mesh, 1.2, (0.3, -0.2, 0.1), flow.p0)
+    R = dgsem.rhs(q, mesh, flow)
+    assert np.abs(R).max() < 1e-12 * flow.p0 * (2 / mesh.h) * (P + 1) ** 2
+
+
+@pytest.mark.parametrize("les", [False, True])
+@pytest.mark.parametrize("K,P,seed", [(3, 3, 0), (2, 6, 1), (4, 2, 2)])
+def test_conservation_of_mass_momentum_energy(K, P, seed, les):
+    """sum over nodes of w w w (h/2)^3 R = 0 for all five variables on the periodic cube,
+    even for a rough random state (telescoping of the common interface fluxes)."""
+    mesh = dgsem.Mesh(K, P)
+    flow = physics.Flow(Re=50.0, Mach=0.3, les=les)
+    shape = (K,) * 3 + (P + 1,) * 3
+    q = inputs.random_conserved(shape, seed, rhoE=(1 / (1.4 * 0.09) / 0.4, 1.0))
+    R = dgsem.rhs(q, mesh, flow)
+    W = mesh.quadrature_weights()
+    for v in range(5):
+        total = (W * R[v]).sum()
+        scale = (W * np.abs(R[v])).sum()
+        assert abs(total) < 1e-13 * scale, (v, total, scale)
+
+
+def _mirror_x(a, vector_sign):
+    """Reflect a (5, K,K,K, n,n,n) field in x: element ex -> K-1-ex, node i -> P-i; flip rho u."""
+    b = a[..., ::-1, :, :, ::-1].copy()
+    b[1] *= vector_sign
+    return b
+
+
+@pytest.mark.parametrize("les", [False, True])
+def test_operator_mirror_equivariance(les):
+    """R(Mirror q) = Mirror R(q): the interface treatment (Roe, central BR1) is symmetric."""
+    mesh = dgsem.Mesh(3, 3)
+    flow = physics.Flow(Re=20.0, Mach=0.3, les=les, Cs=0.5)
+    x, y, z = mesh.coordinates()
+    q = uniform_state(mesh, 1.0, (0, 0, 0), flow.p0)
+    q[0] += 0.1 * np.sin(x + 0.3) * np.cos(y)
+    q[1] += 0.2 * np.cos(x) * np.sin(z + 0.2)
+    q[2] += 0.1 * np.sin(y) * np.cos(x - 0.4)
+    q[4] += 0.3 * np.cos(x + z)
+    R = dgsem.rhs(q, mesh, flow)
+    Rm = dgsem.rhs(_mirror_x(q, -1), mesh, flow)
+    np.testing.assert_allclose(Rm, _mirror_x(R, -1), atol=1e-11 * np.abs(R).max())
+
+
+def test_operator_axis_rotation_equivariance():
+    """Cycling the axes (x,y,z) -> (y,z,x) of the field cycles the operator's result."""
+    mesh = dgsem.Mesh(2, 3)
+    flow = physics.Flow(Re=20.0, Mach=0.3, les=True, Cs=0.5)
+    shape = (2,) * 3 + (4,) * 3
+    q = inputs.random_conserved(shape, 11, rhoE=(8.0, 0.5))
+
+    def rot(a):
+        # new field at (x, y, z) = old field at (y, z, x); axes (ez,ey,ex,k,j,i)
+        b = np.transpose(a, (0, 3, 1, 2, 6, 4, 5))   # new (ez,ey,ex) <- old (ex,ez,ey)
+        b = b.copy()
+        b[1:4] = b[[2, 3, 1]]                        # new v_x = old v_y, v_y = old v_z, v_z = old v_x
+        return b
+    np.testing.assert_allclose(dgsem.rhs(rot(q), mesh, flow), rot(dgsem.rhs(q, mesh, flow)),
+                               atol=1e-11 * np.abs(dgsem.rhs(q, mesh, flow)).max())
+
+
+# ----------------------------------------------------------------------------- Taylor-Green vortex
+
+@pytest.mark.parametrize("K,P", [(4, 3), (8, 3), (3, 6), (2, 8)])
+def test_tgv_initial_kinetic_energy_and_mass(K, P):
+    """Sec. 3.1 Eq. 11: <rho |v|^2 / 2> = rho0 V0^2 / 8 in closed form.  GL quadrature of
+    the trigonometric products is exact to round-off once K >= 3 (errors cancel between
+    elements); on two elements it is only spectrally accurate."""
+    mesh = dgsem.Mesh(K, P)
+    flow = physics.Flow()
+    d = dgsem.diagnostics(dgsem.tgv_state(mesh, flow), mesh, flow)
+    tol = 1e-13 if K >= 3 else 1e-9
+    assert abs(d['ke'] - 0.125) < tol
+    assert abs(d['mass'] - (2 * math.pi) ** 3) < 1e-10
+    assert max(abs(m) for m in d['momentum']) < 1e-12
+
+
+def test_tgv_initial_dissipation_matches_enstrophy_closed_form():
+    """At t = 0, div v = 0 and -dKE/dt = nu <|omega|^2> = 3 / (4 Re) (Eq. 11 field):
+    pins the magnitude of the stress tensor and the viscous lifting."""
+    mesh = dgsem.Mesh(8, 4)
+    for Re in (200.0, 1600.0):
+        flow = physics.Flow(Re=Re, Mach=0.1)
+        q = dgsem.tgv_state(mesh, flow)
+        d = dgsem.diagnostics(q, mesh, flow, R=dgsem.rhs(q, mesh, flow))
+        assert abs(-d['dke_dt'] / (0.75 / Re) - 1.0) < 5e-3, (Re, d['dke_dt'])
+
+
+def test_stable_dt_ratio_matches_printed_cfl_ratio():
+    """Sec. 2.3 Eq. 8 prints 5.06 for the viscous CFL ratio P=8 vs P=3 and 2.25 for the
+    advective one; the (P+1)^2 time-step reading reproduces the first exactly on the
+    same mesh and state, and the dof ratio (9/4)^3 = 11.39 of Sec. 2.3."""
+    g = golden_numbers()
+    flow = physics.Flow()
+    m3, m8 = dgsem.Mesh(2, 3), dgsem.Mesh(2, 8)
+    q3 = uniform_state(m3, 1.0, (1.0, 0, 0), flow.p0)
+    q8 = uniform_state(m8, 1.0, (1.0, 0, 0), flow.p0)
+    ratio = dgsem.stable_dt(q3, m3, flow, 0.7) / dgsem.stable_dt(q8, m8, flow, 0.7)
+    assert round(ratio, 2) == g['cfl_ratio_viscous']
+    assert round(math.sqrt(ratio), 2) == g['cfl_ratio_advective']
+    assert round((9 / 4) ** 3, 2) == g['dof_saving_P8_P3']
+    assert q8[0].size / q3[0].size == pytest.approx((9 / 4) ** 3)
+
+
+# ----------------------------------------------------------------------------- RK3
+
+def test_rk3_amplification_polynomial_is_third_order_exact():
+    """For dq/dt = lam q one step multiplies by 1 + z + z^2/2 + z^3/6 exactly (z = lam dt)."""
+    for z in (0.3, -1.7, 0.5 + 1.2j, -2.1 + 0.4j):
+        q1 = dgsem.rk3_step(np.array([1.0 + 0j]), 1.0, lambda q: z * q)
+        assert abs(q1[0] - (1 + z + z * z / 2 + z ** 3 / 6)) < 1e-15 * 10
+
+
+def test_rk3_order_on_nonlinear_ode():
+    f = lambda q: np.array([-q[0] ** 2 + np.sin(q[1]), q[0] * q[1] - 0.5 * q[1]])
+    from scipy.integrate import solve_ivp
+    T = 1.0
+    ref = solve_ivp(lambda t, y: f(y), (0, T), [1.0, 0.5], rtol=1e-13, atol=1e-14).y[:, -1]
+    errs = []
+    for n in (20, 40, 80):
+        q = np.array([1.0, 0.5])
+        for _ in range(n):
+            q = dgsem.rk3_step(q, T / n, f)
+        errs.append(np.abs(q - ref).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(rates) > 2.8, rates
+
+
+# ----------------------------------------------------------------------------- convergence
+
+def test_euler_density_wave_converges():
+    """Exact Euler solution rho = 1 + 0.2 sin(x + y + z - 3 t), v = (1, 1, 1), p = const
+    (no source).  After RK3 to t = 0.2 the L2 error falls with h; on K = 2, 4, 8 the
+    rate is still pre-asymptotic (one-dimensional runs of the same scheme reach
+    P + 1 only from K = 16 on), so the bar is P - 0.5."""
+    flow = physics.Flow(Mach=0.5, inviscid=True)
+    for P in (2, 3):
+        errs = []
+        for K in (2, 4, 8):
+            mesh = dgsem.Mesh(K, P)
+            x, y, z = mesh.coordinates()
+            def exact(t):
+                rho = 1.0 + 0.2 * np.sin(x + y + z - 3.0 * t)
+                q = uniform_state(mesh, 1.0, (1.0, 1.0, 1.0), flow.p0)
+                q[0] = rho
+                q[1:4] = rho
+                q[4] = flow.p0 / 0.4 + 1.5 * rho
+                return q
+            T, nsteps = 0.2, 5 * K
+            q = exact(0.0)
+            for _ in range(nsteps):
+                q = dgsem.rk3_step(q, T / nsteps, lambda s: dgsem.rhs(s, mesh, flow))
+            W = mesh.quadrature_weights()
+            errs.append(math.sqrt((W * (q[0] - exact(T)[0]) ** 2).sum() / (2 * math.pi) ** 3))
+        rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+        assert errs[2] < 2e-3 and min(rates) > P - 0.5, (P, errs, rates)
+
+
+def _weak_form_1d(P, K):
+    """Textbook weak-form DG on one line of K periodic elements (independent of the
+    strong-form operator): (h/2) w_i du_i/dt = sum_j w_j D_ji F_j - (F*_R d_iP - F*_L d_i0)."""
+    xi, w = dgsem.basis.gl_nodes_weights(P)
+    D = dgsem.basis.lagrange_derivative_matrix(xi)
+    h = 2 * math.pi / K
+
+    def volume_and_surface(F, Fstar_right):
+        Fstar_left = np.roll(Fstar_right, 1)
+        r = F @ (w[:, None] * D)            # sum_j w_j D_ji F_j
+        r[:, -1] -= Fstar_right
+        r[:, 0] += Fstar_left
+        return r / ((h / 2) * w)
+    return volume_and_surface
+
+
+def _planar(field_1d, d, K, n):
+    """Broadcast a (K, n) line field along direction d to (K,K,K,n,n,n)."""
+    shape = [1, 1, 1, 1, 1, 1]
+    shape[2 - d] = K
+    shape[5 - d] = n
+    return np.broadcast_to(field_1d.reshape(shape), (K,) * 3 + (n,) * 3)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_planar_contact_reduces_to_weak_form_upwind_dg(d):
+    """For rho(x_d) with uniform v = e_d and p, the density equation is linear advection
+    and Roe reduces to upwinding: the 3D operator on rough per-element data must equal
+    the weak-form 1D upwind DG (exercises the interface terms that smooth data hide)."""
+    P, K = 3, 4
+    flow = physics.Flow(Mach=0.5, inviscid=True)
+    rho1 = 1.0 + 0.1 * np.random.default_rng(d).standard_normal((K, P + 1))
+    mesh = dgsem.Mesh(K, P)
+    vel = [0.0, 0.0, 0.0]
+    vel[d] = 1.0
+    q = uniform_state(mesh, 1.0, vel, flow.p0)
+    rho = _planar(rho1, d, K, P + 1)
+    q[0] = rho
+    q[1 + d] = rho
+    q[4] = flow.p0 / 0.4 + 0.5 * rho
+    R = dgsem.rhs(q, mesh, flow)
+    ref = _weak_form_1d(P, K)(rho1, rho1[:, -1])
+    np.testing.assert_allclose(R[0], _planar(ref, d, K, P + 1), rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_planar_shear_reduces_to_weak_form_br1(d):
+    """A shear layer v_t(x_d) (t != d) at rest in d with uniform rho and p: the transverse
+    momentum equation is d(rho v_t)/dt = d/dx_d (mu dv_t/dx_d); Roe adds nothing (normal
+    velocity 0).  The 3D operator on rough data must equal textbook weak-form BR1:
+    lifted gradient with central u^, central viscous interface flux."""
+    P, K, mu = 3, 4, 0.7
+    t = (d + 1) % 3
+    flow = physics.Flow(Re=1.0 / mu, Mach=0.5)
+    v1 = 0.2 * np.random.default_rng(10 + d).standard_normal((K, P + 1))
+    weak = _weak_form_1d(P, K)
+    uhat_right = 0.5 * (v1[:, -1] + np.roll(v1[:, 0], -1))
+    G = weak(-v1, -uhat_right)                      # weak gradient: -(sum w D (-u)) ... = lifted dv/dx
+    Fv = -mu * G
+    Fstar = -mu * 0.5 * (G[:, -1] + np.roll(G[:, 0], -1))
+    ref = weak(Fv, Fstar)
+    mesh = dgsem.Mesh(K, P)
+    q = uniform_state(mesh, 1.0, (0, 0, 0), flow.p0)
+    q[1 + t] = _planar(v1, d, K, P + 1)
+    q[4] = flow.p0 / 0.4 + 0.5 * q[1 + t] ** 2
+    R = dgsem.rhs(q, mesh, flow)
+    np.testing.assert_allclose(R[1 + t], _planar(ref, d, K, P + 1), rtol=1e-11, atol=1e-11)
+
+
+def _manufactured(flow, delta):
+    """Exact -div(f^a - f^nu) of a smooth periodic state, derived symbolically
+    from Appendix A with sympy; returns numpy callables for q and the operator."""
+    sp = pytest.importorskip("sympy")
+    X, Y, Z = sp.symbols('x y z', real=True)
+    g = flow.gamma
+    rho = 1 + sp.Rational(1, 5) * sp.sin(X + 2 * Y) * sp.cos(Z)
+    u = sp.Rational(1, 2) * sp.sin(Y) * sp.cos(Z) + sp.Rational(1, 5) * sp.cos(X)
+    v = sp.Rational(2, 5) * sp.cos(X) * sp.sin(Z) + sp.Rational(1, 10) * sp.sin(Y)
+    w = sp.Rational(3, 10) * sp.sin(X) * sp.cos(Y) + sp.Rational(1, 10) * sp.cos(Z)
+    p = flow.p0 + sp.Rational(1, 5) * sp.cos(X) * sp.sin(Y + Z)
+    vel = [u, v, w]
+    coords = [X, Y, Z]
+    E = p / (g - 1) + rho * (u ** 2 + v ** 2 + w ** 2) / 2
+    qs = [rho, rho * u, rho * v, rho * w, E]
+    theta = p / rho
+    grad = [[sp.diff(f, c) for f in (u, v, w, theta)] for c in coords]   # grad[d][a]
+    div = grad[0][0] + grad[1][1] + grad[2][2]
+    mu = flow.mu
+    kap = mu * g / ((g - 1) * flow.Pr)
+    if flow.les:
+        S2 = sum((sp.Rational(1, 2) * (grad[j][i] + grad[i][j])) ** 2 for i in range(3) for j in range(3))
+        mut = rho * (flow.Cs * delta) ** 2 * sp.sqrt(2 * S2)
+        mu = mu + mut
+        kap = kap + mut * g / ((g - 1) * flow.Prt)
+    out = [0] * 5
+    for d in range(3):
+        fa = [rho * vel[d]] + [rho * vel[i] * vel[d] + (p if i == d else 0) for i in range(3)] + [vel[d] * (E + p)]
+        tau = [mu * (grad[d][i] + grad[i][d]) - (sp.Rational(2, 3) * mu * div if i == d else 0) for i in range(3)]
+        fv = [0] + tau + [sum(vel[i] * tau[i] for i in range(3)) + kap * grad[d][3]]
+        for k in range(5):
+            out[k] = out[k] - sp.diff(fa[k] - fv[k], coords[d])
+    lam_q = [sp.lambdify((X, Y, Z), e, 'numpy') for e in qs]
+    lam_r = [sp.lambdify((X, Y, Z), e, 'numpy') for e in out]
+    return lam_q, lam_r
+
+
+@pytest.mark.parametrize("les", [False, True])
+def test_navier_stokes_operator_converges_to_exact_divergence(les):
+    """The discrete operator p(q) at P = 3 on a smooth state converges to
+    -div(f^a - f^nu) (Appendix A) at Re = 1, where viscous and heat fluxes are O(1),
+    for every variable.  The pointwise error of BR1's second-derivative operator is
+    O(h^(P-1)), so the bar is rate >= 1.5 from K = 4 to K = 8 (measured: 2.8 for the
+    momenta, 1.6 for the heat-flux-dominated energy; 2.9 / 2.5 from K = 8 to 16).
+    A dropped or mis-signed term in tau, the heat flux, the Smagorinsky viscosity or
+    the Roe flux leaves an O(1) error and stalls the rate."""
+    flow = physics.Flow(Re=1.0, Mach=0.5, les=les, Cs=1.0, les_delta=0.3)
+    lam_q, lam_r = _manufactured(flow, 0.3)
+    P = 3
+    errs = []
+    for K in (4, 8):
+        mesh = dgsem.Mesh(K, P)
+        x, y, z = mesh.coordinates()
+        q = np.stack([np.broadcast_to(f(x, y, z), x.shape) for f in lam_q])
+        Rex = np.stack([np.broadcast_to(f(x, y, z), x.shape) for f in lam_r])
+        R = dgsem.rhs(q, mesh, flow)
+        W = mesh.quadrature_weights()
+        errs.append([math.sqrt((W * (R[v] - Rex[v]) ** 2).sum() / (W * Rex[v] ** 2).sum()) for v in range(5)])
+    errs = np.array(errs)
+    rates = np.log2(errs[0] / errs[1])
+    assert np.all(errs[1] < 0.1) and np.all(rates > 1.5), (errs, rates)
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_planar_heat_conduction_reduces_to_weak_form_br1(d):
+    """At rest with uniform p and a rough density rho(x_d), theta = p/rho varies and the
+    energy equation is d(rho e)/dt = d/dx_d (kappa dtheta/dx_d), kappa = mu gamma /
+    ((gamma-1) Pr); Roe adds nothing (no normal velocity, no pressure jump).  Must
+    equal weak-form BR1 on the same data."""
+    P, K, mu = 3, 4, 0.5
+    flow = physics.Flow(Re=1.0 / mu, Mach=0.5)
+    kappa = mu * flow.gamma / ((flow.gamma - 1) * flow.Pr)
+    rho1 = 1.0 + 0.1 * np.random.default_rng(20 + d).standard_normal((K, P + 1))
+    th1 = flow.p0 / rho1
+    weak = _weak_form_1d(P, K)
+    that = 0.5 * (th1[:, -1] + np.roll(th1[:, 0], -1))
+    G = weak(-th1, -that)
+    ref = weak(-kappa * G, -kappa * 0.5 * (G[:, -1] + np.roll(G[:, 0], -1)))
+    mesh = dgsem.Mesh(K, P)
+    q = uniform_state(mesh, 1.0, (0, 0, 0), flow.p0)
+    q[0] = _planar(rho1, d, K, P + 1)
+    R = dgsem.rhs(q, mesh, flow)
+    np.testing.assert_allclose(R[4], _planar(ref, d, K, P + 1), rtol=1e-11, atol=1e-11)
+    assert np.abs(R[0]).max() < 1e-12 and np.abs(R[1:4]).max() < 1e-11
+
+
+def test_diagnostics_dke_dt_matches_time_difference():
+    """dke_dt from the operator equals the centred time difference of KE under RK3."""
+    mesh = dgsem.Mesh(4, 3)
+    flow = physics.Flow(Re=200.0)
+    q = dgsem.tgv_state(mesh, flow, inputs.perturbation((5, 4096), eps=1e-6))
+    d0 = dgsem.diagnostics(q, mesh, flow, R=dgsem.rhs(q, mesh, flow))
+    dt = 1e-4
+    f = lambda s: dgsem.rhs(s, mesh, flow)
+    qp = dgsem.rk3_step(q, dt, f)
+    qm = dgsem.rk3_step(q, -dt, f)
+    ke = lambda s: dgsem.diagnostics(s, mesh, flow)['ke']
+    fd = (ke(qp) - ke(qm)) / (2 * dt)
+    assert abs(fd - d0['dke_dt']) < 1e-6 * abs(d0['dke_dt']) + 1e-10
