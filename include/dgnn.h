@@ -1,0 +1,159 @@
+/*
+ * dgnn.h - C ABI of libdgnn.so: nodal DGSEM for the 3D compressible Navier-Stokes
+ * equations with a learned corrective forcing (arXiv 2207.11571), for NVIDIA GB300
+ * (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: DG_OK (0) or a negative dg_status.  dg_last_error() returns a
+ *   thread-local message describing the last failure of the calling thread.
+ * - Unless a parameter says "host", array pointers are DEVICE pointers owned by the
+ *   caller (for example torch CUDA tensors).  The library never frees them.  The
+ *   library owns only what dg_create / nn_create allocate, released by
+ *   dg_destroy / nn_destroy.
+ * - Streams are cudaStream_t passed as void* (NULL = legacy default stream).  All
+ *   work is enqueued on that stream; calls that return host values (diagnostics,
+ *   stable dt, loss) synchronise that stream before returning.
+ * - Conserved state q (Appendix A): five variables (rho, rho v1, rho v2, rho v3,
+ *   rho e), FP64, layout [var][elem][node], node fastest.
+ *   elem = ex + K (ey + K ez) on the periodic K^3 mesh of [-pi, pi]^3 (Sec. 3.1),
+ *   node = i + n (j + n k), n = P + 1 Gauss-Lobatto points per direction, x fastest.
+ *   N = K^3 n^3 nodes; q holds 5 N doubles.
+ * - Nondimensionalisation: rho0 = V0 = L = 1, mu = 1/Re, p0 = 1/(gamma Mach^2),
+ *   heat flux kappa grad T = mu gamma/((gamma-1) Pr) grad(p/rho).
+ * - Errors: a NULL handle or pointer where one is required, or a size out of range,
+ *   returns DG_ERR_INVALID_ARG without enqueuing work.  A CUDA failure returns
+ *   DG_ERR_CUDA with the CUDA error string in dg_last_error().
+ */
+#ifndef DGNN_H
+#define DGNN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_INVALID_ARG = -1,
+  DG_ERR_CUDA = -2,
+  DG_ERR_NONFINITE = -3,   /* a diagnostic found NaN/Inf in the state */
+  DG_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out (error flag set, kernel returned) */
+  DG_ERR_IO = -5,          /* file missing, truncated or with a bad checksum */
+  DG_ERR_UNSUPPORTED = -6  /* a parameter combination this build does not implement */
+} dg_status;
+
+typedef struct dg_ctx dg_ctx;
+typedef struct nn_model nn_model;
+
+/* Arithmetic of the spatial operator.  The state q and the RK accumulation are
+ * FP64 in both modes. */
+typedef enum {
+  DG_PREC_FP64 = 0, /* every step of the operator in FP64 (parity path) */
+  DG_PREC_FP32 = 1  /* operator (fluxes, contractions, lifting) in FP32 */
+} dg_precision;
+
+typedef struct {
+  int precision;      /* dg_precision, default DG_PREC_FP64 */
+  int rk_register_fp32; /* 1: the low-storage RK register g is FP32 (FP32 operator only); default 0 */
+  double gamma;       /* ratio of specific heats, default 1.4 */
+  double Cs;          /* Smagorinsky constant, default 0.1 */
+  double Prt;         /* turbulent Prandtl number, default 0.9 */
+  double les_delta;   /* LES filter width; <= 0 selects h/(P+1) (default) */
+  int elems_per_block;/* elements per CUDA block; <= 0 selects the tuned default for P */
+} dg_opts;
+
+/* Integral diagnostics (Sec. 2.4 Eq. 9 and kinetic-energy budget), FP64. */
+typedef struct {
+  double mass;          /* sum over nodes of w w w (h/2)^3 rho */
+  double momentum[3];
+  double energy;        /* integral of rho e */
+  double ke;            /* (1/(2 pi)^3) integral rho |v|^2 / 2 */
+  double dke_dt;        /* (1/(2 pi)^3) integral (v . R_m - |v|^2 R_rho / 2), R = p(q) (+ forcing) */
+  double e_inf[3];      /* max |q - q_ref| for rho u, rho v, rho w (Eq. 9); 0 when q_ref is NULL */
+  double max_wave;      /* max over nodes of |v| + c */
+  int64_t nonfinite;    /* number of non-finite state values found */
+} dg_diag;
+
+/* Fills *opts with the defaults listed above.  Returns DG_ERR_INVALID_ARG on NULL. */
+int dg_opts_default(dg_opts* opts);
+
+/* Creates a solver for the periodic K^3 hex mesh of [-pi, pi]^3 (Sec. 3.1) at
+ * polynomial order P (1 <= P <= 8) on Gauss-Lobatto nodes, for the flow (Re, Mach,
+ * Pr) and closure (0: none; 1: Smagorinsky, Sec. 3.1 "LES").  Builds the basis on
+ * the host in FP64, uploads it, and allocates the workspace (operator scratch and
+ * the RK register).  opts may be NULL (defaults).  1 <= K <= 256. */
+int dg_create(int K, int P, double Re, double Mach, double Pr, int closure,
+              const dg_opts* opts, dg_ctx** out);
+int dg_destroy(dg_ctx* ctx);
+
+/* Host-only: the 1D Gauss-Lobatto basis of order P (1..8) that the solver uses
+ * (Sec. 2.6: nodal Lagrange bases; nodes = endpoints and roots of L_P', weights
+ * 2/(P(P+1) L_P(xi)^2), D[i*(P+1)+m] = l_m'(xi_i)).  Any output may be NULL. */
+int dg_basis_1d(int P, double* xi, double* w, double* D);
+
+/* Number of nodes N = K^3 (P+1)^3 and elements K^3 of the context. */
+int dg_sizes(const dg_ctx* ctx, int64_t* nodes, int64_t* elems);
+
+/* Taylor-Green vortex initial state (Sec. 3.1, Eq. 11) at the GL nodes:
+ * rho = 1, v1 = sin x cos y cos z, v2 = -cos x sin y cos z, v3 = 0,
+ * p = p0 + (cos 2x + cos 2y)(cos 2z + 2)/16, then q += perturbation.
+ * q: device, 5 N doubles (written).  perturbation: device, 5 N doubles in the layout
+ * of q, or NULL for none (the caller draws it). */
+int dg_init_tgv(dg_ctx* ctx, double* q, const double* perturbation, void* stream);
+
+/* dqdt = p(q) + s(q): the semi-discrete DGSEM operator (Sec. 2, Eq. 3/4): strong-form
+ * volume term with sum-factorised derivative matrices, Roe advective and BR1 viscous
+ * interface fluxes (Sec. 3.1), optional Smagorinsky viscosity, plus the network
+ * forcing when forcing != NULL (Eq. 4).  q, dqdt: device, 5 N doubles. */
+int dg_rhs(dg_ctx* ctx, const double* q, double* dqdt, const nn_model* forcing, void* stream);
+
+/* Advances q in place by nsteps low-storage RK3 steps of size dt (Sec. 2, Eq. 6 with
+ * the third-order Runge-Kutta scheme of Sec. 3.1; Williamson 2N coefficients).  When
+ * forcing != NULL the network forcing s(q_k) is evaluated on every stage state and
+ * added to the operator (Eq. 4 integrated by RK3).  q: device, 5 N doubles. */
+int dg_rk3_step(dg_ctx* ctx, double* q, double dt, int nsteps, const nn_model* forcing,
+                void* stream);
+
+/* Same as dg_rk3_step but q_host is a HOST array (pageable or pinned, 5 N doubles):
+ * copies it to the device, advances, copies it back, and fills *diag (host, may be
+ * NULL) for the final state.  Synchronises the stream. */
+int dg_advance_host(dg_ctx* ctx, double* q_host, double dt, int nsteps,
+                    const nn_model* forcing, dg_diag* diag, void* stream);
+
+/* q_lo = G q_hi: the filter of Eq. 2, per element nodal(P_hi) -> Legendre modes ->
+ * truncation to degree P_lo per direction -> nodal(P_lo) (Sec. 2.6), FP64.  Both
+ * contexts must share K and P_lo <= P_hi.  q_hi, q_lo: device. */
+int dg_project(const dg_ctx* hi, const dg_ctx* lo, const double* q_hi, double* q_lo,
+               void* stream);
+
+/* Diagnostics of q (FP64 reductions, deterministic order).  q_ref (device, same
+ * layout) may be NULL; when given, e_inf = ||q - q_ref||_inf on the momenta (Eq. 9).
+ * forcing (may be NULL) enters dke_dt.  out: HOST.  Returns DG_ERR_NONFINITE (after
+ * filling *out) when the state holds NaN or Inf. */
+int dg_diagnostics(dg_ctx* ctx, const double* q, const double* q_ref,
+                   const nn_model* forcing, dg_diag* out, void* stream);
+
+/* Stable time step dt = cfl h / ((P+1)^2 max(|v| + c)) (Sec. 2.3 gives the CFL
+ * condition as a proportionality; this form is the library's reading).  dt_out: HOST. */
+int dg_stable_dt(dg_ctx* ctx, const double* q, double cfl, double* dt_out, void* stream);
+
+/* Training pairs of Algorithm 1 (Sec. 2.1):
+ *   X[e] = element features of q_bar_n,
+ *   Y[e] = element features of (q_bar_np1 - q_nn_np1) / dt   (difference in FP64),
+ * for the n_vars variables starting at first_var (5 and 0: all; 3 and 1: momenta,
+ * Sec. 2.2).  A feature index is v_slot * n^3 + node.  All three states use the
+ * layout of q for context lo.  X, Y: device float arrays of K^3 * n_vars * n^3
+ * values (row e = one element), written. */
+int dg_make_pairs(const dg_ctx* lo, const double* q_bar_n, const double* q_nn_np1,
+                  const double* q_bar_np1, double dt, int first_var, int n_vars,
+                  float* X, float* Y, void* stream);
+
+const char* dg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGNN_H */

@@ -15,40 +15,63 @@ def legendre_unit(m):
     return c
 
 
-def gl_nodes_weights(P):
-    """Gauss-Lobatto nodes xi_0 = -1 < ... < xi_P = 1 and weights.
+def _legendre_ext(P, x):
+    """L_P(x) and L_P'(x) by the three-term recurrence, in the dtype of x."""
+    one = np.ones_like(x)
+    l0, l1, d0, d1 = one, x, 0 * x, one
+    if P == 0:
+        return one, 0 * x
+    for k in range(1, P):
+        l0, l1 = l1, ((2 * k + 1) * x * l1 - k * l0) / (k + 1)
+        d0, d1 = d1, d0 + (2 * k + 1) * l0
+    return l1, d1
 
-    Nodes: the endpoints and the roots of L_P'(xi) (numpy's Legendre root finder,
-    polished by two Newton steps on L_P').
+
+def gl_nodes_weights_ext(P):
+    """Gauss-Lobatto nodes and weights in extended precision (np.longdouble).
+
+    Nodes: the endpoints and the roots of L_P'(xi) (numpy's Legendre root finder in
+    FP64, then Newton on L_P' in extended precision).
     Weights: w_i = 2 / (P (P+1) L_P(xi_i)^2).
     """
     if P < 1:
         raise ValueError("P >= 1 required")
+    ext = np.longdouble
     dLP = npleg.legder(legendre_unit(P))
-    interior = np.sort(np.real(npleg.legroots(dLP))) if P > 1 else np.zeros(0)
-    d2LP = npleg.legder(dLP)
-    for _ in range(2):
-        interior = interior - npleg.legval(interior, dLP) / npleg.legval(interior, d2LP)
-    xi = np.concatenate(([-1.0], interior, [1.0]))
-    w = 2.0 / (P * (P + 1) * npleg.legval(xi, legendre_unit(P)) ** 2)
+    interior = np.sort(np.real(npleg.legroots(dLP))).astype(ext) if P > 1 else np.zeros(0, ext)
+    for _ in range(6):
+        # Newton on f = (1 - x^2) L_P'(x), f' = -P (P+1) L_P(x) (Legendre's equation)
+        L, dL = _legendre_ext(P, interior)
+        interior = interior - (1 - interior * interior) * dL / (-P * (P + 1) * L)
+    xi = np.concatenate((np.array([-1.0], ext), interior, np.array([1.0], ext)))
+    L, _ = _legendre_ext(P, xi)
+    w = ext(2) / (P * (P + 1) * L * L)
     return xi, w
 
 
+def gl_nodes_weights(P):
+    """Gauss-Lobatto nodes xi_0 = -1 < ... < xi_P = 1 and weights, rounded once to FP64."""
+    xi, w = gl_nodes_weights_ext(P)
+    return xi.astype(np.float64), w.astype(np.float64)
+
+
 def lagrange_derivative_matrix(xi):
-    """D[i, j] = l_j'(xi_i), l_j the Lagrange polynomial through the nodes xi.
+    """D[i, j] = l_j'(xi_i), l_j the Lagrange polynomial through the nodes xi,
+    computed in the dtype of ``xi`` (pass extended-precision nodes and round the
+    result once to obtain the correctly rounded FP64 matrix).
 
     Written from the definition
         l_j'(x) = sum_{m != j} 1/(xi_j - xi_m) * prod_{k != j, m} (x - xi_k)/(xi_j - xi_k).
     """
     n = len(xi)
-    D = np.zeros((n, n))
+    D = np.zeros((n, n), dtype=np.asarray(xi).dtype)
     for i in range(n):
         for j in range(n):
-            total = 0.0
+            total = 0 * xi[0]
             for m in range(n):
                 if m == j:
                     continue
-                prod = 1.0 / (xi[j] - xi[m])
+                prod = 1 / (xi[j] - xi[m])
                 for k in range(n):
                     if k == j or k == m:
                         continue
@@ -56,6 +79,12 @@ def lagrange_derivative_matrix(xi):
                 total += prod
             D[i, j] = total
     return D
+
+
+def derivative_matrix(P):
+    """The FP64 derivative matrix of order P: D of the extended nodes, rounded once."""
+    xi, _ = gl_nodes_weights_ext(P)
+    return lagrange_derivative_matrix(xi).astype(np.float64)
 
 
 def lagrange_interpolation_matrix(xi_from, x_to):

@@ -34,7 +34,7 @@ class Mesh:
         self.K, self.P, self.n = K, P, P + 1
         self.h = 2.0 * math.pi / K
         self.xi, self.w = basis.gl_nodes_weights(P)
-        self.D = basis.lagrange_derivative_matrix(self.xi)
+        self.D = basis.derivative_matrix(P)
 
     def coordinates(self):
         """x, y, z arrays of shape (K, K, K, n, n, n): x = -pi + (e + (xi+1)/2) h."""

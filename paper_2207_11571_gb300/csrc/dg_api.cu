@@ -1,0 +1,322 @@
+// C ABI of libdgnn.so (declared in include/dgnn.h): context management and the
+// solver entry points.  Argument checking, workspace ownership and stage sequencing
+// live here; all arithmetic runs in the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "dg_aux.h"
+#include "dg_kernels.cuh"
+#include "nn_bridge.h"
+
+namespace dgnn {
+
+namespace {
+thread_local std::string g_last_error;
+
+// Williamson (1980) 2N-storage RK3 coefficients (the paper's third-order three-stage
+// Runge-Kutta scheme, Sec. 3.1, is unnamed; this is the reading).
+constexpr double kRkA[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+constexpr double kRkB[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+
+int default_elems_per_block(int P) {
+  static const int E[9] = {0, 32, 16, 4, 2, 2, 1, 1, 1};
+  return E[P];
+}
+
+int max_elems_per_block(int P) {
+  const int np = (P + 1) * (P + 1) * (P + 1);
+  int E = 1;
+  while (((E + 1) * np + 31) / 32 * 32 <= max_threads_for(P)) ++E;
+  return E;
+}
+}  // namespace
+
+int fail(int status, const std::string& msg) {
+  g_last_error = msg;
+  return status;
+}
+
+int cuda_fail(cudaError_t err, const char* what) {
+  return fail(DG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(err));
+}
+
+cudaError_t launch_gradient(const dg_ctx* c, const double* q, cudaStream_t st) {
+  return c->opts.precision == DG_PREC_FP32 ? gradient_f32(c, q, st) : gradient_f64(c, q, st);
+}
+
+cudaError_t launch_flux(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                        double dt, cudaStream_t st) {
+  return c->opts.precision == DG_PREC_FP32 ? flux_f32(c, q, dqdt, f, mode, A, B, dt, st)
+                                           : flux_f64(c, q, dqdt, f, mode, A, B, dt, st);
+}
+
+// Evaluates the network forcing on the current state q (all elements) into c->s_buf.
+static int forcing_for(dg_ctx* c, const double* q, const nn_model* net, Forcing* f, cudaStream_t st) {
+  *f = Forcing{};
+  if (!net) return DG_OK;
+  int first = 0, nv = 0;
+  int rc = nn_forcing_on_state(net, c, q, c->s_buf, &first, &nv, st);
+  if (rc) return rc;
+  f->s = c->s_buf;
+  f->first_var = first;
+  f->n_vars = nv;
+  f->stride = nv * c->np;
+  return DG_OK;
+}
+
+static int rhs_into(dg_ctx* c, const double* q, double* out, const nn_model* net, cudaStream_t st) {
+  DG_CUDA(launch_gradient(c, q, st));
+  Forcing f;
+  int rc = forcing_for(c, q, net, &f, st);
+  if (rc) return rc;
+  DG_CUDA(launch_flux(c, const_cast<double*>(q), out, f, 0, 0.0, 0.0, 0.0, st));
+  return DG_OK;
+}
+
+static int rk3_steps(dg_ctx* c, double* q, double dt, int nsteps, const nn_model* net, cudaStream_t st) {
+  for (int s = 0; s < nsteps; ++s)
+    for (int k = 0; k < 3; ++k) {
+      DG_CUDA(launch_gradient(c, q, st));
+      Forcing f;
+      int rc = forcing_for(c, q, net, &f, st);
+      if (rc) return rc;
+      DG_CUDA(launch_flux(c, q, nullptr, f, 1, kRkA[k], kRkB[k], dt, st));
+    }
+  return DG_OK;
+}
+
+static int diagnostics_into(dg_ctx* c, const double* q, const double* qref, const nn_model* net, bool with_rhs,
+                            dg_diag* out, cudaStream_t st) {
+  const double* R = nullptr;
+  if (with_rhs) {
+    int rc = rhs_into(c, q, c->rhs_tmp, net, st);
+    if (rc) return rc;
+    R = c->rhs_tmp;
+  }
+  double* dev_out = c->red + (size_t)c->red_blocks * kDiagLen;
+  DG_CUDA(launch_diagnostics(c, q, R, qref, c->red, c->red_blocks, dev_out, st));
+  DG_CUDA(cudaMemcpyAsync(c->red_host, dev_out, kDiagLen * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaStreamSynchronize(st));
+  const double* r = c->red_host;
+  const double vol = 8.0 * M_PI * M_PI * M_PI;
+  std::memset(out, 0, sizeof(*out));
+  out->mass = r[0];
+  for (int i = 0; i < 3; ++i) out->momentum[i] = r[1 + i];
+  out->energy = r[4];
+  out->ke = r[5] / vol;
+  out->dke_dt = with_rhs ? r[6] / vol : 0.0;
+  out->nonfinite = (int64_t)r[kDiagNonfinite];
+  for (int i = 0; i < 3; ++i) out->e_inf[i] = qref ? r[8 + i] : 0.0;
+  out->max_wave = r[11];
+  return out->nonfinite ? fail(DG_ERR_NONFINITE, "state holds non-finite values") : DG_OK;
+}
+
+}  // namespace dgnn
+
+using namespace dgnn;
+
+extern "C" {
+
+int dg_opts_default(dg_opts* o) {
+  if (!o) return fail(DG_ERR_INVALID_ARG, "dg_opts_default: NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->precision = DG_PREC_FP64;
+  o->rk_register_fp32 = 0;
+  o->gamma = 1.4;
+  o->Cs = 0.1;
+  o->Prt = 0.9;
+  o->les_delta = 0.0;
+  o->elems_per_block = 0;
+  return DG_OK;
+}
+
+int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, const dg_opts* opts, dg_ctx** out) {
+  if (!out) return fail(DG_ERR_INVALID_ARG, "dg_create: out is NULL");
+  *out = nullptr;
+  if (K < 1 || K > 256) return fail(DG_ERR_INVALID_ARG, "dg_create: K must be in [1, 256]");
+  if (P < 1 || P > kMaxP) return fail(DG_ERR_INVALID_ARG, "dg_create: P must be in [1, 8]");
+  if (!(Re > 0) || !(Mach > 0) || !(Pr > 0)) return fail(DG_ERR_INVALID_ARG, "dg_create: Re, Mach, Pr must be > 0");
+  if (closure != 0 && closure != 1) return fail(DG_ERR_INVALID_ARG, "dg_create: closure must be 0 or 1");
+  dg_opts o;
+  dg_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.precision != DG_PREC_FP64 && o.precision != DG_PREC_FP32)
+    return fail(DG_ERR_INVALID_ARG, "dg_create: unknown precision");
+  if (o.rk_register_fp32 && o.precision != DG_PREC_FP32)
+    return fail(DG_ERR_INVALID_ARG, "dg_create: an FP32 RK register needs the FP32 operator");
+  if (!(o.gamma > 1.0)) return fail(DG_ERR_INVALID_ARG, "dg_create: gamma must be > 1");
+  if (o.elems_per_block > max_elems_per_block(P))
+    return fail(DG_ERR_INVALID_ARG, "dg_create: elems_per_block exceeds the block size limit for this P");
+
+  dg_ctx* c = new dg_ctx();
+  c->K = K;
+  c->P = P;
+  c->n = P + 1;
+  c->np = c->n * c->n * c->n;
+  c->nel = K * K * K;
+  c->N = (long long)c->nel * c->np;
+  c->closure = closure;
+  c->Re = Re;
+  c->Mach = Mach;
+  c->Pr = Pr;
+  c->opts = o;
+  int rc = build_basis(P, &c->basis);
+  if (rc) {
+    delete c;
+    return rc;
+  }
+  const double h = 2.0 * M_PI / K;
+  c->geom.K = K;
+  c->geom.nel = c->nel;
+  c->geom.N = c->N;
+  c->geom.E = o.elems_per_block > 0 ? o.elems_per_block : default_elems_per_block(P);
+  c->geom.two_over_h = 2.0 / h;
+  c->geom.winv = 1.0 / c->basis.w[0];
+  std::memset(c->geom.D, 0, sizeof(c->geom.D));
+  std::memcpy(c->geom.D, c->basis.D, sizeof(double) * c->n * c->n);
+  const double g = o.gamma;
+  c->phys.gamma = g;
+  c->phys.mu = 1.0 / Re;
+  c->phys.lam = c->phys.mu * g / ((g - 1.0) * Pr);
+  c->phys.les = closure;
+  const double delta = o.les_delta > 0 ? o.les_delta : h / (P + 1);
+  c->phys.csd2 = (o.Cs * delta) * (o.Cs * delta);
+  c->phys.lam_t = g / ((g - 1.0) * o.Prt);
+
+  const size_t tsz = o.precision == DG_PREC_FP32 ? sizeof(float) : sizeof(double);
+  const size_t gsz = o.rk_register_fp32 ? sizeof(float) : sizeof(double);
+  c->red_blocks = kDiagBlocks;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&c->qf, 5 * c->N * tsz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->vis, 9 * c->N * tsz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->g, 5 * c->N * gsz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->rhs_tmp, 5 * c->N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->red, (size_t)(c->red_blocks + 1) * kDiagLen * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->red_host, kDiagLen * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->s_buf, 5 * c->N * sizeof(float));
+  if (e != cudaSuccess) {
+    dg_destroy(c);
+    return cuda_fail(e, "dg_create: workspace allocation");
+  }
+  *out = c;
+  return DG_OK;
+}
+
+int dg_destroy(dg_ctx* c) {
+  if (!c) return fail(DG_ERR_INVALID_ARG, "dg_destroy: NULL");
+  cudaFree(c->qf);
+  cudaFree(c->vis);
+  cudaFree(c->g);
+  cudaFree(c->rhs_tmp);
+  cudaFree(c->red);
+  cudaFree(c->s_buf);
+  cudaFree(c->q_dev);
+  if (c->red_host) cudaFreeHost(c->red_host);
+  for (int i = 0; i <= kMaxP; ++i) cudaFree(c->filter_dev[i]);
+  delete c;
+  return DG_OK;
+}
+
+int dg_sizes(const dg_ctx* c, int64_t* nodes, int64_t* elems) {
+  if (!c) return fail(DG_ERR_INVALID_ARG, "dg_sizes: NULL context");
+  if (nodes) *nodes = c->N;
+  if (elems) *elems = c->nel;
+  return DG_OK;
+}
+
+int dg_basis_1d(int P, double* xi, double* w, double* D) {
+  Basis1D b;
+  int rc = build_basis(P, &b);
+  if (rc) return rc;
+  const int n = P + 1;
+  for (int i = 0; i < n; ++i) {
+    if (xi) xi[i] = b.xi[i];
+    if (w) w[i] = b.w[i];
+  }
+  if (D) std::memcpy(D, b.D, sizeof(double) * n * n);
+  return DG_OK;
+}
+
+int dg_init_tgv(dg_ctx* c, double* q, const double* pert, void* stream) {
+  if (!c || !q) return fail(DG_ERR_INVALID_ARG, "dg_init_tgv: NULL argument");
+  DG_CUDA(launch_init_tgv(c, q, pert, (cudaStream_t)stream));
+  return DG_OK;
+}
+
+int dg_rhs(dg_ctx* c, const double* q, double* dqdt, const nn_model* forcing, void* stream) {
+  if (!c || !q || !dqdt) return fail(DG_ERR_INVALID_ARG, "dg_rhs: NULL argument");
+  if (q == dqdt) return fail(DG_ERR_INVALID_ARG, "dg_rhs: q and dqdt must not alias");
+  return rhs_into(c, q, dqdt, forcing, (cudaStream_t)stream);
+}
+
+int dg_rk3_step(dg_ctx* c, double* q, double dt, int nsteps, const nn_model* forcing, void* stream) {
+  if (!c || !q) return fail(DG_ERR_INVALID_ARG, "dg_rk3_step: NULL argument");
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_rk3_step: bad nsteps or dt");
+  return rk3_steps(c, q, dt, nsteps, forcing, (cudaStream_t)stream);
+}
+
+int dg_advance_host(dg_ctx* c, double* q_host, double dt, int nsteps, const nn_model* forcing, dg_diag* diag,
+                    void* stream) {
+  if (!c || !q_host) return fail(DG_ERR_INVALID_ARG, "dg_advance_host: NULL argument");
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_advance_host: bad nsteps or dt");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = 5 * c->N * sizeof(double);
+  if (!c->q_dev) DG_CUDA(cudaMalloc(&c->q_dev, bytes));
+  DG_CUDA(cudaMemcpyAsync(c->q_dev, q_host, bytes, cudaMemcpyHostToDevice, st));
+  int rc = rk3_steps(c, c->q_dev, dt, nsteps, forcing, st);
+  if (rc) return rc;
+  DG_CUDA(cudaMemcpyAsync(q_host, c->q_dev, bytes, cudaMemcpyDeviceToHost, st));
+  if (diag) return diagnostics_into(c, c->q_dev, nullptr, forcing, false, diag, st);
+  DG_CUDA(cudaStreamSynchronize(st));
+  return DG_OK;
+}
+
+int dg_project(const dg_ctx* hi, const dg_ctx* lo, const double* q_hi, double* q_lo, void* stream) {
+  if (!hi || !lo || !q_hi || !q_lo) return fail(DG_ERR_INVALID_ARG, "dg_project: NULL argument");
+  if (hi->K != lo->K) return fail(DG_ERR_INVALID_ARG, "dg_project: contexts must share K");
+  if (lo->P > hi->P) return fail(DG_ERR_INVALID_ARG, "dg_project: needs P_lo <= P_hi");
+  dg_ctx* h = const_cast<dg_ctx*>(hi);
+  if (!h->filter_dev[lo->P]) {
+    double G[kMaxN1 * kMaxN1];
+    int rc = build_filter(hi->P, lo->P, G);
+    if (rc) return rc;
+    DG_CUDA(cudaMalloc(&h->filter_dev[lo->P], sizeof(G)));
+    DG_CUDA(cudaMemcpy(h->filter_dev[lo->P], G, sizeof(double) * lo->n * hi->n, cudaMemcpyHostToDevice));
+  }
+  DG_CUDA(launch_project(hi, lo, q_hi, q_lo, h->filter_dev[lo->P], (cudaStream_t)stream));
+  return DG_OK;
+}
+
+int dg_diagnostics(dg_ctx* c, const double* q, const double* q_ref, const nn_model* forcing, dg_diag* out,
+                   void* stream) {
+  if (!c || !q || !out) return fail(DG_ERR_INVALID_ARG, "dg_diagnostics: NULL argument");
+  return diagnostics_into(c, q, q_ref, forcing, true, out, (cudaStream_t)stream);
+}
+
+int dg_stable_dt(dg_ctx* c, const double* q, double cfl, double* dt_out, void* stream) {
+  if (!c || !q || !dt_out) return fail(DG_ERR_INVALID_ARG, "dg_stable_dt: NULL argument");
+  if (!(cfl > 0)) return fail(DG_ERR_INVALID_ARG, "dg_stable_dt: cfl must be > 0");
+  dg_diag d;
+  int rc = diagnostics_into(c, q, nullptr, nullptr, false, &d, (cudaStream_t)stream);
+  if (rc) return rc;
+  const double h = 2.0 * M_PI / c->K;
+  *dt_out = cfl * h / ((c->P + 1.0) * (c->P + 1.0) * d.max_wave);
+  return DG_OK;
+}
+
+int dg_make_pairs(const dg_ctx* lo, const double* q_bar_n, const double* q_nn_np1, const double* q_bar_np1,
+                  double dt, int first_var, int n_vars, float* X, float* Y, void* stream) {
+  if (!lo || !q_bar_n || !q_nn_np1 || !q_bar_np1 || !X || !Y)
+    return fail(DG_ERR_INVALID_ARG, "dg_make_pairs: NULL argument");
+  if (!(dt != 0.0) || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_make_pairs: dt must be finite, nonzero");
+  if (first_var < 0 || n_vars < 1 || first_var + n_vars > 5)
+    return fail(DG_ERR_INVALID_ARG, "dg_make_pairs: variable range outside 0..4");
+  DG_CUDA(launch_make_pairs(lo, q_bar_n, q_nn_np1, q_bar_np1, dt, first_var, n_vars, X, Y, (cudaStream_t)stream));
+  return DG_OK;
+}
+
+const char* dg_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+// Auxiliary kernels: Taylor-Green initial state (Sec. 3.1, Eq. 11), the filter G
+// (Eq. 2, Sec. 2.6), FP64 integral diagnostics (Sec. 2.4, Eq. 9) and the training
+// pairs of Algorithm 1 (Sec. 2.1).
+#include <cmath>
+
+#include "dg_aux.h"
+
+namespace dgnn {
+
+// ---------------------------------------------------------------- Taylor-Green vortex
+
+__global__ void k_init_tgv(double* __restrict__ q, const double* __restrict__ pert, NodeGeom ng, double p0,
+                           double gamma) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= ng.N) return;
+  const int n = ng.n, np = n * n * n;
+  const int e = (int)(t / np), node = (int)(t - (long long)e * np);
+  const int i = node % n, j = (node / n) % n, k = node / (n * n);
+  const int K = ng.K;
+  const int ex = e % K, ey = (e / K) % K, ez = e / (K * K);
+  const double x = -M_PI + (ex + 0.5 * (ng.xi[i] + 1.0)) * ng.h;
+  const double y = -M_PI + (ey + 0.5 * (ng.xi[j] + 1.0)) * ng.h;
+  const double z = -M_PI + (ez + 0.5 * (ng.xi[k] + 1.0)) * ng.h;
+  double sx, cx, sy, cy, sz, cz;
+  sincos(x, &sx, &cx);
+  sincos(y, &sy, &cy);
+  sincos(z, &sz, &cz);
+  const double u = sx * cy * cz, v = -cx * sy * cz;
+  const double p = p0 + (cos(2.0 * x) + cos(2.0 * y)) * (cos(2.0 * z) + 2.0) / 16.0;
+  double qv[5] = {1.0, u, v, 0.0, p / (gamma - 1.0) + 0.5 * (u * u + v * v)};
+  for (int c = 0; c < 5; ++c) {
+    double val = qv[c];
+    if (pert) val += pert[c * ng.N + t];
+    q[c * ng.N + t] = val;
+  }
+}
+
+cudaError_t launch_init_tgv(const dg_ctx* c, double* q, const double* pert, cudaStream_t st) {
+  NodeGeom ng = node_geom(c);
+  const double p0 = 1.0 / (c->opts.gamma * c->Mach * c->Mach);
+  const int threads = 256;
+  const long long blocks = (c->N + threads - 1) / threads;
+  k_init_tgv<<<(unsigned)blocks, threads, 0, st>>>(q, pert, ng, p0, c->opts.gamma);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- filter G
+
+// One block per element: for each variable, apply the 1D filter along x, y, z.
+__global__ void k_project(const double* __restrict__ qh, double* __restrict__ ql, int nel, int nh, int nl,
+                          long long Nh, long long Nl, const double* __restrict__ Gm) {
+  __shared__ double sG[kMaxN1 * kMaxN1];
+  __shared__ double a[kMaxN1 * kMaxN1 * kMaxN1];
+  __shared__ double b[kMaxN1 * kMaxN1 * kMaxN1];
+  const int e = blockIdx.x;
+  if (e >= nel) return;
+  const int nph = nh * nh * nh, npl = nl * nl * nl;
+  for (int t = threadIdx.x; t < nl * nh; t += blockDim.x) sG[t] = Gm[t];
+  for (int v = 0; v < 5; ++v) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < nph; t += blockDim.x) a[t] = qh[v * Nh + (long long)e * nph + t];
+    __syncthreads();
+    // x pass: b[(ii, j, k)] (ii < nl, j, k < nh), x fastest
+    for (int t = threadIdx.x; t < nl * nh * nh; t += blockDim.x) {
+      const int ii = t % nl, j = (t / nl) % nh, k = t / (nl * nh);
+      double s = 0.0;
+      for (int m = 0; m < nh; ++m) s += sG[ii * nh + m] * a[m + nh * (j + nh * k)];
+      b[t] = s;
+    }
+    __syncthreads();
+    // y pass: a[(ii, jj, k)]
+    for (int t = threadIdx.x; t < nl * nl * nh; t += blockDim.x) {
+      const int ii = t % nl, jj = (t / nl) % nl, k = t / (nl * nl);
+      double s = 0.0;
+      for (int m = 0; m < nh; ++m) s += sG[jj * nh + m] * b[ii + nl * (m + nh * k)];
+      a[t] = s;
+    }
+    __syncthreads();
+    // z pass
+    for (int t = threadIdx.x; t < npl; t += blockDim.x) {
+      const int ii = t % nl, jj = (t / nl) % nl, kk = t / (nl * nl);
+      double s = 0.0;
+      for (int m = 0; m < nh; ++m) s += sG[kk * nh + m] * a[ii + nl * (jj + nl * m)];
+      ql[v * Nl + (long long)e * npl + t] = s;
+    }
+  }
+}
+
+cudaError_t launch_project(const dg_ctx* hi, const dg_ctx* lo, const double* qh, double* ql, const double* Gdev,
+                           cudaStream_t st) {
+  k_project<<<hi->nel, 256, 0, st>>>(qh, ql, hi->nel, hi->n, lo->n, hi->N, lo->N, Gdev);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- diagnostics
+
+// Per-node contributions reduced in a fixed order: block tree, then one block over the
+// block partials in index order -> bitwise reproducible for a given launch shape.
+__device__ __forceinline__ void diag_combine(double* a, const double* b) {
+#pragma unroll
+  for (int i = 0; i < kDiagSum; ++i) a[i] += b[i];
+#pragma unroll
+  for (int i = kDiagSum; i < kDiagLen; ++i) a[i] = fmax(a[i], b[i]);
+}
+
+__global__ void k_diag_partial(const double* __restrict__ q, const double* __restrict__ R,
+                               const double* __restrict__ qref, NodeGeom ng, double gamma,
+                               double* __restrict__ partial) {
+  __shared__ double sh[kDiagThreads][kDiagLen + 1];
+  double acc[kDiagLen];
+  for (int i = 0; i < kDiagLen; ++i) acc[i] = 0.0;
+  const int n = ng.n, np = n * n * n;
+  const double jac = 0.125 * ng.h * ng.h * ng.h;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ng.N;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int node = (int)(t % np);
+    const int i = node % n, j = (node / n) % n, k = node / (n * n);
+    const double W = ng.w[i] * ng.w[j] * ng.w[k] * jac;
+    double qv[5];
+    for (int c = 0; c < 5; ++c) qv[c] = q[c * ng.N + t];
+    bool finite = true;
+    for (int c = 0; c < 5; ++c) finite = finite && isfinite(qv[c]);
+    if (!finite) {
+      acc[kDiagNonfinite] += 1.0;
+      continue;
+    }
+    const double ir = 1.0 / qv[0];
+    const double vx = qv[1] * ir, vy = qv[2] * ir, vz = qv[3] * ir;
+    const double v2 = vx * vx + vy * vy + vz * vz;
+    const double p = (gamma - 1.0) * (qv[4] - 0.5 * qv[0] * v2);
+    acc[0] += W * qv[0];
+    acc[1] += W * qv[1];
+    acc[2] += W * qv[2];
+    acc[3] += W * qv[3];
+    acc[4] += W * qv[4];
+    acc[5] += W * 0.5 * qv[0] * v2;
+    if (R) {
+      const double dk = vx * R[1 * ng.N + t] + vy * R[2 * ng.N + t] + vz * R[3 * ng.N + t] - 0.5 * v2 * R[t];
+      acc[6] += W * dk;
+    }
+    if (qref) {
+      for (int c = 0; c < 3; ++c) acc[8 + c] = fmax(acc[8 + c], fabs(qv[1 + c] - qref[(1 + c) * ng.N + t]));
+    }
+    const double cs = sqrt(fmax(gamma * p * ir, 0.0));
+    acc[11] = fmax(acc[11], sqrt(v2) + cs);
+  }
+  for (int i = 0; i < kDiagLen; ++i) sh[threadIdx.x][i] = acc[i];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) diag_combine(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kDiagLen; ++i) partial[blockIdx.x * kDiagLen + i] = sh[0][i];
+}
+
+__global__ void k_diag_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+  __shared__ double sh[kDiagThreads][kDiagLen + 1];
+  double acc[kDiagLen];
+  for (int i = 0; i < kDiagLen; ++i) acc[i] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) diag_combine(acc, partial + b * kDiagLen);
+  for (int i = 0; i < kDiagLen; ++i) sh[threadIdx.x][i] = acc[i];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) diag_combine(sh[threadIdx.x], sh[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kDiagLen; ++i) out[i] = sh[0][i];
+}
+
+cudaError_t launch_diagnostics(const dg_ctx* c, const double* q, const double* R, const double* qref,
+                               double* partial, int nblocks, double* out, cudaStream_t st) {
+  NodeGeom ng = node_geom(c);
+  k_diag_partial<<<nblocks, kDiagThreads, 0, st>>>(q, R, qref, ng, c->opts.gamma, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_diag_final<<<1, kDiagThreads, 0, st>>>(partial, nblocks, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Algorithm 1 pairs
+
+__global__ void k_make_pairs(const double* __restrict__ qb_n, const double* __restrict__ qnn_np1,
+                             const double* __restrict__ qb_np1, double inv_dt, int first_var, int n_vars,
+                             long long N, int np, float* __restrict__ X, float* __restrict__ Y) {
+  const long long total = N * n_vars;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  // t enumerates (elem, slot, node) in the output order
+  const int feat = n_vars * np;
+  const long long e = t / feat;
+  const int f = (int)(t - e * feat);
+  const int slot = f / np, node = f - slot * np;
+  const long long src = (long long)(first_var + slot) * N + e * np + node;
+  X[t] = (float)qb_n[src];
+  Y[t] = (float)((qb_np1[src] - qnn_np1[src]) * inv_dt);
+}
+
+cudaError_t launch_make_pairs(const dg_ctx* lo, const double* qb_n, const double* qnn_np1, const double* qb_np1,
+                              double dt, int first_var, int n_vars, float* X, float* Y, cudaStream_t st) {
+  const long long total = lo->N * n_vars;
+  const int threads = 256;
+  k_make_pairs<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(
+      qb_n, qnn_np1, qb_np1, 1.0 / dt, first_var, n_vars, lo->N, lo->np, X, Y);
+  return cudaGetLastError();
+}
+
+}  // namespace dgnn

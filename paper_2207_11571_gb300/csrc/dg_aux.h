@@ -1,0 +1,54 @@
+// Declarations of the auxiliary kernels (initial state, filter, diagnostics, pairs).
+#pragma once
+
+#include "dg_common.h"
+
+namespace dgnn {
+
+// Node coordinates and quadrature weights of a context, by value for kernels.
+struct NodeGeom {
+  int K, n;
+  long long N;
+  double h;
+  double xi[kMaxN1];
+  double w[kMaxN1];
+};
+
+inline NodeGeom node_geom(const dg_ctx* c) {
+  NodeGeom g;
+  g.K = c->K;
+  g.n = c->n;
+  g.N = c->N;
+  g.h = 2.0 * M_PI / c->K;
+  for (int i = 0; i < kMaxN1; ++i) {
+    g.xi[i] = i < c->n ? c->basis.xi[i] : 0.0;
+    g.w[i] = i < c->n ? c->basis.w[i] : 0.0;
+  }
+  return g;
+}
+
+// Diagnostic vector: [0] mass, [1..3] momentum, [4] energy, [5] 2 pi^3 ke, [6] 2 pi^3 dke/dt,
+// [7] non-finite count (summed); [8..10] e_inf, [11] max wave speed (maxima).
+constexpr int kDiagSum = 8;
+constexpr int kDiagLen = 12;
+constexpr int kDiagNonfinite = 7;
+constexpr int kDiagThreads = 256;
+constexpr int kDiagBlocks = 1024;
+
+cudaError_t launch_init_tgv(const dg_ctx* c, double* q, const double* pert, cudaStream_t st);
+cudaError_t launch_project(const dg_ctx* hi, const dg_ctx* lo, const double* qh, double* ql, const double* Gdev,
+                           cudaStream_t st);
+cudaError_t launch_diagnostics(const dg_ctx* c, const double* q, const double* R, const double* qref,
+                               double* partial, int nblocks, double* out, cudaStream_t st);
+cudaError_t launch_make_pairs(const dg_ctx* lo, const double* qb_n, const double* qnn_np1, const double* qb_np1,
+                              double dt, int first_var, int n_vars, float* X, float* Y, cudaStream_t st);
+
+// Operator kernels per precision (dg_kernels_f32.cu / dg_kernels_f64.cu).
+cudaError_t gradient_f32(const dg_ctx* c, const double* q, cudaStream_t st);
+cudaError_t gradient_f64(const dg_ctx* c, const double* q, cudaStream_t st);
+cudaError_t flux_f32(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                     double dt, cudaStream_t st);
+cudaError_t flux_f64(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                     double dt, cudaStream_t st);
+
+}  // namespace dgnn

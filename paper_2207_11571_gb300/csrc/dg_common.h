@@ -1,0 +1,101 @@
+// Internal declarations shared by the translation units of libdgnn.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/dgnn.h"
+
+namespace dgnn {
+
+constexpr int kMaxP = 8;
+constexpr int kMaxN1 = kMaxP + 1;
+
+// Thread-local error message; returns the status for convenient `return fail(...)`.
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t err, const char* what);
+
+#define DG_CUDA(call)                                              \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return ::dgnn::cuda_fail(e_, #call);    \
+  } while (0)
+
+// 1D Gauss-Lobatto basis of order P, built on the host in FP64.
+struct Basis1D {
+  int P = 0;
+  double xi[kMaxN1];
+  double w[kMaxN1];
+  double D[kMaxN1 * kMaxN1];  // D[i * n + m] = l_m'(xi_i)
+};
+int build_basis(int P, Basis1D* out);
+// Filter G of Eq. 2 in 1D: (P_lo+1) x (P_hi+1), row-major.
+int build_filter(int P_hi, int P_lo, double* G);
+
+// Mesh and basis constants passed by value to every kernel.
+struct Geom {
+  int K;            // elements per direction
+  int nel;          // K^3
+  long long N;      // nodes = nel * n^3
+  int E;            // elements per block
+  double two_over_h;
+  double winv;      // 1 / w_0 = 1 / w_P
+  double D[kMaxN1 * kMaxN1];
+};
+
+// Physical constants of the operator.
+struct Phys {
+  double gamma;
+  double mu;         // 1 / Re
+  double lam;        // mu gamma / ((gamma-1) Pr): heat coefficient on grad(p/rho)
+  int les;           // Smagorinsky on/off
+  double csd2;       // (Cs * delta)^2
+  double lam_t;      // gamma / ((gamma-1) Prt): turbulent heat coefficient per unit mu_t
+};
+
+// Optional forcing source added to the operator: s[e * stride + slot * n^3 + node]
+// for variables first_var .. first_var + n_vars - 1.
+struct Forcing {
+  const float* s = nullptr;
+  int first_var = 0;
+  int n_vars = 0;
+  int stride = 0;
+};
+
+}  // namespace dgnn
+
+// The solver context behind the opaque dg_ctx handle.
+struct dg_ctx {
+  int K = 0, P = 0, n = 0, np = 0;
+  int closure = 0;
+  double Re = 0, Mach = 0, Pr = 0;
+  dg_opts opts{};
+  dgnn::Basis1D basis;
+  dgnn::Geom geom{};
+  dgnn::Phys phys{};
+  long long N = 0;
+  int nel = 0;
+  // workspace (device)
+  void* qf = nullptr;     // operator-precision copy of q, [5][N]
+  void* vis = nullptr;    // viscous stresses and heat flux, [9][N] operator precision
+  void* g = nullptr;      // RK register [5][N] (double or float)
+  double* rhs_tmp = nullptr;  // [5][N] FP64 operator value for diagnostics
+  double* red = nullptr;  // reduction partials
+  int red_blocks = 0;
+  double* red_host = nullptr;  // pinned host copy of the final reduction
+  double* q_dev = nullptr;     // device state for dg_advance_host
+  float* s_buf = nullptr;      // forcing buffer [nel][5 n^3]
+  double* filter_dev[dgnn::kMaxP + 1] = {};  // filter G to each lower order (dg_project)
+};
+
+namespace dgnn {
+
+// Launchers of the operator kernels (dg_kernels_*.cu).  All return cudaError_t.
+cudaError_t launch_gradient(const dg_ctx* c, const double* q, cudaStream_t st);
+// mode 0: dqdt = R (+ s); mode 1: RK stage g = A g + dt R; q += B g
+cudaError_t launch_flux(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode,
+                        double rkA, double rkB, double dt, cudaStream_t st);
+
+}  // namespace dgnn

@@ -1,0 +1,10 @@
+// FP32 instantiation of the operator kernels (FP32 fluxes and contractions, FP64 state).
+#include "dg_launch.cuh"
+
+namespace dgnn {
+cudaError_t gradient_f32(const dg_ctx* c, const double* q, cudaStream_t st) { return gradient_t<float>(c, q, st); }
+cudaError_t flux_f32(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                     double dt, cudaStream_t st) {
+  return flux_t<float>(c, q, dqdt, f, mode, A, B, dt, st);
+}
+}  // namespace dgnn

@@ -1,0 +1,10 @@
+// FP64 instantiation of the operator kernels (the parity path).
+#include "dg_launch.cuh"
+
+namespace dgnn {
+cudaError_t gradient_f64(const dg_ctx* c, const double* q, cudaStream_t st) { return gradient_t<double>(c, q, st); }
+cudaError_t flux_f64(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                     double dt, cudaStream_t st) {
+  return flux_t<double>(c, q, dqdt, f, mode, A, B, dt, st);
+}
+}  // namespace dgnn

@@ -1,0 +1,13 @@
+// Interface between the solver and the forcing network (nn_*.cu).
+#pragma once
+
+#include "dg_common.h"
+
+namespace dgnn {
+
+// Runs the network on every element of state q (context c) and writes the forcing
+// s[e][slot * n^3 + node] (float) for variables first_var .. first_var + n_vars - 1.
+int nn_forcing_on_state(const nn_model* net, const dg_ctx* c, const double* q, float* s, int* first_var,
+                        int* n_vars, cudaStream_t st);
+
+}  // namespace dgnn

@@ -1,0 +1,236 @@
+"""Thin Python binding of libdgnn.so (C ABI in include/dgnn.h).
+
+Functions keep the C names and only marshal arguments: tensors become device
+pointers, Python numbers become C scalars, a non-zero status raises
+``DGError`` with the library's message.  Every computation runs in the CUDA
+library; there is no fallback: if ``libdgnn.so`` is missing, loading raises.
+"""
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libdgnn.so")
+
+DG_OK = 0
+DG_ERR_INVALID_ARG = -1
+DG_ERR_CUDA = -2
+DG_ERR_NONFINITE = -3
+DG_ERR_TIMEOUT = -4
+DG_ERR_IO = -5
+DG_ERR_UNSUPPORTED = -6
+
+DG_PREC_FP64 = 0
+DG_PREC_FP32 = 1
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libdgnn status {status}: {msg}")
+        self.status = status
+
+
+class dg_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("rk_register_fp32", ctypes.c_int),
+                ("gamma", ctypes.c_double), ("Cs", ctypes.c_double), ("Prt", ctypes.c_double),
+                ("les_delta", ctypes.c_double), ("elems_per_block", ctypes.c_int)]
+
+
+class dg_diag(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("momentum", ctypes.c_double * 3), ("energy", ctypes.c_double),
+                ("ke", ctypes.c_double), ("dke_dt", ctypes.c_double), ("e_inf", ctypes.c_double * 3),
+                ("max_wave", ctypes.c_double), ("nonfinite", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {"mass": self.mass, "momentum": list(self.momentum), "energy": self.energy, "ke": self.ke,
+                "dke_dt": self.dke_dt, "e_inf": list(self.e_inf), "max_wave": self.max_wave,
+                "nonfinite": int(self.nonfinite)}
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+# name -> argument types (all return int)
+_SIGS = {
+    "dg_opts_default": [ctypes.POINTER(dg_opts)],
+    "dg_create": [_I, _I, _D, _D, _D, _I, ctypes.POINTER(dg_opts), ctypes.POINTER(_P)],
+    "dg_destroy": [_P],
+    "dg_basis_1d": [_I, _P, _P, _P],
+    "dg_sizes": [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+    "dg_init_tgv": [_P, _P, _P, _P],
+    "dg_rhs": [_P, _P, _P, _P, _P],
+    "dg_rk3_step": [_P, _P, _D, _I, _P, _P],
+    "dg_advance_host": [_P, _P, _D, _I, _P, ctypes.POINTER(dg_diag), _P],
+    "dg_project": [_P, _P, _P, _P, _P],
+    "dg_diagnostics": [_P, _P, _P, _P, ctypes.POINTER(dg_diag), _P],
+    "dg_stable_dt": [_P, _P, _D, ctypes.POINTER(_D), _P],
+    "dg_make_pairs": [_P, _P, _P, _P, _D, _I, _I, _P, _P, _P],
+}
+
+_lib = None
+
+
+def lib():
+    """Loads libdgnn.so once; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2207_11571_gb300.build` "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.dg_last_error.argtypes = []
+        L.dg_last_error.restype = ctypes.c_char_p
+        _register_nn(L)
+        _lib = L
+    return _lib
+
+
+def _register_nn(L):
+    from . import nn as _nn
+    _nn._register(L)
+
+
+def check(status):
+    if status != DG_OK:
+        raise DGError(status, lib().dg_last_error().decode(errors="replace"))
+    return status
+
+
+def ptr(t):
+    """Device (or host numpy) pointer of a contiguous array, or None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(t.data_ptr())
+    if hasattr(t, "ctypes"):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(t.ctypes.data)
+    raise TypeError(f"cannot take a pointer of {type(t)}")
+
+
+def stream_ptr(stream=None):
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return None
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_state(ctx, t, name, dtype="float64"):
+    n = dg_sizes(ctx)[0]
+    if t.numel() != 5 * n:
+        raise ValueError(f"{name} must hold 5 * {n} values, got {t.numel()}")
+    if str(t.dtype).split(".")[-1] != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if hasattr(t, "is_cuda") and not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+
+
+# ----------------------------------------------------------------------------- entry points
+
+def dg_opts_default():
+    o = dg_opts()
+    check(lib().dg_opts_default(ctypes.byref(o)))
+    return o
+
+
+def dg_create(K, P, Re, Mach, Pr=0.71, closure=0, opts=None, **kw):
+    """Returns an opaque context handle (int).  ``kw`` overrides fields of dg_opts."""
+    o = opts if opts is not None else dg_opts_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    check(lib().dg_create(int(K), int(P), float(Re), float(Mach), float(Pr), int(closure), ctypes.byref(o),
+                          ctypes.byref(h)))
+    return h.value
+
+
+def dg_destroy(ctx):
+    check(lib().dg_destroy(ctypes.c_void_p(ctx)))
+
+
+def dg_basis_1d(P):
+    import numpy as np
+    n = P + 1
+    xi, w, D = np.zeros(n), np.zeros(n), np.zeros((n, n))
+    check(lib().dg_basis_1d(int(P), ptr(xi), ptr(w), ptr(D)))
+    return xi, w, D
+
+
+def dg_sizes(ctx):
+    n, e = ctypes.c_int64(), ctypes.c_int64()
+    check(lib().dg_sizes(ctypes.c_void_p(ctx), ctypes.byref(n), ctypes.byref(e)))
+    return n.value, e.value
+
+
+def _net(net):
+    return None if net is None else ctypes.c_void_p(net if isinstance(net, int) else net.handle)
+
+
+def dg_init_tgv(ctx, q, perturbation=None, stream=None):
+    _check_state(ctx, q, "q")
+    if perturbation is not None:
+        _check_state(ctx, perturbation, "perturbation")
+    check(lib().dg_init_tgv(ctypes.c_void_p(ctx), ptr(q), ptr(perturbation), stream_ptr(stream)))
+
+
+def dg_rhs(ctx, q, dqdt, forcing=None, stream=None):
+    _check_state(ctx, q, "q")
+    _check_state(ctx, dqdt, "dqdt")
+    check(lib().dg_rhs(ctypes.c_void_p(ctx), ptr(q), ptr(dqdt), _net(forcing), stream_ptr(stream)))
+
+
+def dg_rk3_step(ctx, q, dt, nsteps=1, forcing=None, stream=None):
+    _check_state(ctx, q, "q")
+    check(lib().dg_rk3_step(ctypes.c_void_p(ctx), ptr(q), float(dt), int(nsteps), _net(forcing),
+                            stream_ptr(stream)))
+
+
+def dg_advance_host(ctx, q_host, dt, nsteps=1, forcing=None, stream=None, want_diag=True):
+    """q_host: numpy float64 or CPU torch tensor (pinned or pageable), updated in place."""
+    d = dg_diag()
+    check(lib().dg_advance_host(ctypes.c_void_p(ctx), ptr(q_host), float(dt), int(nsteps), _net(forcing),
+                                ctypes.byref(d) if want_diag else None, stream_ptr(stream)))
+    return d.as_dict() if want_diag else None
+
+
+def dg_project(hi, lo, q_hi, q_lo, stream=None):
+    _check_state(hi, q_hi, "q_hi")
+    _check_state(lo, q_lo, "q_lo")
+    check(lib().dg_project(ctypes.c_void_p(hi), ctypes.c_void_p(lo), ptr(q_hi), ptr(q_lo), stream_ptr(stream)))
+
+
+def dg_diagnostics(ctx, q, q_ref=None, forcing=None, stream=None, raise_nonfinite=True):
+    _check_state(ctx, q, "q")
+    d = dg_diag()
+    st = lib().dg_diagnostics(ctypes.c_void_p(ctx), ptr(q), ptr(q_ref), _net(forcing), ctypes.byref(d),
+                              stream_ptr(stream))
+    if st != DG_ERR_NONFINITE or raise_nonfinite:
+        check(st)
+    return d.as_dict()
+
+
+def dg_stable_dt(ctx, q, cfl, stream=None):
+    _check_state(ctx, q, "q")
+    dt = ctypes.c_double()
+    check(lib().dg_stable_dt(ctypes.c_void_p(ctx), ptr(q), float(cfl), ctypes.byref(dt), stream_ptr(stream)))
+    return dt.value
+
+
+def dg_make_pairs(lo, q_bar_n, q_nn_np1, q_bar_np1, dt, first_var, n_vars, X, Y, stream=None):
+    for t, nm in ((q_bar_n, "q_bar_n"), (q_nn_np1, "q_nn_np1"), (q_bar_np1, "q_bar_np1")):
+        _check_state(lo, t, nm)
+    nodes, _ = dg_sizes(lo)
+    for t, nm in ((X, "X"), (Y, "Y")):
+        if t.numel() != nodes * n_vars or str(t.dtype) != "torch.float32":
+            raise ValueError(f"{nm} must be float32 with {nodes * n_vars} values")
+    check(lib().dg_make_pairs(ctypes.c_void_p(lo), ptr(q_bar_n), ptr(q_nn_np1), ptr(q_bar_np1), float(dt),
+                              int(first_var), int(n_vars), ptr(X), ptr(Y), stream_ptr(stream)))

@@ -1,0 +1,81 @@
+"""Host-side checks of the C ABI: the library loads, exports every declared symbol,
+validates arguments, and its host-built basis matches closed forms and the oracle.
+No GPU needed (no device compute is launched)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from tests.libbuild import ensure_built
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    ensure_built()
+    from paper_2207_11571_gb300 import dg
+    return dg.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?\w+\s*\*?\s*((?:dg|nn)_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for required in ("dg_create", "dg_rhs", "dg_rk3_step", "dg_diagnostics", "dg_project", "dg_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_opts_defaults(L):
+    from paper_2207_11571_gb300 import dg
+    o = dg.dg_opts_default()
+    assert o.precision == dg.DG_PREC_FP64 and o.gamma == 1.4 and o.Cs == 0.1 and o.Prt == 0.9
+
+
+@pytest.mark.parametrize("bad", [dict(K=0), dict(K=300), dict(P=0), dict(P=9), dict(Re=-1.0),
+                                 dict(Mach=0.0), dict(closure=2)])
+def test_create_rejects_bad_arguments_before_touching_cuda(L, bad):
+    from paper_2207_11571_gb300 import dg
+    args = dict(K=4, P=3, Re=1600.0, Mach=0.1, Pr=0.71, closure=0)
+    args.update(bad)
+    with pytest.raises(dg.DGError) as e:
+        dg.dg_create(**args)
+    assert e.value.status == dg.DG_ERR_INVALID_ARG
+    assert b"dg_create" in L.dg_last_error()
+
+
+def test_null_handles_are_rejected(L):
+    from paper_2207_11571_gb300 import dg
+    assert L.dg_rhs(None, None, None, None, None) == dg.DG_ERR_INVALID_ARG
+    assert L.dg_destroy(None) == dg.DG_ERR_INVALID_ARG
+    assert L.dg_rk3_step(None, None, 1e-3, 1, None, None) == dg.DG_ERR_INVALID_ARG
+
+
+def test_host_basis_matches_closed_forms_and_oracle(L):
+    from oracle import basis
+    from paper_2207_11571_gb300 import dg
+    xi, w, D = dg.dg_basis_1d(3)
+    np.testing.assert_allclose(xi, [-1, -5 ** -0.5, 5 ** -0.5, 1], atol=1e-15)
+    np.testing.assert_allclose(w, [1 / 6, 5 / 6, 5 / 6, 1 / 6], rtol=1e-14)
+    for P in range(1, 9):
+        xi, w, D = dg.dg_basis_1d(P)
+        xo, wo = basis.gl_nodes_weights(P)
+        np.testing.assert_allclose(xi, xo, atol=2e-15)
+        np.testing.assert_allclose(w, wo, rtol=1e-13)
+        np.testing.assert_allclose(D, basis.lagrange_derivative_matrix(xo), atol=1e-12 * P * P)

@@ -1,0 +1,211 @@
+"""GPU parity of the DGSEM path (C ABI) against the FP64 oracle on the same seeded inputs."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import algorithm1, dgsem, physics
+from paper_2207_11571_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# FP32 operator error bound against the FP64 oracle, relative L2 over the whole
+# 5N vector: O(1e-7) rounding amplified by the cancellation in the flux derivative
+# (energy fluxes ~ v (rho e + p) ~ 250 at Mach 0.1, differences ~ 1).
+FP32_RHS_RTOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def dg():
+    from tests.libbuild import ensure_built
+    ensure_built()
+    from paper_2207_11571_gb300 import dg as _dg
+    _dg.lib()
+    return _dg
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a.reshape(5, -1))).cuda()
+
+
+def to_np(t, K, n):
+    return t.double().cpu().numpy().reshape(5, K, K, K, n, n, n)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+class Ctx:
+    def __init__(self, dg, K, P, Re=1600.0, Mach=0.1, Pr=0.71, les=False, **kw):
+        self.dg, self.K, self.P, self.n = dg, K, P, P + 1
+        self.h = dg.dg_create(K, P, Re, Mach, Pr, int(les), **kw)
+        self.flow = physics.Flow(Re=Re, Mach=Mach, Pr=Pr, les=les)
+        self.mesh = dgsem.Mesh(K, P)
+        self.N = K ** 3 * (P + 1) ** 3
+
+    def __del__(self):
+        try:
+            self.dg.dg_destroy(self.h)
+        except Exception:
+            pass
+
+    def tgv(self, seed=inputs.TGV_SEED):
+        pert = inputs.perturbation((5, self.N), seed=seed)
+        q_or = dgsem.tgv_state(self.mesh, self.flow, pert)
+        q = torch.empty(5 * self.N, dtype=torch.float64, device="cuda")
+        self.dg.dg_init_tgv(self.h, q, torch.from_numpy(pert.ravel()).cuda())
+        return q, q_or
+
+    def rhs(self, q):
+        out = torch.empty_like(q)
+        self.dg.dg_rhs(self.h, q, out)
+        torch.cuda.synchronize()
+        return to_np(out, self.K, self.n)
+
+
+CASES = [  # K, P, les, elems_per_block (0 = default)
+    (4, 3, False, 0), (4, 3, True, 0), (3, 3, False, 4),   # 27 elements in blocks of 4: ragged tail
+    (3, 2, True, 0), (3, 6, False, 0), (2, 8, True, 0), (1, 3, False, 0), (2, 1, False, 0), (2, 5, False, 2),
+]
+
+
+@pytest.mark.parametrize("K,P,les,E", CASES)
+def test_init_tgv_matches_oracle(dg, K, P, les, E):
+    c = Ctx(dg, K, P, les=les, elems_per_block=E)
+    q, q_or = c.tgv()
+    np.testing.assert_allclose(to_np(q, K, P + 1), q_or, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("K,P,les,E", CASES)
+def test_rhs_fp64_matches_oracle_on_tgv(dg, K, P, les, E):
+    c = Ctx(dg, K, P, les=les, elems_per_block=E)
+    q, q_or = c.tgv()
+    # feed both sides the same state: the oracle's initial field
+    q = to_dev(q_or)
+    err = rel_l2(c.rhs(q), dgsem.rhs(q_or, c.mesh, c.flow))
+    assert err < 1e-12, err
+
+
+@pytest.mark.parametrize("K,P,les,E", [(3, 3, True, 4), (2, 6, False, 0), (2, 2, True, 0), (1, 4, True, 0)])
+def test_rhs_fp64_matches_oracle_on_rough_state(dg, K, P, les, E):
+    """Random per-node states (every interface jumps): exercises Roe and BR1 face terms."""
+    c = Ctx(dg, K, P, Re=50.0, Mach=0.3, les=les, elems_per_block=E)
+    q_or = inputs.random_conserved((K,) * 3 + (P + 1,) * 3, seed=100 + P, rhoE=(1 / (1.4 * 0.09) / 0.4, 1.0))
+    err = rel_l2(c.rhs(to_dev(q_or)), dgsem.rhs(q_or, c.mesh, c.flow))
+    assert err < 1e-12, err
+
+
+@pytest.mark.parametrize("K,P,les", [(4, 3, False), (3, 3, True), (2, 6, True), (2, 8, False)])
+def test_rhs_fp32_error_against_fp64_oracle(dg, K, P, les):
+    c = Ctx(dg, K, P, les=les, precision=1)
+    _, q_or = c.tgv()
+    err = rel_l2(c.rhs(to_dev(q_or)), dgsem.rhs(q_or, c.mesh, c.flow))
+    print(f"FP32 operator rel L2 error K={K} P={P} les={les}: {err:.3e}")
+    assert err < FP32_RHS_RTOL, err
+
+
+def test_rk3_100_steps_fp64_matches_oracle(dg):
+    """4^3 elements, P = 3, Re 1600, Mach 0.1, dt = 1e-3, 100 steps, FP64."""
+    c = Ctx(dg, 4, 3)
+    _, q_or = c.tgv()
+    q = to_dev(q_or)
+    dg.dg_rk3_step(c.h, q, 1e-3, 100)
+    ref = q_or
+    for _ in range(100):
+        ref = dgsem.rk3_step(ref, 1e-3, lambda z: dgsem.rhs(z, c.mesh, c.flow))
+    err = rel_l2(to_np(q, 4, 4), ref)
+    assert err < 1e-10, err
+
+
+@pytest.mark.parametrize("prec,rk32", [(0, 0), (1, 0), (1, 1)])
+def test_rk3_conserves_mass_momentum_energy(dg, prec, rk32):
+    c = Ctx(dg, 6, 3, Re=200.0, precision=prec, rk_register_fp32=rk32)
+    q, _ = c.tgv()
+    d0 = dg.dg_diagnostics(c.h, q)
+    dg.dg_rk3_step(c.h, q, 2e-3, 20)
+    d1 = dg.dg_diagnostics(c.h, q)
+    assert abs(d1["mass"] - d0["mass"]) < 1e-13 * d0["mass"]
+    assert abs(d1["energy"] - d0["energy"]) < 1e-13 * d0["energy"]
+    assert max(abs(a - b) for a, b in zip(d1["momentum"], d0["momentum"])) < 1e-12
+    assert d1["ke"] < d0["ke"]
+
+
+def test_diagnostics_match_oracle(dg):
+    c = Ctx(dg, 4, 3, Re=200.0)
+    _, q_or = c.tgv()
+    q = to_dev(q_or)
+    qref = to_dev(q_or * (1 + 1e-3 * inputs.normal(q_or.shape, 3)))
+    d = dg.dg_diagnostics(c.h, q, qref)
+    R = dgsem.rhs(q_or, c.mesh, c.flow)
+    o = dgsem.diagnostics(q_or, c.mesh, c.flow, R=R, q_ref=qref.cpu().numpy().reshape(q_or.shape))
+    for k in ("mass", "energy", "ke", "max_wave"):
+        assert d[k] == pytest.approx(o[k], rel=1e-13), k
+    assert d["dke_dt"] == pytest.approx(o["dke_dt"], rel=1e-10)
+    np.testing.assert_allclose(d["momentum"], o["momentum"], atol=1e-13)
+    np.testing.assert_allclose(d["e_inf"], o["e_inf"], rtol=1e-15)
+    assert d["nonfinite"] == 0
+
+
+def test_diagnostics_flag_nonfinite_state(dg):
+    c = Ctx(dg, 2, 3)
+    q, _ = c.tgv()
+    q[17] = float("nan")
+    with pytest.raises(dg.DGError) as e:
+        dg.dg_diagnostics(c.h, q)
+    assert e.value.status == dg.DG_ERR_NONFINITE
+    assert dg.dg_diagnostics(c.h, q, raise_nonfinite=False)["nonfinite"] == 1
+
+
+def test_stable_dt_matches_oracle(dg):
+    c = Ctx(dg, 4, 3)
+    _, q_or = c.tgv()
+    dt = dg.dg_stable_dt(c.h, to_dev(q_or), 0.7)
+    assert dt == pytest.approx(dgsem.stable_dt(q_or, c.mesh, c.flow, 0.7), rel=1e-14)
+
+
+@pytest.mark.parametrize("P_hi,P_lo,K", [(8, 3, 2), (6, 2, 3), (5, 5, 2)])
+def test_project_matches_oracle(dg, P_hi, P_lo, K):
+    hi, lo = Ctx(dg, K, P_hi), Ctx(dg, K, P_lo)
+    _, q_or = hi.tgv()
+    q_lo = torch.empty(5 * lo.N, dtype=torch.float64, device="cuda")
+    dg.dg_project(hi.h, lo.h, to_dev(q_or), q_lo)
+    np.testing.assert_allclose(to_np(q_lo, K, P_lo + 1), dgsem.project(q_or, P_hi, P_lo), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("first,nv", [(0, 5), (1, 3)])
+def test_make_pairs_match_oracle(dg, first, nv):
+    """Algorithm 1's pair (q_bar^n, (q_bar^{n+1} - q_NN^{n+1}) / dt) on the GPU vs the oracle."""
+    m8, m3 = dgsem.Mesh(2, 5), dgsem.Mesh(2, 3)
+    flow = physics.Flow(Re=200.0)
+    q8 = dgsem.tgv_state(m8, flow, inputs.perturbation((5, 8 * 216)))
+    X_or, T_or, q_end = algorithm1.generate_pairs(q8, m8, m3, flow, flow, 2e-3, 2, 1, tuple(range(first, first + nv)))
+    lo = Ctx(dg, 2, 3, Re=200.0)
+    qb_n = dgsem.project(q8, 5, 3)
+    qnn1 = dgsem.rk3_step(qb_n, 2e-3, lambda z: dgsem.rhs(z, m3, flow))
+    qb1 = dgsem.project(q_end, 5, 3)
+    X = torch.empty(8 * nv * 64, dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(X)
+    dg.dg_make_pairs(lo.h, to_dev(qb_n), to_dev(qnn1), to_dev(qb1), 2e-3, first, nv, X, Y)
+    np.testing.assert_array_equal(X.cpu().numpy().reshape(X_or.shape), X_or.astype(np.float32))
+    np.testing.assert_array_equal(Y.cpu().numpy().reshape(T_or.shape), T_or.astype(np.float32))
+
+
+def test_advance_host_equals_device_path(dg):
+    c = Ctx(dg, 3, 3, precision=1)
+    q, q_or = c.tgv()
+    host = q.cpu().numpy().copy()
+    d = dg.dg_advance_host(c.h, host, 1e-3, 3)
+    dg.dg_rk3_step(c.h, q, 1e-3, 3)
+    np.testing.assert_array_equal(host, q.cpu().numpy())
+    assert d["mass"] == pytest.approx((2 * math.pi) ** 3, rel=1e-12)
+
+
+def test_rhs_rejects_aliasing_and_size_mismatch(dg):
+    c = Ctx(dg, 2, 3)
+    q, _ = c.tgv()
+    with pytest.raises(dg.DGError):
+        dg.dg_rhs(c.h, q, q)
+    with pytest.raises(ValueError):
+        dg.dg_rhs(c.h, q, torch.empty(10, dtype=torch.float64, device="cuda"))
