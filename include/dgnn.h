@@ -47,16 +47,18 @@ typedef enum {
 typedef struct dg_ctx dg_ctx;
 typedef struct nn_model nn_model;
 
-/* Arithmetic of the spatial operator.  The state q and the RK accumulation are
- * FP64 in both modes. */
+/* Arithmetic of the spatial operator.  The state q is FP64 in both modes.
+ * DG_PREC_FP64: every step in FP64, q updated in FP64 at every RK stage (parity path).
+ * DG_PREC_FP32: fluxes, contractions and lifting in FP32 on the state relative to the
+ *   reference (rho0 = 1, p0); within an RK3 step the stages accumulate the increment in
+ *   FP32 and q is updated once per step in FP64. */
 typedef enum {
-  DG_PREC_FP64 = 0, /* every step of the operator in FP64 (parity path) */
-  DG_PREC_FP32 = 1  /* operator (fluxes, contractions, lifting) in FP32 */
+  DG_PREC_FP64 = 0,
+  DG_PREC_FP32 = 1
 } dg_precision;
 
 typedef struct {
   int precision;      /* dg_precision, default DG_PREC_FP64 */
-  int rk_register_fp32; /* 1: the low-storage RK register g is FP32 (FP32 operator only); default 0 */
   double gamma;       /* ratio of specific heats, default 1.4 */
   double Cs;          /* Smagorinsky constant, default 0.1 */
   double Prt;         /* turbulent Prandtl number, default 0.9 */
@@ -149,6 +151,24 @@ int dg_stable_dt(dg_ctx* ctx, const double* q, double cfl, double* dt_out, void*
 int dg_make_pairs(const dg_ctx* lo, const double* q_bar_n, const double* q_nn_np1,
                   const double* q_bar_np1, double dt, int first_var, int n_vars,
                   float* X, float* Y, void* stream);
+
+/* Measurement: advances q like dg_rk3_step (nsteps RK3 steps, no forcing) while
+ * recording CUDA events on `stream` around every kernel launch.  Returns the summed
+ * device time in milliseconds of the phase-A (BR1 gradient) and phase-B (flux, lift,
+ * RK update) kernels, the number of launches of each, and the algorithmic bytes one
+ * phase-B launch moves on average (state, stresses and RK register: each value read
+ * or written once).  All outputs are HOST pointers; any may be NULL.  Synchronises. */
+int dg_profile_rk3(dg_ctx* ctx, double* q, double dt, int nsteps, double* ms_gradient,
+                   double* ms_flux, int* launches_gradient, int* launches_flux,
+                   double* flux_bytes_per_launch, double* gradient_bytes_per_launch,
+                   void* stream);
+
+/* Self-check of the integer-pipe FP64 <-> FP32 conversions the FP32 operator uses:
+ * counts the n DEVICE inputs x where the round-to-nearest-even FP64 -> FP32 conversion
+ * differs from the hardware conversion (mismatches[0]; inputs should be zero or within
+ * the FP32 normal range, outside of which the library flushes to zero) and where the
+ * widening FP32 -> FP64 is not exact (mismatches[1]).  mismatches: HOST, 2 values. */
+int dg_check_conversions(const double* x, int64_t n, int64_t* mismatches, void* stream);
 
 const char* dg_last_error(void);
 

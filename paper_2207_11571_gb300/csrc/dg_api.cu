@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "dg_aux.h"
 #include "dg_kernels.cuh"
@@ -42,14 +43,40 @@ int cuda_fail(cudaError_t err, const char* what) {
   return fail(DG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(err));
 }
 
-cudaError_t launch_gradient(const dg_ctx* c, const double* q, cudaStream_t st) {
-  return c->opts.precision == DG_PREC_FP32 ? gradient_f32(c, q, st) : gradient_f64(c, q, st);
+cudaError_t launch_gradient(const dg_ctx* c, const double* q, int src, cudaStream_t st) {
+  return c->opts.precision == DG_PREC_FP32 ? gradient_f32(c, q, src, st) : gradient_f64(c, q, src, st);
 }
 
 cudaError_t launch_flux(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
                         double dt, cudaStream_t st) {
-  return c->opts.precision == DG_PREC_FP32 ? flux_f32(c, q, dqdt, f, mode, A, B, dt, st)
-                                           : flux_f64(c, q, dqdt, f, mode, A, B, dt, st);
+  RkArgs rk{A, B, dt, 1.0 / kRkB[0]};
+  return c->opts.precision == DG_PREC_FP32 ? flux_f32(c, q, dqdt, f, mode, rk, st)
+                                           : flux_f64(c, q, dqdt, f, mode, rk, st);
+}
+
+// Launch plan of RK stage k (0, 1, 2): source of the phase-A stage state and phase-B mode.
+static void stage_plan(const dg_ctx* c, int k, int* src, int* mode) {
+  if (c->opts.precision == DG_PREC_FP32) {
+    *src = (k == 0) ? 0 : 1;
+    *mode = 2 + k;
+  } else {
+    *src = 0;
+    *mode = 1;
+  }
+}
+
+// Algorithmic bytes per node of the phase-A and phase-B launches of stage k: every value
+// the kernel must read or write once (neighbour interface reads are L2 hits, not counted).
+static void stage_bytes(const dg_ctx* c, int k, double* grad, double* flux) {
+  if (c->opts.precision == DG_PREC_FP32) {
+    const double A[3] = {40 + 20 + 20 + 36, 20 + 20 + 20 + 36, 20 + 20 + 20 + 36};
+    const double B[3] = {20 + 36 + 20, 20 + 36 + 20 + 20 + 20, 20 + 36 + 20 + 20 + 40 + 40};
+    *grad = A[k];
+    *flux = B[k];
+  } else {
+    *grad = 40 + 40 + 72;
+    *flux = 40 + 72 + (k ? 40 : 0) + 40 + 40 + 40;
+  }
 }
 
 // Evaluates the network forcing on the current state q (all elements) into c->s_buf.
@@ -67,7 +94,7 @@ static int forcing_for(dg_ctx* c, const double* q, const nn_model* net, Forcing*
 }
 
 static int rhs_into(dg_ctx* c, const double* q, double* out, const nn_model* net, cudaStream_t st) {
-  DG_CUDA(launch_gradient(c, q, st));
+  DG_CUDA(launch_gradient(c, q, 0, st));
   Forcing f;
   int rc = forcing_for(c, q, net, &f, st);
   if (rc) return rc;
@@ -78,11 +105,13 @@ static int rhs_into(dg_ctx* c, const double* q, double* out, const nn_model* net
 static int rk3_steps(dg_ctx* c, double* q, double dt, int nsteps, const nn_model* net, cudaStream_t st) {
   for (int s = 0; s < nsteps; ++s)
     for (int k = 0; k < 3; ++k) {
-      DG_CUDA(launch_gradient(c, q, st));
+      int src, mode;
+      stage_plan(c, k, &src, &mode);
+      DG_CUDA(launch_gradient(c, q, src, st));
       Forcing f;
       int rc = forcing_for(c, q, net, &f, st);
       if (rc) return rc;
-      DG_CUDA(launch_flux(c, q, nullptr, f, 1, kRkA[k], kRkB[k], dt, st));
+      DG_CUDA(launch_flux(c, q, nullptr, f, mode, kRkA[k], kRkB[k], dt, st));
     }
   return DG_OK;
 }
@@ -123,7 +152,6 @@ int dg_opts_default(dg_opts* o) {
   if (!o) return fail(DG_ERR_INVALID_ARG, "dg_opts_default: NULL");
   std::memset(o, 0, sizeof(*o));
   o->precision = DG_PREC_FP64;
-  o->rk_register_fp32 = 0;
   o->gamma = 1.4;
   o->Cs = 0.1;
   o->Prt = 0.9;
@@ -144,8 +172,6 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
   if (opts) o = *opts;
   if (o.precision != DG_PREC_FP64 && o.precision != DG_PREC_FP32)
     return fail(DG_ERR_INVALID_ARG, "dg_create: unknown precision");
-  if (o.rk_register_fp32 && o.precision != DG_PREC_FP32)
-    return fail(DG_ERR_INVALID_ARG, "dg_create: an FP32 RK register needs the FP32 operator");
   if (!(o.gamma > 1.0)) return fail(DG_ERR_INVALID_ARG, "dg_create: gamma must be > 1");
   if (o.elems_per_block > max_elems_per_block(P))
     return fail(DG_ERR_INVALID_ARG, "dg_create: elems_per_block exceeds the block size limit for this P");
@@ -184,14 +210,26 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
   const double delta = o.les_delta > 0 ? o.les_delta : h / (P + 1);
   c->phys.csd2 = (o.Cs * delta) * (o.Cs * delta);
   c->phys.lam_t = g / ((g - 1.0) * o.Prt);
+  if (o.precision == DG_PREC_FP32) {
+    // reference state: rho0 = 1 and the background pressure p0 = 1/(gamma M^2)
+    c->phys.rho_ref = 1.0;
+    c->phys.p_ref = 1.0 / (g * Mach * Mach);
+    c->phys.E_ref = c->phys.p_ref / (g - 1.0);
+  } else {
+    c->phys.rho_ref = c->phys.p_ref = c->phys.E_ref = 0.0;
+  }
+  c->phys.Hc = c->phys.E_ref + c->phys.p_ref;
+  c->phys.theta_ref = c->phys.rho_ref > 0 ? c->phys.p_ref / c->phys.rho_ref : 0.0;
 
-  const size_t tsz = o.precision == DG_PREC_FP32 ? sizeof(float) : sizeof(double);
-  const size_t gsz = o.rk_register_fp32 ? sizeof(float) : sizeof(double);
+  const bool f32 = o.precision == DG_PREC_FP32;
+  const size_t tsz = f32 ? sizeof(float) : sizeof(double);
   c->red_blocks = kDiagBlocks;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&c->qf, 5 * c->N * tsz);
   if (e == cudaSuccess) e = cudaMalloc(&c->vis, 9 * c->N * tsz);
-  if (e == cudaSuccess) e = cudaMalloc(&c->g, 5 * c->N * gsz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->g, 5 * c->N * tsz);
+  if (f32 && e == cudaSuccess) e = cudaMalloc(&c->qn32, 5 * c->N * sizeof(float));
+  if (f32 && e == cudaSuccess) e = cudaMalloc(&c->dlt, 5 * c->N * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&c->rhs_tmp, 5 * c->N * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->red, (size_t)(c->red_blocks + 1) * kDiagLen * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&c->red_host, kDiagLen * sizeof(double));
@@ -209,6 +247,8 @@ int dg_destroy(dg_ctx* c) {
   cudaFree(c->qf);
   cudaFree(c->vis);
   cudaFree(c->g);
+  cudaFree(c->qn32);
+  cudaFree(c->dlt);
   cudaFree(c->rhs_tmp);
   cudaFree(c->red);
   cudaFree(c->s_buf);
@@ -314,6 +354,55 @@ int dg_make_pairs(const dg_ctx* lo, const double* q_bar_n, const double* q_nn_np
   if (first_var < 0 || n_vars < 1 || first_var + n_vars > 5)
     return fail(DG_ERR_INVALID_ARG, "dg_make_pairs: variable range outside 0..4");
   DG_CUDA(launch_make_pairs(lo, q_bar_n, q_nn_np1, q_bar_np1, dt, first_var, n_vars, X, Y, (cudaStream_t)stream));
+  return DG_OK;
+}
+
+int dg_profile_rk3(dg_ctx* c, double* q, double dt, int nsteps, double* ms_gradient, double* ms_flux,
+                   int* launches_gradient, int* launches_flux, double* flux_bytes, double* grad_bytes,
+                   void* stream) {
+  if (!c || !q) return fail(DG_ERR_INVALID_ARG, "dg_profile_rk3: NULL argument");
+  if (nsteps < 1 || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_profile_rk3: bad nsteps or dt");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nl = 3 * nsteps;
+  std::vector<cudaEvent_t> ev(4 * nl);
+  int created = 0;
+  cudaError_t e = cudaSuccess;
+  for (; created < 4 * nl && e == cudaSuccess; ++created) e = cudaEventCreate(&ev[created]);
+  double tg = 0.0, tf = 0.0, bg = 0.0, bf = 0.0;
+  if (e == cudaSuccess) {
+    for (int s = 0; s < nsteps && e == cudaSuccess; ++s)
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        const int i = 4 * (3 * s + k);
+        int src, mode;
+        stage_plan(c, k, &src, &mode);
+        double gb, fb;
+        stage_bytes(c, k, &gb, &fb);
+        bg += gb;
+        bf += fb;
+        cudaEventRecord(ev[i], st);
+        e = launch_gradient(c, q, src, st);
+        cudaEventRecord(ev[i + 1], st);
+        cudaEventRecord(ev[i + 2], st);
+        if (e == cudaSuccess) e = launch_flux(c, q, nullptr, Forcing{}, mode, kRkA[k], kRkB[k], dt, st);
+        cudaEventRecord(ev[i + 3], st);
+      }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (int l = 0; l < nl && e == cudaSuccess; ++l) {
+      float a = 0.f, b = 0.f;
+      cudaEventElapsedTime(&a, ev[4 * l], ev[4 * l + 1]);
+      cudaEventElapsedTime(&b, ev[4 * l + 2], ev[4 * l + 3]);
+      tg += a;
+      tf += b;
+    }
+  }
+  for (int i = 0; i < created; ++i) cudaEventDestroy(ev[i]);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_profile_rk3");
+  if (ms_gradient) *ms_gradient = tg;
+  if (ms_flux) *ms_flux = tf;
+  if (launches_gradient) *launches_gradient = nl;
+  if (launches_flux) *launches_flux = nl;
+  if (flux_bytes) *flux_bytes = bf / nl * (double)c->N;
+  if (grad_bytes) *grad_bytes = bg / nl * (double)c->N;
   return DG_OK;
 }
 

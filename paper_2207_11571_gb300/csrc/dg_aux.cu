@@ -4,6 +4,7 @@
 #include <cmath>
 
 #include "dg_aux.h"
+#include "dg_device.cuh"
 
 namespace dgnn {
 
@@ -206,4 +207,41 @@ cudaError_t launch_make_pairs(const dg_ctx* lo, const double* qb_n, const double
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- conversion self-check
+
+// Counts the inputs where the integer-pipe conversions differ from the hardware ones:
+// d2f_rn vs __double2float_rn (inputs in the FP32 normal range or zero), and the exact
+// widening f2d vs (double) of the FP32 result.
+__global__ void k_check_conversions(const double* __restrict__ x, long long n, unsigned long long* __restrict__ bad) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const double v = x[t];
+  const float a = d2f_rn(v), b = __double2float_rn(v);
+  const bool same = (__float_as_uint(a) == __float_as_uint(b)) || (isnan(a) && isnan(b));
+  const bool wide = (f2d(b) == (double)b) || isnan(b);
+  if (!same) atomicAdd(&bad[0], 1ull);
+  if (!wide) atomicAdd(&bad[1], 1ull);
+}
+
 }  // namespace dgnn
+
+extern "C" int dg_check_conversions(const double* x, int64_t n, int64_t* mismatches, void* stream) {
+  using namespace dgnn;
+  if (!x || n < 0 || !mismatches) return fail(DG_ERR_INVALID_ARG, "dg_check_conversions: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* bad = nullptr;
+  DG_CUDA(cudaMalloc(&bad, 2 * sizeof(unsigned long long)));
+  cudaError_t e = cudaMemsetAsync(bad, 0, 2 * sizeof(unsigned long long), st);
+  if (e == cudaSuccess && n > 0) {
+    k_check_conversions<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, n, bad);
+    e = cudaGetLastError();
+  }
+  unsigned long long h[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, bad, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(bad);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_check_conversions");
+  mismatches[0] = (int64_t)h[0];
+  mismatches[1] = (int64_t)h[1];
+  return DG_OK;
+}

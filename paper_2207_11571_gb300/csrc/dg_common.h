@@ -45,7 +45,12 @@ struct Geom {
   double D[kMaxN1 * kMaxN1];
 };
 
-// Physical constants of the operator.
+// Physical constants of the operator.  The operator works on the state relative to a
+// constant reference (rho_ref, E_ref): r = rho - rho_ref, e = rho e - E_ref, with
+// p' = p - p_ref and theta' = theta - p_ref / rho_ref.  Constant parts of the fluxes
+// have zero divergence and cancel in the interface terms, so the operator is unchanged;
+// in FP32 this keeps the Mach-0.1 background pressure (p0 ~ 71) out of the momentum
+// flux derivatives.  The FP64 operator uses zero references (the plain formulas).
 struct Phys {
   double gamma;
   double mu;         // 1 / Re
@@ -53,6 +58,9 @@ struct Phys {
   int les;           // Smagorinsky on/off
   double csd2;       // (Cs * delta)^2
   double lam_t;      // gamma / ((gamma-1) Prt): turbulent heat coefficient per unit mu_t
+  double rho_ref, E_ref, p_ref;  // reference state (zero in the FP64 operator)
+  double Hc;         // E_ref + p_ref: constant part of the total enthalpy flux density
+  double theta_ref;  // p_ref / rho_ref
 };
 
 // Optional forcing source added to the operator: s[e * stride + slot * n^3 + node]
@@ -78,7 +86,9 @@ struct dg_ctx {
   long long N = 0;
   int nel = 0;
   // workspace (device)
-  void* qf = nullptr;     // operator-precision copy of q, [5][N]
+  void* qf = nullptr;     // operator-precision stage state (reference-shifted), [5][N]
+  float* qn32 = nullptr;  // FP32 operator: reference-shifted FP32 image of q at the step start, [5][N]
+  float* dlt = nullptr;   // FP32 operator: RK increment accumulated within the step, [5][N]
   void* vis = nullptr;    // viscous stresses and heat flux, [9][N] operator precision
   void* g = nullptr;      // RK register [5][N] (double or float)
   double* rhs_tmp = nullptr;  // [5][N] FP64 operator value for diagnostics
@@ -92,9 +102,13 @@ struct dg_ctx {
 
 namespace dgnn {
 
-// Launchers of the operator kernels (dg_kernels_*.cu).  All return cudaError_t.
-cudaError_t launch_gradient(const dg_ctx* c, const double* q, cudaStream_t st);
-// mode 0: dqdt = R (+ s); mode 1: RK stage g = A g + dt R; q += B g
+// Launchers of the operator kernels.  All return cudaError_t.
+// Phase A.  src 0: stage state from q (FP64); src 1: from qn32 + dlt (FP32 operator,
+// RK stages 2 and 3).
+cudaError_t launch_gradient(const dg_ctx* c, const double* q, int src, cudaStream_t st);
+// Phase B.  mode 0: dqdt = R (+ s).  mode 1: FP64 RK stage, g = A g + dt R, q += B g.
+// modes 2, 3, 4: FP32 operator RK stages 1, 2, 3 on the FP32 increment; stage 3 adds
+// the increment to the FP64 state.
 cudaError_t launch_flux(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode,
                         double rkA, double rkB, double dt, cudaStream_t st);
 

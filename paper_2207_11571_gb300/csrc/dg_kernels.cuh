@@ -1,19 +1,25 @@
 // The two phases of one evaluation of the DGSEM operator p(q) (Sec. 2, Eq. 3):
 //
-//  phase A (k_gradient): BR1 lifted gradient of (v1, v2, v3, theta = p/rho)
+//  phase A (k_gradient): BR1 lifted gradient of (v1, v2, v3, theta)
 //     G_d = (2/h) [ D_d U + (U^ - U)|right / w_P - (U^ - U)|left / w_0 ],  U^ central,
 //     then the viscous stresses and heat flux of Appendix A (Eq. A.3), optionally with
-//     the Smagorinsky viscosity; writes them (9 values per node) and an operator-precision
-//     copy of q that phase B reads for the neighbours' interface states.
+//     the Smagorinsky viscosity.  Writes them (9 values per node) and the stage state s
+//     (reference-shifted, operator precision) that phase B and the neighbours read.
 //  phase B (k_flux): volume term -(2/h) sum_d D_d (f^a_d - f^nu_d), Roe + central-BR1
 //     interface fluxes and their lifting (strong form), optional forcing s (Eq. 4), then
-//     either writes dq/dt or applies one low-storage RK3 stage in FP64.
+//     writes dq/dt or applies one stage of the low-storage RK3.
 //
-// Layout: each CUDA block owns E consecutive elements, one thread per node; element
-// tiles (derivative matrix, per-node fields) are staged in shared memory and the 1D
-// derivative contractions read them there.  Neighbour interface values are gathered
-// straight from global memory (they are L2-resident: the neighbours are processed by
-// nearby blocks at the same time).
+// RK3 in the FP32 operator: the state q stays FP64 and is read and written once per
+// step.  Within a step the stage state is qn32 + dlt (FP32 image of q at the step start
+// plus the FP32 increment accumulated by the stages); stage 3 adds the increment to q
+// in FP64.  The Williamson register of stage 1 is recovered as g1 = dlt1 / B1, so only
+// stage 2 stores it.  In the FP64 operator every stage updates q in FP64 (the plain
+// 2N scheme).
+//
+// Each CUDA block owns E consecutive elements, one thread per node; element tiles (the
+// derivative matrix, per-node fields) are staged in shared memory, where the 1D
+// derivative contractions read them.  Neighbour interface values are gathered from
+// global memory (L2-resident: neighbours are processed by nearby blocks).
 #pragma once
 
 #include "dg_device.cuh"
@@ -31,18 +37,26 @@ __device__ __forceinline__ int neighbour_elem(int e, int K, int d, int shift) {
   return c[0] + K * (c[1] + K * c[2]);
 }
 
-template <typename T>
-__device__ __forceinline__ void gradient_vars(const T q[5], T gm1, T U[4]) {
-  const T ir = T(1) / q[0];
-  U[0] = q[1] * ir;
-  U[1] = q[2] * ir;
-  U[2] = q[3] * ir;
-  U[3] = pressure(q, gm1) * ir;
+// Stage state of node gi.  SRC 0: from the FP64 state q; SRC 1: qn32 + dlt (FP32).
+template <typename T, int SRC>
+__device__ __forceinline__ void stage_state(const double* __restrict__ q, const float* __restrict__ qn32,
+                                            const float* __restrict__ dlt, long long N, long long gi, const Phys& ph,
+                                            T s[5]) {
+  if (SRC == 0) {
+    double qd[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) qd[v] = q[v * N + gi];
+    shift_state<T>(qd, ph, s);
+  } else {
+#pragma unroll
+    for (int v = 0; v < 5; ++v) s[v] = T(qn32[v * N + gi] + dlt[v * N + gi]);
+  }
 }
 
-template <int P, typename T>
+template <int P, typename T, int SRC>
 __global__ void __launch_bounds__(max_threads_for(P))
-k_gradient(const double* __restrict__ q, T* __restrict__ qf, T* __restrict__ vis, Geom geom, Phys ph) {
+k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, const float* __restrict__ dlt,
+           T* __restrict__ qf, float* __restrict__ qn32_out, T* __restrict__ vis, Geom geom, Phys ph) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sD = reinterpret_cast<T*>(smem_raw);
@@ -57,15 +71,20 @@ k_gradient(const double* __restrict__ q, T* __restrict__ qf, T* __restrict__ vis
   const bool active = (le < E) && (e < geom.nel);
   const long long N = geom.N;
   const long long gi = (long long)e * np + node;
-  const T gm1 = T(ph.gamma - 1.0);
+  const T gm1 = T(ph.gamma - 1.0), rho_ref = T(ph.rho_ref), th_ref = T(ph.theta_ref);
 
-  T qv[5], U[4];
+  T s[5], U[4];
+  Prim<T> w;
   if (active) {
+    stage_state<T, SRC>(q, qn32_in, dlt, N, gi, ph, s);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) qv[v] = T(q[v * N + gi]);
+    for (int v = 0; v < 5; ++v) qf[v * N + gi] = s[v];
+    if (SRC == 0 && qn32_out != nullptr) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) qf[v * N + gi] = qv[v];
-    gradient_vars(qv, gm1, U);
+      for (int v = 0; v < 5; ++v) qn32_out[v * N + gi] = float(s[v]);
+    }
+    w = primitives(s, rho_ref, gm1);
+    gradient_vars(s, w, th_ref, U);
 #pragma unroll
     for (int a = 0; a < 4; ++a) sU[a * tileN + le * np + node] = U[a];
   }
@@ -91,13 +110,12 @@ k_gradient(const double* __restrict__ q, T* __restrict__ qf, T* __restrict__ vis
     // interface lifting with the central U^ = (U + U_nb) / 2
     const bool right = (idx[d] == P), left = (idx[d] == 0);
     if (right || left) {
-      const int shift = right ? 1 : -1;
-      const int enb = neighbour_elem(e, geom.K, d, shift);
+      const int enb = neighbour_elem(e, geom.K, d, right ? 1 : -1);
       const long long gnb = (long long)enb * np + node + (right ? -P : P) * stride[d];
-      T qn[5], Un[4];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) qn[v] = T(q[v * N + gnb]);
-      gradient_vars(qn, gm1, Un);
+      T sn[5], Un[4];
+      stage_state<T, SRC>(q, qn32_in, dlt, N, gnb, ph, sn);
+      const Prim<T> wn = primitives(sn, rho_ref, gm1);
+      gradient_vars(sn, wn, th_ref, Un);
       const T sgn = right ? lift : -lift;
 #pragma unroll
       for (int a = 0; a < 4; ++a) G[d][a] += sgn * (Un[a] - U[a]);
@@ -105,7 +123,7 @@ k_gradient(const double* __restrict__ q, T* __restrict__ qf, T* __restrict__ vis
   }
 
   T mu, lam;
-  transport(ph, qv[0], G, &mu, &lam);
+  transport(ph, w.rho, G, &mu, &lam);
   const T div = G[0][0] + G[1][1] + G[2][2];
   const T t23 = T(2.0 / 3.0) * mu * div;
   // G[d][a] = d u_a / d x_d, tau_ab = mu (du_a/dx_b + du_b/dx_a) - 2/3 mu div delta_ab
@@ -123,12 +141,18 @@ k_gradient(const double* __restrict__ q, T* __restrict__ qf, T* __restrict__ vis
   for (int c = 0; c < 9; ++c) vis[c * N + gi] = out[c];
 }
 
-// MODE 0: dqdt = R.  MODE 1: RK stage g = A g + dt R, q += B g (FP64 state, register GT).
+// Per-launch RK data of phase B.
+struct RkArgs {
+  double A, B, dt;   // Williamson coefficients of the stage and the step size
+  double invB1;      // 1 / B of stage 1 (the FP32 increment scheme recovers g1 = dlt1 / B1)
+};
+
+// MODE 0: dqdt = R.  MODE 1: FP64 RK stage (g = A g + dt R; q += B g, register GT).
+// MODES 2, 3, 4: FP32 increment scheme, stages 1, 2, 3.
 template <int P, typename T, int MODE, typename GT>
 __global__ void __launch_bounds__(max_threads_for(P))
-k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ vis,
-       double* __restrict__ dqdt, GT* __restrict__ greg, Forcing fc, Geom geom, Phys ph,
-       double rkA, double rkB, double dt) {
+k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ vis, double* __restrict__ dqdt,
+       GT* __restrict__ greg, float* __restrict__ dlt, Forcing fc, Geom geom, Phys ph, RkArgs rk) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sD = reinterpret_cast<T*>(smem_raw);
@@ -143,23 +167,16 @@ k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ v
   const bool active = (le < E) && (e < geom.nel);
   const long long N = geom.N;
   const long long gi = (long long)e * np + node;
-  const T gm1 = T(ph.gamma - 1.0);
+  const T gm1 = T(ph.gamma - 1.0), rho_ref = T(ph.rho_ref), Hc = T(ph.Hc);
 
-  double qd[5];
-  T qv[5], vs[9], vel[3], p = T(0);
+  T s[5], vs[9];
+  Prim<T> w;
   if (active) {
 #pragma unroll
-    for (int v = 0; v < 5; ++v) {
-      qd[v] = q[v * N + gi];
-      qv[v] = T(qd[v]);
-    }
+    for (int v = 0; v < 5; ++v) s[v] = qf[v * N + gi];
 #pragma unroll
     for (int c = 0; c < 9; ++c) vs[c] = vis[c * N + gi];
-    const T ir = T(1) / qv[0];
-    vel[0] = qv[1] * ir;
-    vel[1] = qv[2] * ir;
-    vel[2] = qv[3] * ir;
-    p = pressure(qv, gm1);
+    w = primitives(s, rho_ref, gm1);
   }
   const int idx[3] = {node % n, (node / n) % n, node / n2};
   const int stride[3] = {1, n, n2};
@@ -171,8 +188,8 @@ k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ v
   for (int d = 0; d < 3; ++d) {
     if (active) {
       T F[5], fv[5];
-      euler_flux(qv, p, d, F);
-      viscous_flux(vs, vel, d, fv);
+      euler_flux(s, w, Hc, d, F);
+      viscous_flux(vs, w.v, d, fv);
 #pragma unroll
       for (int c = 0; c < 5; ++c) sF[c * tileN + le * np + node] = F[c] - fv[c];
     }
@@ -200,21 +217,18 @@ k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ v
     if (!(right || left)) continue;
     const int enb = neighbour_elem(e, geom.K, d, right ? 1 : -1);
     const long long gnb = (long long)enb * np + node + (right ? -P : P) * stride[d];
-    T qn[5], vn[9], veln[3];
+    T sn[5], vn[9];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) qn[v] = qf[v * N + gnb];
+    for (int v = 0; v < 5; ++v) sn[v] = qf[v * N + gnb];
 #pragma unroll
     for (int c = 0; c < 9; ++c) vn[c] = vis[c * N + gnb];
-    const T irn = T(1) / qn[0];
-    veln[0] = qn[1] * irn;
-    veln[1] = qn[2] * irn;
-    veln[2] = qn[3] * irn;
+    const Prim<T> wn = primitives(sn, rho_ref, gm1);
     T Fs[5], fvo[5], fvn[5], Fo[5];
-    if (right) roe_flux(qv, qn, d, gm1, Fs);
-    else roe_flux(qn, qv, d, gm1, Fs);
-    viscous_flux(vs, vel, d, fvo);
-    viscous_flux(vn, veln, d, fvn);
-    euler_flux(qv, p, d, Fo);
+    if (right) roe_flux(s, w, sn, wn, d, gm1, Hc, Fs);
+    else roe_flux(sn, wn, s, w, d, gm1, Hc, Fs);
+    viscous_flux(vs, w.v, d, fvo);
+    viscous_flux(vn, wn.v, d, fvn);
+    euler_flux(s, w, Hc, d, Fo);
     const T sgn = right ? -lift : lift;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
@@ -235,14 +249,34 @@ k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ v
   if (MODE == 0) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) dqdt[c * N + gi] = double(R[c]);
-  } else {
+  } else if (MODE == 1) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-      double gnew = dt * double(R[c]);
-      if (rkA != 0.0) gnew = fma(rkA, double(greg[c * N + gi]), gnew);
+      double gnew = rk.dt * double(R[c]);
+      if (rk.A != 0.0) gnew = fma(rk.A, double(greg[c * N + gi]), gnew);
       const GT gst = GT(gnew);
       greg[c * N + gi] = gst;
-      q[c * N + gi] = fma(rkB, double(gst), qd[c]);
+      q[c * N + gi] = fma(rk.B, double(gst), q[c * N + gi]);
+    }
+  } else {
+    // FP32 increment scheme
+    const float dt = float(rk.dt), A = float(rk.A), B = float(rk.B);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const long long o = c * N + gi;
+      const float r = float(R[c]);
+      if (MODE == 2) {
+        dlt[o] = B * (dt * r);                       // g1 = dt R1; dlt1 = B1 g1
+      } else if (MODE == 3) {
+        const float d1 = dlt[o];
+        const float g2 = A * (d1 * float(rk.invB1)) + dt * r;
+        greg[o] = GT(g2);
+        dlt[o] = d1 + B * g2;
+      } else {
+        const float g3 = A * float(greg[o]) + dt * r;
+        const float d3 = dlt[o] + B * g3;
+        q[o] = q[o] + f2d(d3);                     // once per step, in FP64
+      }
     }
   }
 }

@@ -2,9 +2,11 @@
 #include "dg_launch.cuh"
 
 namespace dgnn {
-cudaError_t gradient_f64(const dg_ctx* c, const double* q, cudaStream_t st) { return gradient_t<double>(c, q, st); }
-cudaError_t flux_f64(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
-                     double dt, cudaStream_t st) {
-  return flux_t<double>(c, q, dqdt, f, mode, A, B, dt, st);
+cudaError_t gradient_f64(const dg_ctx* c, const double* q, int src, cudaStream_t st) {
+  return gradient_t<double>(c, q, src, st);
+}
+cudaError_t flux_f64(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, const RkArgs& rk,
+                     cudaStream_t st) {
+  return flux_t<double>(c, q, dqdt, f, mode, rk, st);
 }
 }  // namespace dgnn

@@ -12,75 +12,88 @@ inline int block_threads(int P, int E) {
   return ((E * np + 31) / 32) * 32;
 }
 
-template <int P, typename T>
+template <typename K>
+cudaError_t set_smem(K kern, size_t smem) {
+  if (smem > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaSuccess;
+}
+
+template <int P, typename T, int SRC>
 cudaError_t gradient_p(const dg_ctx* c, const double* q, cudaStream_t st) {
   constexpr int n = P + 1, np = n * n * n;
   const int E = c->geom.E;
   const size_t smem = sizeof(T) * (n * n + 4 * E * np);
-  auto kern = k_gradient<P, T>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  auto kern = k_gradient<P, T, SRC>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
   const int grid = (c->nel + E - 1) / E;
-  kern<<<grid, block_threads(P, E), smem, st>>>(q, static_cast<T*>(c->qf), static_cast<T*>(c->vis), c->geom, c->phys);
+  kern<<<grid, block_threads(P, E), smem, st>>>(q, c->qn32, c->dlt, static_cast<T*>(c->qf),
+                                                SRC == 0 ? c->qn32 : nullptr, static_cast<T*>(c->vis), c->geom,
+                                                c->phys);
   return cudaGetLastError();
 }
 
 template <int P, typename T, int MODE, typename GT>
-cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, double A, double B,
-                   double dt, cudaStream_t st) {
+cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, const RkArgs& rk, cudaStream_t st) {
   constexpr int n = P + 1, np = n * n * n;
   const int E = c->geom.E;
   const size_t smem = sizeof(T) * (n * n + 5 * E * np);
   auto kern = k_flux<P, T, MODE, GT>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
   const int grid = (c->nel + E - 1) / E;
-  kern<<<grid, block_threads(P, E), smem, st>>>(q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis),
-                                                dqdt, static_cast<GT*>(c->g), f, c->geom, c->phys, A, B, dt);
+  kern<<<grid, block_threads(P, E), smem, st>>>(q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt,
+                                                static_cast<GT*>(c->g), c->dlt, f, c->geom, c->phys, rk);
   return cudaGetLastError();
 }
 
+// FP64 operator: modes 0 (dq/dt) and 1 (FP64 RK stage).  FP32 operator: modes 0, 2, 3, 4.
 template <int P, typename T>
 cudaError_t flux_dispatch_mode(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode,
-                               double A, double B, double dt, cudaStream_t st) {
-  if (mode == 0) return flux_p<P, T, 0, double>(c, q, dqdt, f, A, B, dt, st);
-  if (c->opts.rk_register_fp32) return flux_p<P, T, 1, float>(c, q, dqdt, f, A, B, dt, st);
-  return flux_p<P, T, 1, double>(c, q, dqdt, f, A, B, dt, st);
-}
-
-template <typename T>
-cudaError_t gradient_t(const dg_ctx* c, const double* q, cudaStream_t st) {
-  switch (c->P) {
-    case 1: return gradient_p<1, T>(c, q, st);
-    case 2: return gradient_p<2, T>(c, q, st);
-    case 3: return gradient_p<3, T>(c, q, st);
-    case 4: return gradient_p<4, T>(c, q, st);
-    case 5: return gradient_p<5, T>(c, q, st);
-    case 6: return gradient_p<6, T>(c, q, st);
-    case 7: return gradient_p<7, T>(c, q, st);
-    case 8: return gradient_p<8, T>(c, q, st);
+                               const RkArgs& rk, cudaStream_t st) {
+  using GT = T;  // RK register in the operator precision
+  switch (mode) {
+    case 0: return flux_p<P, T, 0, GT>(c, q, dqdt, f, rk, st);
+    case 1: return flux_p<P, T, 1, GT>(c, q, dqdt, f, rk, st);
+    case 2: return flux_p<P, T, 2, GT>(c, q, dqdt, f, rk, st);
+    case 3: return flux_p<P, T, 3, GT>(c, q, dqdt, f, rk, st);
+    case 4: return flux_p<P, T, 4, GT>(c, q, dqdt, f, rk, st);
   }
   return cudaErrorInvalidValue;
 }
 
-template <typename T>
-cudaError_t flux_t(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A,
-                   double B, double dt, cudaStream_t st) {
-  switch (c->P) {
-    case 1: return flux_dispatch_mode<1, T>(c, q, dqdt, f, mode, A, B, dt, st);
-    case 2: return flux_dispatch_mode<2, T>(c, q, dqdt, f, mode, A, B, dt, st);
-    case 3: return flux_dispatch_mode<3, T>(c, q, dqdt, f, mode, A, B, dt, st);
-    case 4: return flux_dispatch_mode<4, T>(c, q, dqdt, f, mode, A, B, dt, st);
-    case 5: return flux_dispatch_mode<5, T>(c, q, dqdt, f, mode, A, B, dt, st);
-    case 6: return flux_dispatch_mode<6, T>(c, q, dqdt, f, mode, A, B, dt, st);
-    case 7: return flux_dispatch_mode<7, T>(c, q, dqdt, f, mode, A, B, dt, st);
-    case 8: return flux_dispatch_mode<8, T>(c, q, dqdt, f, mode, A, B, dt, st);
-  }
+template <int P, typename T>
+cudaError_t gradient_dispatch_src(const dg_ctx* c, const double* q, int src, cudaStream_t st) {
+  if (src == 0) return gradient_p<P, T, 0>(c, q, st);
+  return gradient_p<P, T, 1>(c, q, st);
+}
+
+#define DG_FOR_EACH_P(CALL)        \
+  switch (c->P) {                  \
+    case 1: return CALL(1);        \
+    case 2: return CALL(2);        \
+    case 3: return CALL(3);        \
+    case 4: return CALL(4);        \
+    case 5: return CALL(5);        \
+    case 6: return CALL(6);        \
+    case 7: return CALL(7);        \
+    case 8: return CALL(8);        \
+  }                                \
   return cudaErrorInvalidValue;
+
+template <typename T>
+cudaError_t gradient_t(const dg_ctx* c, const double* q, int src, cudaStream_t st) {
+#define DG_G(PP) gradient_dispatch_src<PP, T>(c, q, src, st)
+  DG_FOR_EACH_P(DG_G)
+#undef DG_G
+}
+
+template <typename T>
+cudaError_t flux_t(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, const RkArgs& rk,
+                   cudaStream_t st) {
+#define DG_F(PP) flux_dispatch_mode<PP, T>(c, q, dqdt, f, mode, rk, st)
+  DG_FOR_EACH_P(DG_F)
+#undef DG_F
 }
 
 }  // namespace dgnn

@@ -1,8 +1,781 @@
-// Forcing network (Sec. 2.2): placeholder until the tcgen05 network lands.
+// Corrective-forcing network (Sec. 2.2, Fig. 2): model state, CUDA-core kernels around
+// the tensor-core GEMMs (input scaling, loss, gradient preparation, transposes, Adam)
+// and the C ABI of include/dgnn_nn.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dgnn_nn.h"
+#include "dg_common.h"
 #include "nn_bridge.h"
+#include "nn_gemm.h"
+
+using bf16 = __nv_bfloat16;
+
+struct nn_model {
+  nn_desc d{};
+  int L = 0;                    // dense layers = n_hidden + 1
+  int dims[10] = {};            // dims[0] = n_in, dims[1..n_hidden] = width, dims[L] = n_out
+  int pad[10] = {};             // round_up(dims[l], 64): leading dimension of bf16 rows
+  int bpad = 0;                 // round_up(max_batch, 64)
+  float* W[9] = {};             // FP32 master [out][in]
+  float* b[9] = {};
+  bf16* Wb[9] = {};             // [out][pad(in)]
+  bf16* Wt[9] = {};             // [in][pad(out)]
+  float *mW[9] = {}, *vW[9] = {}, *mb[9] = {}, *vb[9] = {};
+  float *gW[9] = {}, *gb[9] = {};
+  float *mean_in = nullptr, *std_in = nullptr, *mean_out = nullptr, *std_out = nullptr;
+  int adam_t = 0;
+  bf16* act[10] = {};           // act[l]: input of layer l, [max_batch][pad(l)]
+  bf16* actT[10] = {};          // [dims[l]][bpad]
+  float* y = nullptr;           // [max_batch][n_out], scaled output
+  float* dy = nullptr;          // [max_batch][max dim] gradient of the current layer output
+  float* dx = nullptr;          // [max_batch][max dim] gradient of the current layer input
+  bf16* dyb = nullptr;          // [max_batch][pad(max dim)]
+  bf16* dyT = nullptr;          // [max dim][bpad]
+  double* loss_part = nullptr;  // reduction partials
+  double* loss_dev = nullptr;
+  double* loss_host = nullptr;  // pinned
+  int* err = nullptr;           // device error flag of the tensor-core kernels
+  int maxdim = 0;
+};
 
 namespace dgnn {
-int nn_forcing_on_state(const nn_model*, const dg_ctx*, const double*, float*, int*, int*, cudaStream_t) {
-  return fail(DG_ERR_UNSUPPORTED, "forcing network not built yet");
+
+namespace {
+
+constexpr int kLossBlocks = 256;
+constexpr int kLossThreads = 256;
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ------------------------------------------------------------------------------- kernels
+
+// act0[r][f] = bf16((X[row(r)][f] - mean[f]) / std[f]) for f < n_in, 0 for the padding.
+__global__ void k_prep_features(const float* __restrict__ X, const int64_t* __restrict__ idx, int rows, int n_in,
+                                int ld, const float* __restrict__ mean, const float* __restrict__ sd,
+                                bf16* __restrict__ out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)rows * ld) return;
+  const int r = (int)(t / ld), f = (int)(t - (long long)r * ld);
+  float v = 0.f;
+  if (f < n_in) {
+    const long long src = idx ? idx[r] : r;
+    v = (X[src * n_in + f] - mean[f]) / sd[f];
+  }
+  out[t] = __float2bfloat16_rn(v);
 }
+
+// act0[e][slot * np + node] from the FP64 state q[var][elem][node] of elements e0 .. e0 + rows.
+__global__ void k_prep_state(const double* __restrict__ q, long long N, int np, int first_var, int n_vars, int e0,
+                             int rows, int ld, const float* __restrict__ mean, const float* __restrict__ sd,
+                             bf16* __restrict__ out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)rows * ld) return;
+  const int r = (int)(t / ld), f = (int)(t - (long long)r * ld);
+  float v = 0.f;
+  if (f < n_vars * np) {
+    const int slot = f / np, node = f - slot * np;
+    const double x = q[(long long)(first_var + slot) * N + (long long)(e0 + r) * np + node];
+    v = ((float)x - mean[f]) / sd[f];
+  }
+  out[t] = __float2bfloat16_rn(v);
+}
+
+// Same from the FP32 reference-shifted stage state qf[var][elem][node] of an FP32 context.
+__global__ void k_prep_state_f32(const float* __restrict__ qf, long long N, int np, int first_var, int n_vars, int e0,
+                                 int rows, int ld, float rho_ref, float E_ref, const float* __restrict__ mean,
+                                 const float* __restrict__ sd, bf16* __restrict__ out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)rows * ld) return;
+  const int r = (int)(t / ld), f = (int)(t - (long long)r * ld);
+  float v = 0.f;
+  if (f < n_vars * np) {
+    const int slot = f / np, node = f - slot * np;
+    const int var = first_var + slot;
+    float x = qf[(long long)var * N + (long long)(e0 + r) * np + node];
+    if (var == 0) x += rho_ref;
+    if (var == 4) x += E_ref;
+    v = (x - mean[f]) / sd[f];
+  }
+  out[t] = __float2bfloat16_rn(v);
+}
+
+// MSE against scaled targets: dy = 2 (y - t_s) / (rows n), partial sums of (y - t_s)^2.
+__global__ void k_loss(const float* __restrict__ y, const float* __restrict__ Y, const int64_t* __restrict__ idx,
+                       int rows, int n, const float* __restrict__ mean, const float* __restrict__ sd,
+                       float* __restrict__ dy, double* __restrict__ partial) {
+  __shared__ double sh[kLossThreads];
+  double acc = 0.0;
+  const long long total = (long long)rows * n;
+  const float g = 2.f / (float)total;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / n), f = (int)(t - (long long)r * n);
+    const long long src = idx ? idx[r] : r;
+    const float ts = (Y[src * n + f] - mean[f]) / sd[f];
+    const float diff = y[t] - ts;
+    dy[t] = g * diff;
+    acc += (double)diff * (double)diff;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int n, double scale, double* __restrict__ out) {
+  __shared__ double sh[kLossThreads];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0] * scale;
+}
+
+// From the FP32 gradient g[rows][n]: bf16 copy [rows][ldb] (zero padded), bf16 transpose
+// [n][ldt] (ldt = padded rows, zero padded), column sums db[n] in a fixed order.
+// One block of 32 x 8 threads per 32-column strip; rows walked in 32-row tiles.
+__global__ void k_grad_prep(const float* __restrict__ g, int rows, int n, int ldb, int ldt, bf16* __restrict__ gb,
+                            bf16* __restrict__ gT, float* __restrict__ db) {
+  __shared__ float tile[32][33];
+  __shared__ float colsum[8][32];
+  const int c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  float cs = 0.f;
+  const int rows_pad = ldt;
+  for (int r0 = 0; r0 < rows_pad; r0 += 32) {
+    for (int k = ty; k < 32; k += 8) {
+      const int r = r0 + k, c = c0 + tx;
+      float v = (r < rows && c < n) ? g[(long long)r * n + c] : 0.f;
+      tile[k][tx] = v;
+      if (r < rows && c < ldb) gb[(long long)r * ldb + c] = __float2bfloat16_rn(v);
+      if (r < rows && c < n) cs += v;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+      const int c = c0 + k, r = r0 + tx;
+      if (c < n && r < ldt) gT[(long long)c * ldt + r] = __float2bfloat16_rn(tile[tx][k]);
+    }
+    __syncthreads();
+  }
+  colsum[ty][tx] = cs;
+  __syncthreads();
+  if (ty == 0 && c0 + tx < n) {
+    float s = 0.f;
+    for (int k = 0; k < 8; ++k) s += colsum[k][tx];
+    db[c0 + tx] = s;
+  }
+}
+
+// act[rows][ld] (bf16) -> actT[n][ldt] for the first n columns, rows padded with zeros.
+__global__ void k_transpose_bf16(const bf16* __restrict__ a, int rows, int n, int ld, int ldt, bf16* __restrict__ aT) {
+  __shared__ bf16 tile[32][34];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int k = ty; k < 32; k += 8) {
+    const int r = r0 + k, c = c0 + tx;
+    tile[k][tx] = (r < rows && c < n) ? a[(long long)r * ld + c] : __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int c = c0 + k, r = r0 + tx;
+    if (c < n && r < ldt) aT[(long long)c * ldt + r] = tile[tx][k];
+  }
+}
+
+// Adam on one parameter tensor [out][in] (in = 1 for biases), refreshing the bf16 copies
+// Wb[out][ldb] and Wt[in][ldt] when given.
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       long long count, int in, float lr, float b1, float b2, float eps, float bc1, float bc2,
+                       bf16* __restrict__ Wb, int ldb, bf16* __restrict__ Wt, int ldt) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const float gi = g[t];
+  const float mi = b1 * m[t] + (1.f - b1) * gi;
+  const float vi = b2 * v[t] + (1.f - b2) * gi * gi;
+  m[t] = mi;
+  v[t] = vi;
+  const float mh = mi / bc1, vh = vi / bc2;
+  const float w = p[t] - lr * mh / (sqrtf(vh) + eps);
+  p[t] = w;
+  if (Wb) {
+    const int o = (int)(t / in), i = (int)(t - (long long)o * in);
+    const bf16 wb = __float2bfloat16_rn(w);
+    Wb[(long long)o * ldb + i] = wb;
+    Wt[(long long)i * ldt + o] = wb;
+  }
+}
+
+// bf16 copies of an FP32 weight [out][in].
+__global__ void k_refresh_bf16(const float* __restrict__ W, long long count, int in, bf16* __restrict__ Wb, int ldb,
+                               bf16* __restrict__ Wt, int ldt) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const int o = (int)(t / in), i = (int)(t - (long long)o * in);
+  const bf16 wb = __float2bfloat16_rn(W[t]);
+  Wb[(long long)o * ldb + i] = wb;
+  Wt[(long long)i * ldt + o] = wb;
+}
+
+// Per-feature sums of x and x^2 over rows (FP64), blocks stride over rows.
+__global__ void k_moments(const float* __restrict__ X, long long rows, int n, double* __restrict__ s1,
+                          double* __restrict__ s2) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  double a = 0.0, b = 0.0;
+  for (long long r = blockIdx.y; r < rows; r += gridDim.y) {
+    const double x = X[r * n + f];
+    a += x;
+    b += x * x;
+  }
+  s1[(long long)blockIdx.y * n + f] = a;
+  s2[(long long)blockIdx.y * n + f] = b;
+}
+
+// ------------------------------------------------------------------------------- helpers
+
+int check_err(const nn_model* m, cudaStream_t st) {
+  int h = 0;
+  DG_CUDA(cudaMemcpyAsync(&h, m->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    cudaMemsetAsync(m->err, 0, sizeof(int), st);
+    return fail(DG_ERR_TIMEOUT, "tensor-core GEMM: a bounded wait expired (code " + std::to_string(h) + ")");
+  }
+  return DG_OK;
+}
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Forward through all layers for `rows` rows whose scaled inputs are in act[0].
+// last: if S != null, unscaled forcing into S (ld n_out); else scaled output into m->y.
+int forward_layers(const nn_model* m, int rows, float* S, cudaStream_t st) {
+  for (int l = 0; l < m->L; ++l) {
+    GemmEpilogue ep;
+    ep.bias = m->b[l];
+    if (l < m->L - 1) {
+      ep.kind = kGemmBiasReluBf16;
+      ep.out = m->act[l + 1];
+      ep.ldo = m->pad[l + 1];
+    } else if (S) {
+      ep.kind = kGemmAffineF32;
+      ep.scale = m->std_out;
+      ep.shift = m->mean_out;
+      ep.out = S;
+      ep.ldo = m->dims[m->L];
+    } else {
+      ep.kind = kGemmF32;
+      ep.out = m->y;
+      ep.ldo = m->dims[m->L];
+    }
+    int rc = gemm_bf16(m->act[l], m->pad[l], m->Wb[l], m->pad[l], rows, m->dims[l + 1], m->dims[l], ep, m->err, st);
+    if (rc) return rc;
+  }
+  return DG_OK;
+}
+
+void free_model(nn_model* m) {
+  if (!m) return;
+  for (int l = 0; l < 9; ++l) {
+    cudaFree(m->W[l]); cudaFree(m->b[l]); cudaFree(m->Wb[l]); cudaFree(m->Wt[l]);
+    cudaFree(m->mW[l]); cudaFree(m->vW[l]); cudaFree(m->mb[l]); cudaFree(m->vb[l]);
+    cudaFree(m->gW[l]); cudaFree(m->gb[l]);
+  }
+  for (int l = 0; l < 10; ++l) { cudaFree(m->act[l]); cudaFree(m->actT[l]); }
+  cudaFree(m->mean_in); cudaFree(m->std_in); cudaFree(m->mean_out); cudaFree(m->std_out);
+  cudaFree(m->y); cudaFree(m->dy); cudaFree(m->dx); cudaFree(m->dyb); cudaFree(m->dyT);
+  cudaFree(m->loss_part); cudaFree(m->loss_dev); cudaFree(m->err);
+  if (m->loss_host) cudaFreeHost(m->loss_host);
+  delete m;
+}
+
+int validate_desc(const nn_desc* d) {
+  if (!d) return fail(DG_ERR_INVALID_ARG, "nn_create: NULL desc");
+  if (d->n_in < 1 || d->n_in > 4096 || d->n_out < 1 || d->n_out > 4096)
+    return fail(DG_ERR_INVALID_ARG, "nn_create: n_in and n_out must be in [1, 4096]");
+  if (d->width < 8 || d->width > 1024 || d->width % 8)
+    return fail(DG_ERR_INVALID_ARG, "nn_create: width must be a multiple of 8 in [8, 1024]");
+  if (d->n_hidden < 1 || d->n_hidden > 8) return fail(DG_ERR_INVALID_ARG, "nn_create: n_hidden must be in [1, 8]");
+  if (d->max_batch < 1 || d->max_batch > (1 << 22)) return fail(DG_ERR_INVALID_ARG, "nn_create: bad max_batch");
+  if (!((d->first_var == 0 && d->n_vars == 5) || (d->first_var == 1 && d->n_vars == 3)))
+    return fail(DG_ERR_INVALID_ARG, "nn_create: (first_var, n_vars) must be (0, 5) or (1, 3)");
+  return DG_OK;
+}
+
+int alloc_model(const nn_desc* d, nn_model** out) {
+  int rc = validate_desc(d);
+  if (rc) return rc;
+  nn_model* m = new nn_model();
+  m->d = *d;
+  m->L = d->n_hidden + 1;
+  m->dims[0] = d->n_in;
+  for (int l = 1; l <= d->n_hidden; ++l) m->dims[l] = d->width;
+  m->dims[m->L] = d->n_out;
+  for (int l = 0; l <= m->L; ++l) {
+    m->pad[l] = round_up(m->dims[l], 64);
+    m->maxdim = std::max(m->maxdim, m->dims[l]);
+  }
+  m->bpad = round_up(d->max_batch, 64);
+  const long long B = d->max_batch;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) e = cudaMemset(*p, 0, bytes);
+  };
+  for (int l = 0; l < m->L; ++l) {
+    const size_t in = m->dims[l], o = m->dims[l + 1];
+    A((void**)&m->W[l], in * o * 4); A((void**)&m->b[l], o * 4);
+    A((void**)&m->Wb[l], o * m->pad[l] * 2); A((void**)&m->Wt[l], in * m->pad[l + 1] * 2);
+    A((void**)&m->mW[l], in * o * 4); A((void**)&m->vW[l], in * o * 4);
+    A((void**)&m->mb[l], o * 4); A((void**)&m->vb[l], o * 4);
+    A((void**)&m->gW[l], in * o * 4); A((void**)&m->gb[l], o * 4);
+  }
+  for (int l = 0; l < m->L; ++l) {
+    A((void**)&m->act[l], B * m->pad[l] * 2);
+    A((void**)&m->actT[l], (size_t)m->dims[l] * m->bpad * 2);
+  }
+  A((void**)&m->mean_in, d->n_in * 4); A((void**)&m->std_in, d->n_in * 4);
+  A((void**)&m->mean_out, d->n_out * 4); A((void**)&m->std_out, d->n_out * 4);
+  A((void**)&m->y, B * d->n_out * 4);
+  A((void**)&m->dy, B * m->maxdim * 4);
+  A((void**)&m->dx, B * m->maxdim * 4);
+  A((void**)&m->dyb, B * round_up(m->maxdim, 64) * 2);
+  A((void**)&m->dyT, (size_t)m->maxdim * m->bpad * 2);
+  A((void**)&m->loss_part, kLossBlocks * 8);
+  A((void**)&m->loss_dev, 8);
+  A((void**)&m->err, 4);
+  if (e == cudaSuccess) e = cudaMallocHost(&m->loss_host, 8);
+  if (e != cudaSuccess) {
+    free_model(m);
+    return cuda_fail(e, "nn_create: allocation");
+  }
+  std::vector<float> ones(std::max(d->n_in, d->n_out), 1.f);
+  cudaMemcpy(m->std_in, ones.data(), d->n_in * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(m->std_out, ones.data(), d->n_out * 4, cudaMemcpyHostToDevice);
+  *out = m;
+  return DG_OK;
+}
+
+int refresh_bf16(nn_model* m, int l, cudaStream_t st) {
+  const long long cnt = (long long)m->dims[l] * m->dims[l + 1];
+  k_refresh_bf16<<<blocks_for(cnt, 256), 256, 0, st>>>(m->W[l], cnt, m->dims[l], m->Wb[l], m->pad[l], m->Wt[l],
+                                                        m->pad[l + 1]);
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+}  // namespace
+
+int nn_forcing_on_state(const nn_model* m, const dg_ctx* c, const double* q, float* s, int* first_var, int* n_vars,
+                        cudaStream_t st) {
+  if (!m || !c || !q || !s) return fail(DG_ERR_INVALID_ARG, "forcing: NULL argument");
+  const int feat = m->d.n_vars * c->np;
+  if (m->d.n_in != feat || m->d.n_out != feat)
+    return fail(DG_ERR_INVALID_ARG, "forcing: network features do not match n_vars (P+1)^3 of the context");
+  for (int e0 = 0; e0 < c->nel; e0 += m->d.max_batch) {
+    const int rows = std::min(m->d.max_batch, c->nel - e0);
+    const long long tot = (long long)rows * m->pad[0];
+    if (c->opts.precision == DG_PREC_FP32) {
+      // the stage state of the FP32 operator is the reference-shifted copy written by phase A
+      k_prep_state_f32<<<blocks_for(tot, 256), 256, 0, st>>>(static_cast<const float*>(c->qf), c->N, c->np,
+                                                             m->d.first_var, m->d.n_vars, e0, rows, m->pad[0],
+                                                             (float)c->phys.rho_ref, (float)c->phys.E_ref,
+                                                             m->mean_in, m->std_in, m->act[0]);
+    } else {
+      k_prep_state<<<blocks_for(tot, 256), 256, 0, st>>>(q, c->N, c->np, m->d.first_var, m->d.n_vars, e0, rows,
+                                                         m->pad[0], m->mean_in, m->std_in, m->act[0]);
+    }
+    DG_CUDA(cudaGetLastError());
+    int rc = forward_layers(m, rows, s + (long long)e0 * feat, st);
+    if (rc) return rc;
+  }
+  if (first_var) *first_var = m->d.first_var;
+  if (n_vars) *n_vars = m->d.n_vars;
+  return DG_OK;
+}
+
 }  // namespace dgnn
+
+using namespace dgnn;
+
+extern "C" {
+
+int nn_create(const nn_desc* desc, const float* init_uniform, nn_model** out) {
+  if (!out) return fail(DG_ERR_INVALID_ARG, "nn_create: out is NULL");
+  *out = nullptr;
+  nn_model* m = nullptr;
+  int rc = alloc_model(desc, &m);
+  if (rc) return rc;
+  if (init_uniform) {
+    size_t off = 0;
+    for (int l = 0; l < m->L; ++l) {
+      const size_t cnt = (size_t)m->dims[l] * m->dims[l + 1];
+      std::vector<float> w(cnt);
+      const double s = std::sqrt(6.0 / m->dims[l]);
+      for (size_t i = 0; i < cnt; ++i) w[i] = (float)(init_uniform[off + i] * s);
+      off += cnt;
+      cudaError_t e = cudaMemcpy(m->W[l], w.data(), cnt * 4, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        free_model(m);
+        return cuda_fail(e, "nn_create: weight upload");
+      }
+    }
+  }
+  for (int l = 0; l < m->L; ++l) {
+    rc = refresh_bf16(m, l, 0);
+    if (rc) { free_model(m); return rc; }
+  }
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { free_model(m); return cuda_fail(e, "nn_create"); }
+  *out = m;
+  return DG_OK;
+}
+
+int nn_destroy(nn_model* m) {
+  if (!m) return fail(DG_ERR_INVALID_ARG, "nn_destroy: NULL");
+  free_model(m);
+  return DG_OK;
+}
+
+int nn_get_desc(const nn_model* m, nn_desc* d) {
+  if (!m || !d) return fail(DG_ERR_INVALID_ARG, "nn_get_desc: NULL");
+  *d = m->d;
+  return DG_OK;
+}
+
+int nn_set_scalers(nn_model* m, const float* mi, const float* si, const float* mo, const float* so) {
+  if (!m || !mi || !si || !mo || !so) return fail(DG_ERR_INVALID_ARG, "nn_set_scalers: NULL argument");
+  for (int i = 0; i < m->d.n_in; ++i)
+    if (!(si[i] > 0) || !std::isfinite(mi[i])) return fail(DG_ERR_INVALID_ARG, "nn_set_scalers: std_in must be > 0");
+  for (int i = 0; i < m->d.n_out; ++i)
+    if (!(so[i] > 0) || !std::isfinite(mo[i])) return fail(DG_ERR_INVALID_ARG, "nn_set_scalers: std_out must be > 0");
+  DG_CUDA(cudaMemcpy(m->mean_in, mi, m->d.n_in * 4, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(m->std_in, si, m->d.n_in * 4, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(m->mean_out, mo, m->d.n_out * 4, cudaMemcpyHostToDevice));
+  DG_CUDA(cudaMemcpy(m->std_out, so, m->d.n_out * 4, cudaMemcpyHostToDevice));
+  return DG_OK;
+}
+
+int nn_get_scalers(const nn_model* m, float* mi, float* si, float* mo, float* so) {
+  if (!m) return fail(DG_ERR_INVALID_ARG, "nn_get_scalers: NULL");
+  if (mi) DG_CUDA(cudaMemcpy(mi, m->mean_in, m->d.n_in * 4, cudaMemcpyDeviceToHost));
+  if (si) DG_CUDA(cudaMemcpy(si, m->std_in, m->d.n_in * 4, cudaMemcpyDeviceToHost));
+  if (mo) DG_CUDA(cudaMemcpy(mo, m->mean_out, m->d.n_out * 4, cudaMemcpyDeviceToHost));
+  if (so) DG_CUDA(cudaMemcpy(so, m->std_out, m->d.n_out * 4, cudaMemcpyDeviceToHost));
+  return DG_OK;
+}
+
+int nn_compute_scalers(nn_model* m, const float* X, const float* Y, int64_t rows, void* stream) {
+  if (!m || !X || !Y || rows < 1) return fail(DG_ERR_INVALID_ARG, "nn_compute_scalers: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int G = 64;
+  for (int which = 0; which < 2; ++which) {
+    const int n = which ? m->d.n_out : m->d.n_in;
+    const float* A = which ? Y : X;
+    double* buf = nullptr;
+    DG_CUDA(cudaMalloc(&buf, 2 * (size_t)G * n * 8));
+    dim3 grid((n + 127) / 128, G);
+    k_moments<<<grid, 128, 0, st>>>(A, rows, n, buf, buf + (size_t)G * n);
+    cudaError_t e = cudaGetLastError();
+    std::vector<double> h(2 * (size_t)G * n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), buf, h.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "nn_compute_scalers");
+    std::vector<float> mean(n), sd(n);
+    for (int f = 0; f < n; ++f) {
+      double s1 = 0, s2 = 0;
+      for (int g = 0; g < G; ++g) {
+        s1 += h[(size_t)g * n + f];
+        s2 += h[(size_t)G * n + (size_t)g * n + f];
+      }
+      const double mu = s1 / rows;
+      const double var = std::max(s2 / rows - mu * mu, 0.0);
+      mean[f] = (float)mu;
+      sd[f] = var > 0 ? (float)std::sqrt(var) : 1.f;
+      if (!(sd[f] > 0)) sd[f] = 1.f;
+    }
+    DG_CUDA(cudaMemcpy(which ? m->mean_out : m->mean_in, mean.data(), n * 4, cudaMemcpyHostToDevice));
+    DG_CUDA(cudaMemcpy(which ? m->std_out : m->std_in, sd.data(), n * 4, cudaMemcpyHostToDevice));
+  }
+  return DG_OK;
+}
+
+int nn_forward(const nn_model* m, const float* X, float* S, int rows, void* stream) {
+  if (!m || !X || !S) return fail(DG_ERR_INVALID_ARG, "nn_forward: NULL argument");
+  if (rows < 1 || rows > m->d.max_batch) return fail(DG_ERR_INVALID_ARG, "nn_forward: rows outside [1, max_batch]");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long tot = (long long)rows * m->pad[0];
+  k_prep_features<<<blocks_for(tot, 256), 256, 0, st>>>(X, nullptr, rows, m->d.n_in, m->pad[0], m->mean_in,
+                                                        m->std_in, m->act[0]);
+  DG_CUDA(cudaGetLastError());
+  return forward_layers(m, rows, S, st);
+}
+
+int nn_forcing_infer(const nn_model* m, const dg_ctx* c, const double* q, float* s, void* stream) {
+  if (!m || !c || !q || !s) return fail(DG_ERR_INVALID_ARG, "nn_forcing_infer: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  // the FP32 operator feeds the network its stage state: build it from q (phase A)
+  if (c->opts.precision == DG_PREC_FP32) DG_CUDA(launch_gradient(c, q, 0, st));
+  return nn_forcing_on_state(m, c, q, s, nullptr, nullptr, st);
+}
+
+int nn_train_step(nn_model* m, const float* X, const float* Y, const int64_t* idx, int batch, const nn_adam* hp,
+                  float* loss_out, void* stream) {
+  if (!m || !X || !Y) return fail(DG_ERR_INVALID_ARG, "nn_train_step: NULL argument");
+  if (batch < 1 || batch > m->d.max_batch) return fail(DG_ERR_INVALID_ARG, "nn_train_step: batch outside [1, max_batch]");
+  nn_adam a{1e-3f, 0.9f, 0.999f, 1e-7f};
+  if (hp) a = *hp;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int L = m->L, n_out = m->d.n_out;
+  // forward, keeping every layer input (bf16) in act[]
+  long long tot = (long long)batch * m->pad[0];
+  k_prep_features<<<blocks_for(tot, 256), 256, 0, st>>>(X, idx, batch, m->d.n_in, m->pad[0], m->mean_in, m->std_in,
+                                                        m->act[0]);
+  DG_CUDA(cudaGetLastError());
+  int rc = forward_layers(m, batch, nullptr, st);
+  if (rc) return rc;
+  // loss and dL/dy
+  k_loss<<<kLossBlocks, kLossThreads, 0, st>>>(m->y, Y, idx, batch, n_out, m->mean_out, m->std_out, m->dy,
+                                               m->loss_part);
+  DG_CUDA(cudaGetLastError());
+  k_sum_partials<<<1, kLossThreads, 0, st>>>(m->loss_part, kLossBlocks, 1.0 / ((double)batch * n_out), m->loss_dev);
+  DG_CUDA(cudaGetLastError());
+  // backward
+  float* g = m->dy;   // gradient w.r.t. the output of layer l, [batch][dims[l+1]]
+  float* gnext = m->dx;
+  for (int l = L - 1; l >= 0; --l) {
+    const int o = m->dims[l + 1], in = m->dims[l];
+    const int ldb = round_up(o, 64);
+    dim3 gp((o + 31) / 32), bt(32, 8);
+    k_grad_prep<<<gp, bt, 0, st>>>(g, batch, o, ldb, m->bpad, m->dyb, m->dyT, m->gb[l]);
+    DG_CUDA(cudaGetLastError());
+    dim3 gt((in + 31) / 32, (m->bpad + 31) / 32);
+    k_transpose_bf16<<<gt, bt, 0, st>>>(m->act[l], batch, in, m->pad[l], m->bpad, m->actT[l]);
+    DG_CUDA(cudaGetLastError());
+    // dW = g^T act : M = o, N = in, K = batch
+    GemmEpilogue ew;
+    ew.kind = kGemmF32;
+    ew.out = m->gW[l];
+    ew.ldo = in;
+    rc = gemm_bf16(m->dyT, m->bpad, m->actT[l], m->bpad, o, in, batch, ew, m->err, st);
+    if (rc) return rc;
+    if (l > 0) {
+      // d act = g W, masked by the ReLU of the layer that produced act[l]
+      GemmEpilogue ex;
+      ex.kind = kGemmMaskF32;
+      ex.mask = m->act[l];
+      ex.ldm = m->pad[l];
+      ex.out = gnext;
+      ex.ldo = in;
+      rc = gemm_bf16(m->dyb, ldb, m->Wt[l], m->pad[l + 1], batch, in, o, ex, m->err, st);
+      if (rc) return rc;
+      std::swap(g, gnext);
+    }
+  }
+  // Adam
+  ++m->adam_t;
+  const float bc1 = 1.f - std::pow(a.beta1, (float)m->adam_t);
+  const float bc2 = 1.f - std::pow(a.beta2, (float)m->adam_t);
+  for (int l = 0; l < L; ++l) {
+    const long long cw = (long long)m->dims[l] * m->dims[l + 1];
+    k_adam<<<blocks_for(cw, 256), 256, 0, st>>>(m->W[l], m->gW[l], m->mW[l], m->vW[l], cw, m->dims[l], a.lr, a.beta1,
+                                                a.beta2, a.eps, bc1, bc2, m->Wb[l], m->pad[l], m->Wt[l], m->pad[l + 1]);
+    DG_CUDA(cudaGetLastError());
+    const long long cb = m->dims[l + 1];
+    k_adam<<<blocks_for(cb, 256), 256, 0, st>>>(m->b[l], m->gb[l], m->mb[l], m->vb[l], cb, 1, a.lr, a.beta1, a.beta2,
+                                                a.eps, bc1, bc2, nullptr, 0, nullptr, 0);
+    DG_CUDA(cudaGetLastError());
+  }
+  if (loss_out) {
+    DG_CUDA(cudaMemcpyAsync(m->loss_host, m->loss_dev, 8, cudaMemcpyDeviceToHost, st));
+    rc = check_err(m, st);
+    if (rc) return rc;
+    *loss_out = (float)*m->loss_host;
+  }
+  return DG_OK;
+}
+
+int nn_get_params(const nn_model* m, int l, float* W, float* b) {
+  if (!m || l < 0 || l >= m->L) return fail(DG_ERR_INVALID_ARG, "nn_get_params: bad layer");
+  DG_CUDA(cudaDeviceSynchronize());
+  if (W) DG_CUDA(cudaMemcpy(W, m->W[l], (size_t)m->dims[l] * m->dims[l + 1] * 4, cudaMemcpyDeviceToHost));
+  if (b) DG_CUDA(cudaMemcpy(b, m->b[l], (size_t)m->dims[l + 1] * 4, cudaMemcpyDeviceToHost));
+  return DG_OK;
+}
+
+int nn_set_params(nn_model* m, int l, const float* W, const float* b) {
+  if (!m || l < 0 || l >= m->L) return fail(DG_ERR_INVALID_ARG, "nn_set_params: bad layer");
+  DG_CUDA(cudaDeviceSynchronize());
+  if (W) DG_CUDA(cudaMemcpy(m->W[l], W, (size_t)m->dims[l] * m->dims[l + 1] * 4, cudaMemcpyHostToDevice));
+  if (b) DG_CUDA(cudaMemcpy(m->b[l], b, (size_t)m->dims[l + 1] * 4, cudaMemcpyHostToDevice));
+  int rc = refresh_bf16(m, l, 0);
+  if (rc) return rc;
+  DG_CUDA(cudaDeviceSynchronize());
+  return DG_OK;
+}
+
+int nn_get_grads(const nn_model* m, int l, float* dW, float* db) {
+  if (!m || l < 0 || l >= m->L) return fail(DG_ERR_INVALID_ARG, "nn_get_grads: bad layer");
+  DG_CUDA(cudaDeviceSynchronize());
+  if (dW) DG_CUDA(cudaMemcpy(dW, m->gW[l], (size_t)m->dims[l] * m->dims[l + 1] * 4, cudaMemcpyDeviceToHost));
+  if (db) DG_CUDA(cudaMemcpy(db, m->gb[l], (size_t)m->dims[l + 1] * 4, cudaMemcpyDeviceToHost));
+  return DG_OK;
+}
+
+int nn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb, const float* bias, int relu,
+                 float* C, int ldc, void* stream) {
+  if (!A || !B || !C) return fail(DG_ERR_INVALID_ARG, "nn_gemm_bf16: NULL argument");
+  if (lda < K || ldb < K) return fail(DG_ERR_INVALID_ARG, "nn_gemm_bf16: leading dimension below K");
+  static int* err = nullptr;
+  if (!err) {
+    DG_CUDA(cudaMalloc(&err, sizeof(int)));
+    DG_CUDA(cudaMemset(err, 0, sizeof(int)));
+  }
+  GemmEpilogue ep;
+  ep.kind = kGemmF32;
+  ep.bias = bias;
+  ep.relu = relu;
+  ep.out = C;
+  ep.ldo = ldc;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = gemm_bf16(static_cast<const bf16*>(A), lda, static_cast<const bf16*>(B), ldb, M, N, K, ep, err, st);
+  if (rc) return rc;
+  int h = 0;
+  DG_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    cudaMemset(err, 0, sizeof(int));
+    return fail(DG_ERR_TIMEOUT, "nn_gemm_bf16: a bounded wait expired");
+  }
+  return DG_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------- save / load
+// File: "DGNNNET1", u32 version, nn_desc, i32 adam step, scalers, then per layer W, b and
+// the Adam moments (FP32), then the FNV-1a 64-bit hash of every byte after the magic.
+
+namespace {
+
+struct Blob {
+  std::vector<unsigned char> bytes;
+  void put(const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    bytes.insert(bytes.end(), c, c + n);
+  }
+};
+
+uint64_t fnv1a(const unsigned char* p, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+const char kMagic[8] = {'D', 'G', 'N', 'N', 'N', 'E', 'T', '1'};
+
+std::vector<float> to_host(const float* d, size_t n) {
+  std::vector<float> h(n);
+  cudaMemcpy(h.data(), d, n * 4, cudaMemcpyDeviceToHost);
+  return h;
+}
+
+}  // namespace
+
+extern "C" int nn_save(const nn_model* m, const char* path) {
+  if (!m || !path) return fail(DG_ERR_INVALID_ARG, "nn_save: NULL argument");
+  DG_CUDA(cudaDeviceSynchronize());
+  Blob b;
+  const uint32_t version = 1;
+  b.put(&version, 4);
+  b.put(&m->d, sizeof(nn_desc));
+  b.put(&m->adam_t, 4);
+  for (const float* p : {m->mean_in, m->std_in}) b.put(to_host(p, m->d.n_in).data(), m->d.n_in * 4);
+  for (const float* p : {m->mean_out, m->std_out}) b.put(to_host(p, m->d.n_out).data(), m->d.n_out * 4);
+  for (int l = 0; l < m->L; ++l) {
+    const size_t w = (size_t)m->dims[l] * m->dims[l + 1], o = m->dims[l + 1];
+    for (const float* p : {m->W[l], m->mW[l], m->vW[l]}) b.put(to_host(p, w).data(), w * 4);
+    for (const float* p : {m->b[l], m->mb[l], m->vb[l]}) b.put(to_host(p, o).data(), o * 4);
+  }
+  const uint64_t h = fnv1a(b.bytes.data(), b.bytes.size());
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(DG_ERR_IO, std::string("nn_save: cannot open ") + path);
+  bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(b.bytes.data(), 1, b.bytes.size(), f) == b.bytes.size() &&
+            std::fwrite(&h, 1, 8, f) == 8;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? DG_OK : fail(DG_ERR_IO, std::string("nn_save: write failed for ") + path);
+}
+
+extern "C" int nn_load(const char* path, int max_batch, nn_model** out) {
+  if (!path || !out) return fail(DG_ERR_INVALID_ARG, "nn_load: NULL argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(DG_ERR_IO, std::string("nn_load: cannot open ") + path);
+  std::vector<unsigned char> all;
+  unsigned char buf[65536];
+  size_t r;
+  while ((r = std::fread(buf, 1, sizeof(buf), f)) > 0) all.insert(all.end(), buf, buf + r);
+  std::fclose(f);
+  const size_t head = 8 + 4 + sizeof(nn_desc) + 4;
+  if (all.size() < head + 8 || std::memcmp(all.data(), kMagic, 8) != 0)
+    return fail(DG_ERR_IO, "nn_load: not a network file (bad magic or truncated)");
+  uint64_t h_file;
+  std::memcpy(&h_file, all.data() + all.size() - 8, 8);
+  if (fnv1a(all.data() + 8, all.size() - 16) != h_file) return fail(DG_ERR_IO, "nn_load: checksum mismatch");
+  size_t off = 8;
+  auto get = [&](void* dst, size_t n) -> bool {
+    if (off + n > all.size() - 8) return false;
+    std::memcpy(dst, all.data() + off, n);
+    off += n;
+    return true;
+  };
+  uint32_t version = 0;
+  nn_desc d;
+  int adam_t = 0;
+  get(&version, 4);
+  get(&d, sizeof(d));
+  get(&adam_t, 4);
+  if (version != 1) return fail(DG_ERR_IO, "nn_load: unsupported version");
+  d.max_batch = max_batch > 0 ? max_batch : d.max_batch;
+  nn_model* m = nullptr;
+  int rc = alloc_model(&d, &m);
+  if (rc) return rc;
+  m->adam_t = adam_t;
+  auto upload = [&](float* dst, size_t n) -> bool {
+    std::vector<float> h(n);
+    if (!get(h.data(), n * 4)) return false;
+    return cudaMemcpy(dst, h.data(), n * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  bool ok = upload(m->mean_in, d.n_in) && upload(m->std_in, d.n_in) && upload(m->mean_out, d.n_out) &&
+            upload(m->std_out, d.n_out);
+  for (int l = 0; ok && l < m->L; ++l) {
+    const size_t w = (size_t)m->dims[l] * m->dims[l + 1], o = m->dims[l + 1];
+    ok = upload(m->W[l], w) && upload(m->mW[l], w) && upload(m->vW[l], w) && upload(m->b[l], o) &&
+         upload(m->mb[l], o) && upload(m->vb[l], o);
+  }
+  if (!ok || off != all.size() - 8) {
+    free_model(m);
+    return fail(DG_ERR_IO, "nn_load: truncated or inconsistent file");
+  }
+  for (int l = 0; l < m->L; ++l) {
+    rc = refresh_bf16(m, l, 0);
+    if (rc) { free_model(m); return rc; }
+  }
+  DG_CUDA(cudaDeviceSynchronize());
+  *out = m;
+  return DG_OK;
+}

@@ -30,7 +30,7 @@ class DGError(RuntimeError):
 
 
 class dg_opts(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("rk_register_fp32", ctypes.c_int),
+    _fields_ = [("precision", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("Cs", ctypes.c_double), ("Prt", ctypes.c_double),
                 ("les_delta", ctypes.c_double), ("elems_per_block", ctypes.c_int)]
 
@@ -65,6 +65,9 @@ _SIGS = {
     "dg_diagnostics": [_P, _P, _P, _P, ctypes.POINTER(dg_diag), _P],
     "dg_stable_dt": [_P, _P, _D, ctypes.POINTER(_D), _P],
     "dg_make_pairs": [_P, _P, _P, _P, _D, _I, _I, _P, _P, _P],
+    "dg_check_conversions": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P],
+    "dg_profile_rk3": [_P, _P, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I),
+                       ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D), _P],
 }
 
 _lib = None
@@ -234,3 +237,22 @@ def dg_make_pairs(lo, q_bar_n, q_nn_np1, q_bar_np1, dt, first_var, n_vars, X, Y,
             raise ValueError(f"{nm} must be float32 with {nodes * n_vars} values")
     check(lib().dg_make_pairs(ctypes.c_void_p(lo), ptr(q_bar_n), ptr(q_nn_np1), ptr(q_bar_np1), float(dt),
                               int(first_var), int(n_vars), ptr(X), ptr(Y), stream_ptr(stream)))
+
+
+def dg_profile_rk3(ctx, q, dt, nsteps=1, stream=None):
+    """Per-kernel device times of nsteps RK3 steps (CUDA events inside the library)."""
+    _check_state(ctx, q, "q")
+    tg, tf, fb, gb = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lg, lf = ctypes.c_int(), ctypes.c_int()
+    check(lib().dg_profile_rk3(ctypes.c_void_p(ctx), ptr(q), float(dt), int(nsteps), ctypes.byref(tg),
+                               ctypes.byref(tf), ctypes.byref(lg), ctypes.byref(lf), ctypes.byref(fb),
+                               ctypes.byref(gb), stream_ptr(stream)))
+    return {"ms_gradient": tg.value, "ms_flux": tf.value, "launches_gradient": lg.value,
+            "launches_flux": lf.value, "flux_bytes_per_launch": fb.value, "gradient_bytes_per_launch": gb.value}
+
+
+def dg_check_conversions(x, stream=None):
+    """(mismatches of the FP64->FP32 conversion, of the FP32->FP64 widening) on device array x."""
+    mm = (ctypes.c_int64 * 2)()
+    check(lib().dg_check_conversions(ptr(x), int(x.numel()), mm, stream_ptr(stream)))
+    return int(mm[0]), int(mm[1])

@@ -1,6 +1,182 @@
-"""Thin Python binding of the forcing-network part of libdgnn.so (include/dgnn_nn.h)."""
+"""Thin Python binding of the forcing network in libdgnn.so (C ABI in include/dgnn_nn.h).
+
+Same names as the C entry points; arguments are marshalled (tensors to device
+pointers, numpy arrays to host pointers) and statuses raised as ``DGError``.
+"""
+import ctypes
+
+import numpy as np
+
+
+class nn_desc(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int), ("n_out", ctypes.c_int), ("width", ctypes.c_int),
+                ("n_hidden", ctypes.c_int), ("first_var", ctypes.c_int), ("n_vars", ctypes.c_int),
+                ("max_batch", ctypes.c_int)]
+
+
+class nn_adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIGS = {
+    "nn_create": [ctypes.POINTER(nn_desc), _P, ctypes.POINTER(_P)],
+    "nn_destroy": [_P],
+    "nn_set_scalers": [_P, _P, _P, _P, _P],
+    "nn_get_scalers": [_P, _P, _P, _P, _P],
+    "nn_compute_scalers": [_P, _P, _P, ctypes.c_int64, _P],
+    "nn_forward": [_P, _P, _P, _I, _P],
+    "nn_forcing_infer": [_P, _P, _P, _P, _P],
+    "nn_train_step": [_P, _P, _P, _P, _I, ctypes.POINTER(nn_adam), ctypes.POINTER(ctypes.c_float), _P],
+    "nn_get_params": [_P, _I, _P, _P],
+    "nn_set_params": [_P, _I, _P, _P],
+    "nn_get_grads": [_P, _I, _P, _P],
+    "nn_get_desc": [_P, ctypes.POINTER(nn_desc)],
+    "nn_save": [_P, ctypes.c_char_p],
+    "nn_load": [ctypes.c_char_p, _I, ctypes.POINTER(_P)],
+    "nn_gemm_bf16": [_I, _I, _I, _P, _I, _P, _I, _P, _I, _P, _I, _P],
+}
 
 
 def _register(L):
-    """Declares the C signatures of the network entry points present in the library."""
+    for name, args in _SIGS.items():
+        f = getattr(L, name, None)
+        if f is None:
+            continue
+        f.argtypes = args
+        f.restype = ctypes.c_int
     return L
+
+
+def _dg():
+    from . import dg
+    return dg
+
+
+def _h(net):
+    return ctypes.c_void_p(net)
+
+
+def layer_dims(desc):
+    return [desc.n_in] + [desc.width] * desc.n_hidden + [desc.n_out]
+
+
+def nn_create(n_in, n_out, width, n_hidden, first_var=0, n_vars=5, max_batch=4096, init_uniform=None):
+    """Returns an opaque handle.  init_uniform: list of U(-1,1) arrays (out, in) per layer, or None."""
+    dg = _dg()
+    d = nn_desc(n_in, n_out, width, n_hidden, first_var, n_vars, max_batch)
+    flat = None
+    if init_uniform is not None:
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(a, np.float32).ravel() for a in init_uniform]))
+        if flat.size != sum(a * b for a, b in zip(layer_dims(d)[:-1], layer_dims(d)[1:])):
+            raise ValueError("init_uniform does not match the layer shapes")
+    h = ctypes.c_void_p()
+    dg.check(dg.lib().nn_create(ctypes.byref(d), dg.ptr(flat), ctypes.byref(h)))
+    return h.value
+
+
+def nn_destroy(net):
+    dg = _dg()
+    dg.check(dg.lib().nn_destroy(_h(net)))
+
+
+def nn_get_desc(net):
+    dg = _dg()
+    d = nn_desc()
+    dg.check(dg.lib().nn_get_desc(_h(net), ctypes.byref(d)))
+    return d
+
+
+def nn_set_scalers(net, mean_in, std_in, mean_out, std_out):
+    dg = _dg()
+    arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (mean_in, std_in, mean_out, std_out)]
+    dg.check(dg.lib().nn_set_scalers(_h(net), *[dg.ptr(a) for a in arrs]))
+
+
+def nn_get_scalers(net):
+    dg = _dg()
+    d = nn_get_desc(net)
+    out = [np.zeros(n, np.float32) for n in (d.n_in, d.n_in, d.n_out, d.n_out)]
+    dg.check(dg.lib().nn_get_scalers(_h(net), *[dg.ptr(a) for a in out]))
+    return tuple(out)
+
+
+def nn_compute_scalers(net, X, Y, stream=None):
+    dg = _dg()
+    dg.check(dg.lib().nn_compute_scalers(_h(net), dg.ptr(X), dg.ptr(Y), int(X.shape[0]), dg.stream_ptr(stream)))
+
+
+def nn_forward(net, X, S, stream=None):
+    dg = _dg()
+    dg.check(dg.lib().nn_forward(_h(net), dg.ptr(X), dg.ptr(S), int(X.shape[0]), dg.stream_ptr(stream)))
+
+
+def nn_forcing_infer(net, ctx, q, s, stream=None):
+    dg = _dg()
+    dg.check(dg.lib().nn_forcing_infer(_h(net), ctypes.c_void_p(ctx), dg.ptr(q), dg.ptr(s), dg.stream_ptr(stream)))
+
+
+def nn_train_step(net, X, Y, idx=None, batch=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-7, want_loss=True,
+                  stream=None):
+    dg = _dg()
+    if batch is None:
+        batch = int(idx.shape[0]) if idx is not None else int(X.shape[0])
+    hp = nn_adam(lr, beta1, beta2, eps)
+    loss = ctypes.c_float()
+    dg.check(dg.lib().nn_train_step(_h(net), dg.ptr(X), dg.ptr(Y), dg.ptr(idx), int(batch), ctypes.byref(hp),
+                                    ctypes.byref(loss) if want_loss else None, dg.stream_ptr(stream)))
+    return loss.value if want_loss else None
+
+
+def _layer_shape(net, layer):
+    dims = layer_dims(nn_get_desc(net))
+    return dims[layer + 1], dims[layer]
+
+
+def nn_get_params(net, layer):
+    dg = _dg()
+    o, i = _layer_shape(net, layer)
+    W, b = np.zeros((o, i), np.float32), np.zeros(o, np.float32)
+    dg.check(dg.lib().nn_get_params(_h(net), int(layer), dg.ptr(W), dg.ptr(b)))
+    return W, b
+
+
+def nn_set_params(net, layer, W, b):
+    dg = _dg()
+    W = np.ascontiguousarray(W, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    dg.check(dg.lib().nn_set_params(_h(net), int(layer), dg.ptr(W), dg.ptr(b)))
+
+
+def nn_get_grads(net, layer):
+    dg = _dg()
+    o, i = _layer_shape(net, layer)
+    dW, db = np.zeros((o, i), np.float32), np.zeros(o, np.float32)
+    dg.check(dg.lib().nn_get_grads(_h(net), int(layer), dg.ptr(dW), dg.ptr(db)))
+    return dW, db
+
+
+def nn_save(net, path):
+    dg = _dg()
+    dg.check(dg.lib().nn_save(_h(net), str(path).encode()))
+
+
+def nn_load(path, max_batch=4096):
+    dg = _dg()
+    h = ctypes.c_void_p()
+    dg.check(dg.lib().nn_load(str(path).encode(), int(max_batch), ctypes.byref(h)))
+    return h.value
+
+
+def nn_gemm_bf16(A, B, bias=None, relu=False, stream=None):
+    """C = A B^T (+ bias, ReLU) for bf16 CUDA tensors A (M x K) and B (N x K); returns float32 C."""
+    import torch
+    dg = _dg()
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    dg.check(dg.lib().nn_gemm_bf16(M, N, K, dg.ptr(A), A.stride(0), dg.ptr(B), B.stride(0), dg.ptr(bias),
+                                   int(bool(relu)), dg.ptr(C), N, dg.stream_ptr(stream)))
+    return C

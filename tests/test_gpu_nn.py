@@ -1,0 +1,239 @@
+"""GPU parity of the forcing network (tcgen05 BF16 GEMMs, training kernels) against the
+FP64 oracle with the same bf16 rounding points, through the C ABI."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import algorithm1, dgsem, mlp, physics
+from paper_2207_11571_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# BF16 network against the oracle with the same rounding points: FP32 vs FP64
+# accumulation (~1e-6) plus rare one-ulp (2^-8) differences in bf16-rounded activations
+# near rounding ties.
+NN_RTOL = 2e-3
+
+
+@pytest.fixture(scope="module")
+def L():
+    from tests.libbuild import ensure_built
+    ensure_built()
+    from paper_2207_11571_gb300 import dg
+    dg.lib()
+    return dg
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def bf16_dev(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).cuda()
+
+
+@pytest.mark.parametrize("M,N,K,bias,relu", [
+    (128, 64, 64, False, False), (300, 320, 320, True, False), (4096, 512, 320, True, True),
+    (1000, 192, 512, False, True), (77, 100, 135, True, False), (4096, 320, 512, True, False),
+    (256, 256, 4096, False, False)])
+def test_tcgen05_gemm_matches_float64_reference(L, M, N, K, bias, relu):
+    from paper_2207_11571_gb300 import nn
+    lda = (K + 7) // 8 * 8
+    A = torch.randn(M, lda, generator=torch.Generator().manual_seed(M + K)).to(torch.bfloat16)
+    B = torch.randn(N, lda, generator=torch.Generator().manual_seed(N + 3 * K)).to(torch.bfloat16)
+    if lda > K:  # padding columns hold garbage: TMA must read them as zeros (K is the extent)
+        A[:, K:] = 1e4
+        B[:, K:] = -1e4
+    b = torch.randn(N, generator=torch.Generator().manual_seed(7)) if bias else None
+    C = nn.nn_gemm_bf16(A.cuda(), B.cuda(), b.cuda() if bias else None, relu).cpu().double()
+    ref = A[:, :K].double() @ B[:, :K].double().T
+    if bias:
+        ref += b.double()
+    if relu:
+        ref = ref.clamp_min(0)
+    err = (C - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 1e-5, err
+
+
+def make_net(nn, n_in, width, n_hidden, seed, max_batch=512, first_var=0, n_vars=5):
+    dims = [n_in] + [width] * n_hidden + [n_in]
+    draws = inputs.uniform_draws(dims, seed)
+    h = nn.nn_create(n_in, n_in, width, n_hidden, first_var, n_vars, max_batch, draws)
+    params = mlp.he_uniform_init(dims, draws)
+    # the library keeps FP32 masters: the oracle starts from the same FP32 values
+    params = [(W.astype(np.float32).astype(np.float64), b) for W, b in params]
+    return h, params
+
+
+def set_random_scalers(nn, h, n, seed):
+    rng = np.random.default_rng(seed)
+    sc = (rng.normal(0, 0.5, n).astype(np.float32), rng.uniform(0.5, 2.0, n).astype(np.float32),
+          rng.normal(0, 0.1, n).astype(np.float32), rng.uniform(0.1, 1.0, n).astype(np.float32))
+    nn.nn_set_scalers(h, *sc)
+    return tuple(s.astype(np.float64) for s in sc)
+
+
+@pytest.mark.parametrize("n_in,width,n_hidden,rows", [(320, 256, 4, 300), (192, 512, 2, 129), (320, 512, 6, 512)])
+def test_forward_matches_oracle(L, n_in, width, n_hidden, rows):
+    from paper_2207_11571_gb300 import nn
+    h, params = make_net(nn, n_in, width, n_hidden, seed=n_in + width)
+    sc = set_random_scalers(nn, h, n_in, 1)
+    X = inputs.normal((rows, n_in), 2).astype(np.float32)
+    S = torch.empty(rows, n_in, dtype=torch.float32, device="cuda")
+    nn.nn_forward(h, torch.from_numpy(X).cuda(), S)
+    ref = mlp.infer(params, sc, X.astype(np.float64), bf16=True)
+    assert rel(S.cpu().numpy(), ref) < NN_RTOL
+    nn.nn_destroy(h)
+
+
+def test_train_step_gradients_loss_and_adam_match_oracle(L):
+    from paper_2207_11571_gb300 import nn
+    n, width, nh, B = 320, 256, 3, 384
+    h, params = make_net(nn, n, width, nh, seed=11)
+    sc = set_random_scalers(nn, h, n, 2)
+    X = inputs.normal((1000, n), 3).astype(np.float32)
+    Y = (0.3 * inputs.normal((1000, n), 4)).astype(np.float32)
+    idx = np.random.default_rng(5).permutation(1000)[:B].astype(np.int64)
+    loss = nn.nn_train_step(h, torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), torch.from_numpy(idx).cuda(),
+                            lr=1e-3)
+    state = {}
+    new, loss_or, grads = mlp.train_step(params, state, sc, X[idx].astype(np.float64), Y[idx].astype(np.float64),
+                                         bf16=True, lr=1e-3, eps=1e-7)
+    assert loss == pytest.approx(loss_or, rel=NN_RTOL)
+    for l in range(nh + 1):
+        dW, db = nn.nn_get_grads(h, l)
+        assert rel(dW, grads[l][0]) < NN_RTOL, l
+        assert rel(db, grads[l][1]) < NN_RTOL, l
+    # Adam on the library's own gradients: isolate the optimiser arithmetic
+    params2 = [(W, b) for W, b in params]
+    g_lib = [tuple(a.astype(np.float64) for a in nn.nn_get_grads(h, l)) for l in range(nh + 1)]
+    new_lib = mlp.adam_step(params2, g_lib, {}, lr=1e-3, eps=1e-7)
+    for l in range(nh + 1):
+        W, b = nn.nn_get_params(h, l)
+        np.testing.assert_allclose(W, new_lib[l][0], rtol=0, atol=2e-6 * max(1.0, np.abs(W).max()))
+        np.testing.assert_allclose(b, new_lib[l][1], rtol=0, atol=2e-6)
+    nn.nn_destroy(h)
+
+
+def test_training_reduces_loss_tenfold(L):
+    from paper_2207_11571_gb300 import nn
+    n, B = 192, 256
+    h, _ = make_net(nn, n, 256, 3, seed=21, max_batch=B, first_var=1, n_vars=3)
+    X = inputs.normal((4096, n), 6).astype(np.float32)
+    A = inputs.normal((n, n), 7, 1.0 / np.sqrt(n)).astype(np.float32)
+    Y = np.tanh(X @ A).astype(np.float32)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    nn.nn_compute_scalers(h, Xd, Yd)
+    losses = []
+    for epoch in range(15):
+        perm = torch.from_numpy(inputs.epoch_permutation(4096, 9, epoch)).cuda()
+        for b0 in range(0, 4096, B):
+            losses.append(nn.nn_train_step(h, Xd, Yd, perm[b0:b0 + B], lr=2e-3))
+    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+    nn.nn_destroy(h)
+
+
+def test_compute_scalers_matches_numpy(L):
+    from paper_2207_11571_gb300 import nn
+    h, _ = make_net(nn, 320, 64, 1, seed=3)
+    X = (5 + 2 * inputs.normal((3000, 320), 8)).astype(np.float32)
+    Y = inputs.normal((3000, 320), 9).astype(np.float32)
+    Y[:, 7] = 1.5  # zero spread -> std 1
+    nn.nn_compute_scalers(h, torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda())
+    mi, si, mo, so = nn.nn_get_scalers(h)
+    ref = algorithm1.scalers_from_data(X.astype(np.float64), Y.astype(np.float64))
+    for a, b in zip((mi, si, mo, so), ref):
+        np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-6)
+    assert so[7] == 1.0
+    nn.nn_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_forcing_infer_matches_forward_on_element_features(L, prec):
+    from paper_2207_11571_gb300 import dg, nn
+    K, P = 3, 3
+    ctx = dg.dg_create(K, P, 1600.0, 0.1, 0.71, 0, precision=prec)
+    N = K ** 3 * 64
+    q = torch.empty(5 * N, dtype=torch.float64, device="cuda")
+    dg.dg_init_tgv(ctx, q, torch.from_numpy(inputs.perturbation((5, N)).ravel()).cuda())
+    h, _ = make_net(nn, 320, 256, 2, seed=4, max_batch=10)   # 27 elements in chunks of 10
+    feats = dgsem.element_features(q.cpu().numpy().reshape(5, K, K, K, 4, 4, 4)).astype(np.float32)
+    mean, sd = feats.mean(0), feats.std(0) + 1e-3
+    nn.nn_set_scalers(h, mean, sd, np.zeros(320, np.float32), np.full(320, 0.01, np.float32))
+    s = torch.empty(K ** 3 * 320, dtype=torch.float32, device="cuda")
+    nn.nn_forcing_infer(h, ctx, q, s)
+    S = torch.empty(10, 320, dtype=torch.float32, device="cuda")
+    ref = np.concatenate([_fw(nn, h, feats[i:i + 10], S) for i in range(0, 27, 10)])
+    tol = 0 if prec == 0 else NN_RTOL
+    assert rel(s.cpu().numpy().reshape(27, 320), ref) <= tol
+    nn.nn_destroy(h)
+    dg.dg_destroy(ctx)
+
+
+def _fw(nn, h, X, S):
+    rows = X.shape[0]
+    nn.nn_forward(h, torch.from_numpy(np.ascontiguousarray(X)).cuda(), S[:rows])
+    return S[:rows].cpu().numpy().copy()
+
+
+def test_rhs_and_rk3_with_forcing_match_oracle(L):
+    """dq/dt = p_LO(q) + s(q) (Eq. 4) and RK3 with s in every stage, FP64 operator."""
+    from paper_2207_11571_gb300 import dg, nn
+    K, P = 2, 3
+    flow = physics.Flow(Re=200.0, Mach=0.1)
+    mesh = dgsem.Mesh(K, P)
+    N = K ** 3 * 64
+    pert = inputs.perturbation((5, N))
+    q_or = dgsem.tgv_state(mesh, flow, pert)
+    ctx = dg.dg_create(K, P, 200.0, 0.1, 0.71, 0)
+    q = torch.from_numpy(q_or.reshape(5, -1).copy()).cuda()
+    h, params = make_net(nn, 320, 128, 2, seed=8, max_batch=8)
+    feats = dgsem.element_features(q_or)
+    sc32 = (feats.mean(0).astype(np.float32), (feats.std(0) + 1e-2).astype(np.float32),
+            np.zeros(320, np.float32), np.full(320, 0.05, np.float32))
+    nn.nn_set_scalers(h, *sc32)
+    sc = tuple(s.astype(np.float64) for s in sc32)
+    R = torch.empty_like(q)
+    dg.dg_rhs(ctx, q, R, forcing=h)
+    s_or = algorithm1.forcing_field(params, sc, q_or, 4, bf16=True)
+    R_plain = dgsem.rhs(q_or, mesh, flow)
+    got_s = R.cpu().numpy().reshape(q_or.shape) - R_plain
+    assert rel(got_s, s_or) < NN_RTOL
+    dg.dg_rk3_step(ctx, q, 1e-3, 2, forcing=h)
+    ref = q_or
+    for _ in range(2):
+        ref = algorithm1.corrected_step(ref, 1e-3, mesh, flow, params, sc, mode="stage", bf16=True)
+    incr_gpu = q.cpu().numpy().reshape(q_or.shape) - q_or
+    assert rel(incr_gpu, ref - q_or) < NN_RTOL
+    nn.nn_destroy(h)
+    dg.dg_destroy(ctx)
+
+
+def test_save_load_roundtrip_and_corruption_detection(L, tmp_path):
+    from paper_2207_11571_gb300 import dg, nn
+    h, _ = make_net(nn, 192, 64, 2, seed=5, first_var=1, n_vars=3)
+    set_random_scalers(nn, h, 192, 3)
+    path = tmp_path / "net.bin"
+    nn.nn_save(h, path)
+    h2 = nn.nn_load(path, max_batch=64)
+    for l in range(3):
+        for a, b in zip(nn.nn_get_params(h, l), nn.nn_get_params(h2, l)):
+            np.testing.assert_array_equal(a, b)
+    for a, b in zip(nn.nn_get_scalers(h), nn.nn_get_scalers(h2)):
+        np.testing.assert_array_equal(a, b)
+    raw = bytearray(path.read_bytes())
+    raw[100] ^= 0xFF
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(dg.DGError) as e:
+        nn.nn_load(bad)
+    assert e.value.status == dg.DG_ERR_IO
+    (tmp_path / "short.bin").write_bytes(bytes(raw[:50]))
+    with pytest.raises(dg.DGError):
+        nn.nn_load(tmp_path / "short.bin")
+    with pytest.raises(dg.DGError):
+        nn.nn_load(tmp_path / "missing.bin")
+    nn.nn_destroy(h)
+    nn.nn_destroy(h2)
