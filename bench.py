@@ -215,7 +215,7 @@ def run_ours(args, rank, ws):
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
 
-    ctxs, states, dts, nodes = [], [], [], []
+    ctxs, states, dts, nodes, tuned = [], [], [], [], []
     for K, P in WORKLOAD:
         c = dg.dg_create(K, P, RE, MACH, PR, 0, precision=dg.DG_PREC_FP32)
         N = dg.dg_sizes(c)[0]
@@ -224,6 +224,7 @@ def run_ours(args, rank, ws):
         dg.dg_init_tgv(c, q, pert)
         del pert
         dts.append(dg.dg_stable_dt(c, q, CFL))
+        tuned.append(dg.dg_autotune(c, q, dts[-1])[0])
         ctxs.append(c)
         states.append(q)
         nodes.append(N)
@@ -310,6 +311,7 @@ def run_ours(args, rank, ws):
                 "data": "synthetic (closed-form TGV field + seeded 1e-6 perturbation)",
                 "config": {"workload": WORKLOAD_NAME, "meshes": [f"{K}^3/P{P}" for K, P in WORKLOAD],
                            "nodes": nodes, "l2": "working set per mesh 190-400 MB > 129 MB L2 (no flush)",
+                           "elems_per_block": tuned,
                            "parallelism": f"replicas x{ws}", "per_workload": per_workload},
                 "roofline": roofline, "kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 6 * len(WORKLOAD) * args.steps, "clocks": clk}

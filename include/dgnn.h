@@ -163,6 +163,12 @@ int dg_profile_rk3(dg_ctx* ctx, double* q, double dt, int nsteps, double* ms_gra
                    double* flux_bytes_per_launch, double* gradient_bytes_per_launch,
                    void* stream);
 
+/* Autotuner: times one RK3 step (on a scratch copy of the DEVICE state q; q is not
+ * modified) for every elements-per-block value E = 1, 2, 4, ... that fits the block size
+ * and shared memory of this P, and keeps the fastest for the context.  best_E (HOST,
+ * may be NULL) receives it, best_ms (HOST, may be NULL) its time per step.  Synchronises. */
+int dg_autotune(dg_ctx* ctx, const double* q, double dt, int* best_E, double* best_ms, void* stream);
+
 /* Self-check of the integer-pipe FP64 <-> FP32 conversions the FP32 operator uses:
  * counts the n DEVICE inputs x where the round-to-nearest-even FP64 -> FP32 conversion
  * differs from the hardware conversion (mismatches[0]; inputs should be zero or within

@@ -95,7 +95,9 @@ int nn_load(const char* path, int max_batch, nn_model** out);
 
 /* Library primitive used by the network: C[M x N] = A[M x K] B[N x K]^T on the tensor cores,
  * A, B row-major bf16 (DEVICE, leading dimensions lda, ldb multiples of 8 elements,
- * 16-byte aligned), C row-major float (ldc >= N), optional bias[N] and ReLU. */
+ * 16-byte aligned), C row-major float (ldc >= N), optional bias[N] and ReLU.  The operands
+ * are read in 16-byte chunks: when K is not a multiple of 8, columns K .. roundup(K, 8) - 1
+ * of A and B must hold zeros; columns beyond are never read. */
 int nn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                  const float* bias, int relu, float* C, int ldc, void* stream);
 

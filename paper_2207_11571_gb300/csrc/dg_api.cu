@@ -49,9 +49,9 @@ cudaError_t launch_gradient(const dg_ctx* c, const double* q, int src, cudaStrea
 
 cudaError_t launch_flux(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
                         double dt, cudaStream_t st) {
-  RkArgs rk{A, B, dt, 1.0 / kRkB[0]};
-  return c->opts.precision == DG_PREC_FP32 ? flux_f32(c, q, dqdt, f, mode, rk, st)
-                                           : flux_f64(c, q, dqdt, f, mode, rk, st);
+  const double invB1 = 1.0 / kRkB[0];
+  return c->opts.precision == DG_PREC_FP32 ? flux_f32(c, q, dqdt, f, mode, A, B, dt, invB1, st)
+                                           : flux_f64(c, q, dqdt, f, mode, A, B, dt, invB1, st);
 }
 
 // Launch plan of RK stage k (0, 1, 2): source of the phase-A stage state and phase-B mode.
@@ -409,3 +409,52 @@ int dg_profile_rk3(dg_ctx* c, double* q, double dt, int nsteps, double* ms_gradi
 const char* dg_last_error(void) { return g_last_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- autotuner
+
+extern "C" int dg_autotune(dg_ctx* c, const double* q, double dt, int* best_E, double* best_ms, void* stream) {
+  using namespace dgnn;
+  if (!c || !q) return fail(DG_ERR_INVALID_ARG, "dg_autotune: NULL argument");
+  if (!std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_autotune: bad dt");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = 5 * c->N * sizeof(double);
+  double* work = nullptr;
+  DG_CUDA(cudaMalloc(&work, bytes));
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  const int E0 = c->geom.E;
+  int bestE = E0;
+  double best = 1e300;
+  for (int E = 1; e == cudaSuccess && E <= max_elems_per_block(c->P); E *= 2) {
+    c->geom.E = E;
+    e = cudaMemcpyAsync(work, q, bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) break;
+    if (rk3_steps(c, work, dt, 1, nullptr, st) != DG_OK) {  // shared memory too large for this E: skip
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(a, st);
+    const int reps = 3;
+    if (rk3_steps(c, work, dt, reps, nullptr, st) != DG_OK) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(b, st);
+    e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && ms / reps < best) {
+      best = ms / reps;
+      bestE = E;
+    }
+  }
+  c->geom.E = (best < 1e300) ? bestE : E0;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(work);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_autotune");
+  if (best_E) *best_E = c->geom.E;
+  if (best_ms) *best_ms = best;
+  return DG_OK;
+}

@@ -44,12 +44,11 @@ cudaError_t launch_make_pairs(const dg_ctx* lo, const double* qb_n, const double
                               double dt, int first_var, int n_vars, float* X, float* Y, cudaStream_t st);
 
 // Operator kernels per precision (dg_kernels_f32.cu / dg_kernels_f64.cu).
-struct RkArgs;
 cudaError_t gradient_f32(const dg_ctx* c, const double* q, int src, cudaStream_t st);
 cudaError_t gradient_f64(const dg_ctx* c, const double* q, int src, cudaStream_t st);
-cudaError_t flux_f32(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, const RkArgs& rk,
-                     cudaStream_t st);
-cudaError_t flux_f64(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, const RkArgs& rk,
-                     cudaStream_t st);
+cudaError_t flux_f32(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                     double dt, double invB1, cudaStream_t st);
+cudaError_t flux_f64(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                     double dt, double invB1, cudaStream_t st);
 
 }  // namespace dgnn

@@ -57,16 +57,6 @@ __device__ __forceinline__ float from_double<float>(double x) { return d2f_rn(x)
 template <>
 __device__ __forceinline__ double from_double<double>(double x) { return x; }
 
-// Reference-shifted operator state of one node from the FP64 conserved variables.
-template <typename T>
-__device__ __forceinline__ void shift_state(const double q[5], const Phys& ph, T s[5]) {
-  s[0] = from_double<T>(q[0] - ph.rho_ref);
-  s[1] = from_double<T>(q[1]);
-  s[2] = from_double<T>(q[2]);
-  s[3] = from_double<T>(q[3]);
-  s[4] = from_double<T>(q[4] - ph.E_ref);
-}
-
 // ---------------------------------------------------------------- node quantities
 
 // Index of tau_ab in the packed 6-vector (xx, yy, zz, xy, xz, yz).
@@ -130,12 +120,13 @@ __device__ __forceinline__ void viscous_flux(const T vis[9], const T v[3], int d
   f[4] = v[0] * t0 + v[1] * t1 + v[2] * t2 + vis[6 + d];
 }
 
-// Roe flux in direction +e_d between the left state sL and the right state sR:
-// F* = (f(qL) + f(qR))/2 - |A~|(qR - qL)/2 with Roe-averaged velocity, enthalpy and
-// sound speed; acoustic waves (Vn -/+ c), entropy wave and shear waves (Vn).
+// Roe dissipation |A~| (qR - qL) in direction +e_d between the left state sL and the
+// right state sR, with Roe-averaged velocity, enthalpy and sound speed; acoustic waves
+// (Vn -/+ c), entropy wave and shear waves (Vn).  The Roe flux is
+// F* = (f(qL) + f(qR))/2 - diss/2.
 template <typename T>
-__device__ __forceinline__ void roe_flux(const T sL[5], const Prim<T>& wL, const T sR[5], const Prim<T>& wR, int d,
-                                         T gm1, T Hc, T F[5]) {
+__device__ __forceinline__ void roe_dissipation(const T sL[5], const Prim<T>& wL, const T sR[5], const Prim<T>& wR,
+                                                int d, T gm1, T Hc, T diss[5]) {
   const T HL = (sL[4] + wL.pp + Hc) * wL.ir, HR = (sR[4] + wR.pp + Hc) * wR.ir;
   const T sqL = dsqrt(wL.rho), sqR = dsqrt(wR.rho);
   const T wden = T(1) / (sqL + sqR);
@@ -155,10 +146,6 @@ __device__ __forceinline__ void roe_flux(const T sL[5], const Prim<T>& wL, const
   const T a2 = dr - dp * (T(2) * inv2c2);
   const T a5 = (dp + rt * c * dVn) * inv2c2;
   const T l1 = fabs(Vn - c) * a1, l2 = fabs(Vn), l5 = fabs(Vn + c) * a5;
-  T fL[5], fR[5];
-  euler_flux(sL, wL, Hc, d, fL);
-  euler_flux(sR, wR, Hc, d, fR);
-  T diss[5];
   diss[0] = l1 + l2 * a2 + l5;
   T shear_dot = T(0);
 #pragma unroll
@@ -169,30 +156,18 @@ __device__ __forceinline__ void roe_flux(const T sL[5], const Prim<T>& wL, const
   }
   diss[1 + d] += (l5 - l1) * c;
   diss[4] = l1 * (Ht - c * Vn) + l2 * (a2 * ke + shear_dot) + l5 * (Ht + c * Vn);
-#pragma unroll
-  for (int v = 0; v < 5; ++v) F[v] = T(0.5) * (fL[v] + fR[v] - diss[v]);
 }
 
-// Effective viscosity and heat coefficient at a node from the velocity gradient
-// G[d][a] = d u_a / d x_d (a < 3).  Smagorinsky: mu_t = rho (Cs delta)^2 sqrt(2 S:S).
+// Roe flux F* = (f(qL) + f(qR))/2 - |A~|(qR - qL)/2 in direction +e_d.
 template <typename T>
-__device__ __forceinline__ void transport(const Phys& ph, T rho, const T G[3][4], T* mu, T* lam) {
-  T m = T(ph.mu), l = T(ph.lam);
-  if (ph.les) {
-    T ss = T(0);
+__device__ __forceinline__ void roe_flux(const T sL[5], const Prim<T>& wL, const T sR[5], const Prim<T>& wR, int d,
+                                         T gm1, T Hc, T F[5]) {
+  T fL[5], fR[5], diss[5];
+  euler_flux(sL, wL, Hc, d, fL);
+  euler_flux(sR, wR, Hc, d, fR);
+  roe_dissipation(sL, wL, sR, wR, d, gm1, Hc, diss);
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const T s = T(0.5) * (G[b][a] + G[a][b]);
-        ss += s * s;
-      }
-    const T mut = rho * T(ph.csd2) * dsqrt(T(2) * ss);
-    m += mut;
-    l += mut * T(ph.lam_t);
-  }
-  *mu = m;
-  *lam = l;
+  for (int v = 0; v < 5; ++v) F[v] = T(0.5) * (fL[v] + fR[v] - diss[v]);
 }
 
 }  // namespace dgnn

@@ -16,10 +16,16 @@
 // stage 2 stores it.  In the FP64 operator every stage updates q in FP64 (the plain
 // 2N scheme).
 //
-// Each CUDA block owns E consecutive elements, one thread per node; element tiles (the
-// derivative matrix, per-node fields) are staged in shared memory, where the 1D
-// derivative contractions read them.  Neighbour interface values are gathered from
-// global memory (L2-resident: neighbours are processed by nearby blocks).
+// Each CUDA block owns E consecutive elements, one thread per node for the nodal work.
+// At kernel start the block issues all its global loads: its own nodes into registers
+// and a halo (the neighbours' face nodes of all six faces of its elements) into shared
+// memory.  The interface fluxes are then computed as dense work items, one per
+// (element, face, face node), so that every lane of a warp does useful Roe work (with
+// one thread per node, each warp would walk all three face directions at half
+// occupancy); node threads add the lifted results in a fixed order.  The 1D derivative
+// contractions read element tiles in shared memory.  All constants arrive in the
+// operator precision (OpConst): no FP64 arithmetic or conversion runs per node except
+// where the FP64 state is read or written.
 #pragma once
 
 #include "dg_device.cuh"
@@ -31,70 +37,154 @@ __host__ __device__ constexpr int max_threads_for(int P) {
   return P == 1 ? 256 : P <= 4 ? 512 : P == 5 ? 448 : P == 6 ? 352 : P == 7 ? 512 : 736;
 }
 
+// Mesh, basis and physics constants in the operator precision T.
+template <typename T>
+struct OpConst {
+  int K, E, nel;
+  long long N;
+  T gm1, rho_ref, theta_ref, Hc;  // reference-shifted state (zero references in FP64)
+  T s2h;                          // 2 / h
+  T winv;                         // 1 / w_0 = 1 / w_P
+  T mu, lam, csd2, lam_t;         // transport
+  int les;
+  double drho_ref, dE_ref;        // references for shifting the FP64 state
+  T D[kMaxN1 * kMaxN1];
+};
+
 __device__ __forceinline__ int neighbour_elem(int e, int K, int d, int shift) {
   int c[3] = {e % K, (e / K) % K, e / (K * K)};
   c[d] = (c[d] + shift + K) % K;
   return c[0] + K * (c[1] + K * c[2]);
 }
 
+// Node of face (d, side) with tangential index ab, at normal index m.
+template <int P>
+__device__ __forceinline__ int face_node(int d, int m, int ab) {
+  constexpr int n = P + 1;
+  const int a = ab % n, b = ab / n;
+  return d == 0 ? m + n * (a + n * b) : d == 1 ? a + n * (m + n * b) : a + n * (b + n * m);
+}
+
+// Tangential index of node (i, j, k) on a face normal to d.
+template <int P>
+__device__ __forceinline__ int face_ab(int d, const int idx[3]) {
+  constexpr int n = P + 1;
+  return d == 0 ? idx[1] + n * idx[2] : d == 1 ? idx[0] + n * idx[2] : idx[0] + n * idx[1];
+}
+
+// Neighbour element table of the block: nb[6 le + 2 d + side], side 1 = +d, side 0 = -d.
+__device__ __forceinline__ void fill_neighbours(int* nb, int e0, int E, int K, int nel) {
+  for (int t = threadIdx.x; t < 6 * E; t += blockDim.x) {
+    const int e = e0 + t / 6, f = t % 6;
+    nb[t] = (e < nel) ? neighbour_elem(e, K, f >> 1, (f & 1) ? 1 : -1) : 0;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ Prim<T> prim_c(const T s[5], const OpConst<T>& C) {
+  return primitives(s, C.rho_ref, C.gm1);
+}
+
 // Stage state of node gi.  SRC 0: from the FP64 state q; SRC 1: qn32 + dlt (FP32).
 template <typename T, int SRC>
 __device__ __forceinline__ void stage_state(const double* __restrict__ q, const float* __restrict__ qn32,
-                                            const float* __restrict__ dlt, long long N, long long gi, const Phys& ph,
-                                            T s[5]) {
+                                            const float* __restrict__ dlt, long long N, long long gi,
+                                            const OpConst<T>& C, T s[5]) {
   if (SRC == 0) {
     double qd[5];
 #pragma unroll
     for (int v = 0; v < 5; ++v) qd[v] = q[v * N + gi];
-    shift_state<T>(qd, ph, s);
+    s[0] = from_double<T>(qd[0] - C.drho_ref);
+    s[1] = from_double<T>(qd[1]);
+    s[2] = from_double<T>(qd[2]);
+    s[3] = from_double<T>(qd[3]);
+    s[4] = from_double<T>(qd[4] - C.dE_ref);
   } else {
 #pragma unroll
     for (int v = 0; v < 5; ++v) s[v] = T(qn32[v * N + gi] + dlt[v * N + gi]);
   }
 }
 
+// Effective viscosity and heat coefficient (Smagorinsky when les != 0).
+template <typename T>
+__device__ __forceinline__ void transport_c(const OpConst<T>& C, T rho, const T G[3][4], T* mu, T* lam) {
+  T m = C.mu, l = C.lam;
+  if (C.les) {
+    T ss = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const T s = T(0.5) * (G[b][a] + G[a][b]);
+        ss += s * s;
+      }
+    const T mut = rho * C.csd2 * dsqrt(T(2) * ss);
+    m += mut;
+    l += mut * C.lam_t;
+  }
+  *mu = m;
+  *lam = l;
+}
+
 template <int P, typename T, int SRC>
 __global__ void __launch_bounds__(max_threads_for(P))
 k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, const float* __restrict__ dlt,
-           T* __restrict__ qf, float* __restrict__ qn32_out, T* __restrict__ vis, Geom geom, Phys ph) {
+           T* __restrict__ qf, float* __restrict__ qn32_out, T* __restrict__ vis, const OpConst<T> C) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sD = reinterpret_cast<T*>(smem_raw);
-  T* sU = sD + n2;
-  const int E = geom.E;
+  const int E = C.E;
   const int tileN = E * np;
-  for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = T(geom.D[t]);
+  const int haloN = E * 6 * n2;
+  T* sD = reinterpret_cast<T*>(smem_raw);
+  T* sU = sD + n2;            // [4][E np]
+  T* sH = sU + 4 * tileN;     // [4][E 6 n2]: neighbours' gradient variables on each face
+  int* nb = reinterpret_cast<int*>(sH + 4 * haloN);
+  const int e0 = blockIdx.x * E;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
+  fill_neighbours(nb, e0, E, C.K, C.nel);
 
   const int le = threadIdx.x / np;
   const int node = threadIdx.x - le * np;
-  const int e = blockIdx.x * E + le;
-  const bool active = (le < E) && (e < geom.nel);
-  const long long N = geom.N;
+  const int e = e0 + le;
+  const bool active = (le < E) && (e < C.nel);
+  const long long N = C.N;
   const long long gi = (long long)e * np + node;
-  const T gm1 = T(ph.gamma - 1.0), rho_ref = T(ph.rho_ref), th_ref = T(ph.theta_ref);
 
   T s[5], U[4];
   Prim<T> w;
   if (active) {
-    stage_state<T, SRC>(q, qn32_in, dlt, N, gi, ph, s);
+    stage_state<T, SRC>(q, qn32_in, dlt, N, gi, C, s);
 #pragma unroll
     for (int v = 0; v < 5; ++v) qf[v * N + gi] = s[v];
     if (SRC == 0 && qn32_out != nullptr) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) qn32_out[v * N + gi] = float(s[v]);
     }
-    w = primitives(s, rho_ref, gm1);
-    gradient_vars(s, w, th_ref, U);
+    w = prim_c(s, C);
+    gradient_vars(s, w, C.theta_ref, U);
 #pragma unroll
     for (int a = 0; a < 4; ++a) sU[a * tileN + le * np + node] = U[a];
+  }
+  __syncthreads();  // neighbour table
+  // halo: gradient variables of the neighbours' face nodes
+  for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
+    const int ab = t % n2, f = (t / n2) % 6, hl = t / (6 * n2);
+    if (e0 + hl >= C.nel) continue;
+    const int d = f >> 1, side = f & 1;
+    const long long gnb = (long long)nb[6 * hl + f] * np + face_node<P>(d, side ? 0 : P, ab);
+    T sn[5], Un[4];
+    stage_state<T, SRC>(q, qn32_in, dlt, N, gnb, C, sn);
+    const Prim<T> wn = prim_c(sn, C);
+    gradient_vars(sn, wn, C.theta_ref, Un);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) sH[a * haloN + t] = Un[a];
   }
   __syncthreads();
   if (!active) return;
 
   const int idx[3] = {node % n, (node / n) % n, node / n2};
   const int stride[3] = {1, n, n2};
-  const T s2h = T(geom.two_over_h);
-  const T lift = s2h * T(geom.winv) * T(0.5);
+  const T lift = C.s2h * C.winv * T(0.5);
   T G[3][4];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -105,25 +195,20 @@ k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, cons
       T acc = T(0);
 #pragma unroll
       for (int m = 0; m < n; ++m) acc += Drow[m] * sU[a * tileN + base + m * stride[d]];
-      G[d][a] = s2h * acc;
+      G[d][a] = C.s2h * acc;
     }
     // interface lifting with the central U^ = (U + U_nb) / 2
     const bool right = (idx[d] == P), left = (idx[d] == 0);
     if (right || left) {
-      const int enb = neighbour_elem(e, geom.K, d, right ? 1 : -1);
-      const long long gnb = (long long)enb * np + node + (right ? -P : P) * stride[d];
-      T sn[5], Un[4];
-      stage_state<T, SRC>(q, qn32_in, dlt, N, gnb, ph, sn);
-      const Prim<T> wn = primitives(sn, rho_ref, gm1);
-      gradient_vars(sn, wn, th_ref, Un);
+      const int h = (le * 6 + 2 * d + (right ? 1 : 0)) * n2 + face_ab<P>(d, idx);
       const T sgn = right ? lift : -lift;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) G[d][a] += sgn * (Un[a] - U[a]);
+      for (int a = 0; a < 4; ++a) G[d][a] += sgn * (sH[a * haloN + h] - U[a]);
     }
   }
 
   T mu, lam;
-  transport(ph, w.rho, G, &mu, &lam);
+  transport_c(C, w.rho, G, &mu, &lam);
   const T div = G[0][0] + G[1][1] + G[2][2];
   const T t23 = T(2.0 / 3.0) * mu * div;
   // G[d][a] = d u_a / d x_d, tau_ab = mu (du_a/dx_b + du_b/dx_a) - 2/3 mu div delta_ab
@@ -141,46 +226,137 @@ k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, cons
   for (int c = 0; c < 9; ++c) vis[c * N + gi] = out[c];
 }
 
-// Per-launch RK data of phase B.
+// Per-launch RK data of phase B in the arithmetic of the update.
+template <typename R>
 struct RkArgs {
-  double A, B, dt;   // Williamson coefficients of the stage and the step size
-  double invB1;      // 1 / B of stage 1 (the FP32 increment scheme recovers g1 = dlt1 / B1)
+  R A, B, dt;   // Williamson coefficients of the stage and the step size
+  R invB1;      // 1 / B of stage 1 (the FP32 increment scheme recovers g1 = dlt1 / B1)
 };
 
-// MODE 0: dqdt = R.  MODE 1: FP64 RK stage (g = A g + dt R; q += B g, register GT).
+constexpr int kHaloComponents = 14;  // stage state (5) and viscous quantities (9)
+
+// One interface work item normal to D (compile-time, so flux arrays stay in registers):
+//   F* - F = (f_nb - f_own - diss)/2 + (f^nu_own - f^nu_nb)/2, lifted with -/+ (2/h)/w on
+// the right / left face; diss = |A~|(q_R - q_L) in the face's left/right order.
+// own: own node's 14 components at stride `ostride`; nbr: the neighbour's at stride `hstride`;
+// out: 5 results at stride `hstride`.
+template <int D, typename T>
+__device__ __forceinline__ void interface_item(const T* own, int ostride, const T* nbr, T* out, int hstride,
+                                               int side, const OpConst<T>& C) {
+  T so[5], vo[9], sn[5], vn[9];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) so[v] = own[v * ostride];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) vo[c] = own[(5 + c) * ostride];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) sn[v] = nbr[v * hstride];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) vn[c] = nbr[(5 + c) * hstride];
+  const Prim<T> wo = primitives(so, C.rho_ref, C.gm1), wn = primitives(sn, C.rho_ref, C.gm1);
+  T fo[5], fnb[5], fvo[5], fvn[5], diss[5];
+  euler_flux(so, wo, C.Hc, D, fo);
+  euler_flux(sn, wn, C.Hc, D, fnb);
+  if (side) roe_dissipation(so, wo, sn, wn, D, C.gm1, C.Hc, diss);
+  else roe_dissipation(sn, wn, so, wo, D, C.gm1, C.Hc, diss);
+  viscous_flux(vo, wo.v, D, fvo);
+  viscous_flux(vn, wn.v, D, fvn);
+  const T lift = C.s2h * C.winv;
+  const T sgn = side ? -lift : lift;
+  if (sizeof(T) == 8) {
+    // FP64 parity path: the plain form, F* assembled first and F subtracted after
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const T fstar = T(0.5) * (fo[c] + fnb[c] - diss[c]) - T(0.5) * (fvo[c] + fvn[c]);
+      out[c * hstride] = sgn * (fstar - (fo[c] - fvo[c]));
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c)
+      out[c * hstride] = sgn * (T(0.5) * (fnb[c] - fo[c] - diss[c]) + T(0.5) * (fvo[c] - fvn[c]));
+  }
+}
+
+// MODE 0: dqdt = R.  MODE 1: FP64 RK stage (g = A g + dt R; q += B g).
 // MODES 2, 3, 4: FP32 increment scheme, stages 1, 2, 3.
-template <int P, typename T, int MODE, typename GT>
+template <int P, typename T, int MODE>
 __global__ void __launch_bounds__(max_threads_for(P))
 k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ vis, double* __restrict__ dqdt,
-       GT* __restrict__ greg, float* __restrict__ dlt, Forcing fc, Geom geom, Phys ph, RkArgs rk) {
+       T* __restrict__ greg, float* __restrict__ dlt, Forcing fc, const OpConst<T> C, RkArgs<T> rk) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
+  constexpr int HC = kHaloComponents;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sD = reinterpret_cast<T*>(smem_raw);
-  T* sF = sD + n2;
-  const int E = geom.E;
+  const int E = C.E;
   const int tileN = E * np;
-  for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = T(geom.D[t]);
+  const int haloN = E * 6 * n2;
+  T* sD = reinterpret_cast<T*>(smem_raw);
+  T* sF = sD + n2;             // [5][E np]  volume fluxes of one direction
+  T* sO = sF + 5 * tileN;      // [14][E np] own stage state and viscous quantities
+  T* sH = sO + HC * tileN;     // [14][E 6 n2] neighbours' face data
+  T* sS = sH + HC * haloN;     // [5][E 6 n2] lifted interface terms
+  int* nb = reinterpret_cast<int*>(sS + 5 * haloN);
+  const int e0 = blockIdx.x * E;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
+  fill_neighbours(nb, e0, E, C.K, C.nel);
 
   const int le = threadIdx.x / np;
   const int node = threadIdx.x - le * np;
-  const int e = blockIdx.x * E + le;
-  const bool active = (le < E) && (e < geom.nel);
-  const long long N = geom.N;
+  const int e = e0 + le;
+  const bool active = (le < E) && (e < C.nel);
+  const long long N = C.N;
   const long long gi = (long long)e * np + node;
-  const T gm1 = T(ph.gamma - 1.0), rho_ref = T(ph.rho_ref), Hc = T(ph.Hc);
 
+  // own loads first (all independent), the RK operands with them
   T s[5], vs[9];
-  Prim<T> w;
+  T gold[5], dold[5];
   if (active) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) s[v] = qf[v * N + gi];
 #pragma unroll
     for (int c = 0; c < 9; ++c) vs[c] = vis[c * N + gi];
-    w = primitives(s, rho_ref, gm1);
+    if (MODE == 3 || MODE == 4) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) dold[v] = T(dlt[v * N + gi]);
+    }
+    if (MODE == 4 || MODE == 1) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) gold[v] = (MODE == 1 && rk.A == T(0)) ? T(0) : greg[v * N + gi];
+    }
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sO[v * tileN + le * np + node] = s[v];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) sO[(5 + c) * tileN + le * np + node] = vs[c];
   }
+  __syncthreads();  // neighbour table
+  // halo: neighbours' stage state and viscous quantities on every face
+  for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
+    const int ab = t % n2, f = (t / n2) % 6, hl = t / (6 * n2);
+    if (e0 + hl >= C.nel) continue;
+    const int d = f >> 1, side = f & 1;
+    const long long gnb = (long long)nb[6 * hl + f] * np + face_node<P>(d, side ? 0 : P, ab);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sH[v * haloN + t] = qf[v * N + gnb];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) sH[(5 + c) * haloN + t] = vis[c * N + gnb];
+  }
+  __syncthreads();
+
+  // interface terms, one work item per (element, face, face node)
+  for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
+    const int ab = t % n2, f = (t / n2) % 6, hl = t / (6 * n2);
+    if (e0 + hl >= C.nel) continue;
+    const int side = f & 1;
+    const int m = side ? P : 0;
+    switch (f >> 1) {
+      case 0: interface_item<0>(sO + hl * np + face_node<P>(0, m, ab), tileN, sH + t, sS + t, haloN, side, C); break;
+      case 1: interface_item<1>(sO + hl * np + face_node<P>(1, m, ab), tileN, sH + t, sS + t, haloN, side, C); break;
+      default: interface_item<2>(sO + hl * np + face_node<P>(2, m, ab), tileN, sH + t, sS + t, haloN, side, C);
+    }
+  }
+
+  Prim<T> w;
+  if (active) w = prim_c(s, C);
   const int idx[3] = {node % n, (node / n) % n, node / n2};
   const int stride[3] = {1, n, n2};
-  const T s2h = T(geom.two_over_h);
   T R[5] = {T(0), T(0), T(0), T(0), T(0)};
 
   // volume term, one direction at a time through shared memory
@@ -188,7 +364,7 @@ k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ v
   for (int d = 0; d < 3; ++d) {
     if (active) {
       T F[5], fv[5];
-      euler_flux(s, w, Hc, d, F);
+      euler_flux(s, w, C.Hc, d, F);
       viscous_flux(vs, w.v, d, fv);
 #pragma unroll
       for (int c = 0; c < 5; ++c) sF[c * tileN + le * np + node] = F[c] - fv[c];
@@ -202,39 +378,21 @@ k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ v
         T acc = T(0);
 #pragma unroll
         for (int m = 0; m < n; ++m) acc += Drow[m] * sF[c * tileN + base + m * stride[d]];
-        R[c] -= s2h * acc;
+        R[c] -= C.s2h * acc;
       }
     }
     __syncthreads();
   }
   if (!active) return;
 
-  // interface fluxes and strong-form lifting
-  const T lift = s2h * T(geom.winv);
+  // add the lifted interface terms of this node's faces (fixed order x, y, z)
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const bool right = (idx[d] == P), left = (idx[d] == 0);
     if (!(right || left)) continue;
-    const int enb = neighbour_elem(e, geom.K, d, right ? 1 : -1);
-    const long long gnb = (long long)enb * np + node + (right ? -P : P) * stride[d];
-    T sn[5], vn[9];
+    const int h = (le * 6 + 2 * d + (right ? 1 : 0)) * n2 + face_ab<P>(d, idx);
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sn[v] = qf[v * N + gnb];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) vn[c] = vis[c * N + gnb];
-    const Prim<T> wn = primitives(sn, rho_ref, gm1);
-    T Fs[5], fvo[5], fvn[5], Fo[5];
-    if (right) roe_flux(s, w, sn, wn, d, gm1, Hc, Fs);
-    else roe_flux(sn, wn, s, w, d, gm1, Hc, Fs);
-    viscous_flux(vs, w.v, d, fvo);
-    viscous_flux(vn, wn.v, d, fvn);
-    euler_flux(s, w, Hc, d, Fo);
-    const T sgn = right ? -lift : lift;
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const T fstar = Fs[c] - T(0.5) * (fvo[c] + fvn[c]);
-      R[c] += sgn * (fstar - (Fo[c] - fvo[c]));
-    }
+    for (int c = 0; c < 5; ++c) R[c] += sS[c * haloN + h];
   }
 
   if (fc.s != nullptr) {
@@ -250,32 +408,30 @@ k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ v
 #pragma unroll
     for (int c = 0; c < 5; ++c) dqdt[c * N + gi] = double(R[c]);
   } else if (MODE == 1) {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      double gnew = rk.dt * double(R[c]);
-      if (rk.A != 0.0) gnew = fma(rk.A, double(greg[c * N + gi]), gnew);
-      const GT gst = GT(gnew);
-      greg[c * N + gi] = gst;
-      q[c * N + gi] = fma(rk.B, double(gst), q[c * N + gi]);
-    }
-  } else {
-    // FP32 increment scheme
-    const float dt = float(rk.dt), A = float(rk.A), B = float(rk.B);
+    // FP64 operator: plain 2N update of the FP64 state
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const long long o = c * N + gi;
-      const float r = float(R[c]);
+      T gnew = rk.dt * R[c];
+      if (rk.A != T(0)) gnew = rk.A * gold[c] + gnew;
+      greg[o] = gnew;
+      q[o] = double(rk.B) * double(gnew) + q[o];
+    }
+  } else {
+    // FP32 increment scheme
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const long long o = c * N + gi;
       if (MODE == 2) {
-        dlt[o] = B * (dt * r);                       // g1 = dt R1; dlt1 = B1 g1
+        dlt[o] = float(rk.B * (rk.dt * R[c]));                 // g1 = dt R1; dlt1 = B1 g1
       } else if (MODE == 3) {
-        const float d1 = dlt[o];
-        const float g2 = A * (d1 * float(rk.invB1)) + dt * r;
-        greg[o] = GT(g2);
-        dlt[o] = d1 + B * g2;
+        const T g2 = rk.A * (dold[c] * rk.invB1) + rk.dt * R[c];
+        greg[o] = g2;
+        dlt[o] = float(dold[c] + rk.B * g2);
       } else {
-        const float g3 = A * float(greg[o]) + dt * r;
-        const float d3 = dlt[o] + B * g3;
-        q[o] = q[o] + f2d(d3);                     // once per step, in FP64
+        const T g3 = rk.A * gold[c] + rk.dt * R[c];
+        const float d3 = float(dold[c] + rk.B * g3);
+        q[o] = q[o] + f2d(d3);                                 // once per step, in FP64
       }
     }
   }

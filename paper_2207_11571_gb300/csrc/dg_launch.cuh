@@ -12,52 +12,89 @@ inline int block_threads(int P, int E) {
   return ((E * np + 31) / 32) * 32;
 }
 
+template <typename T>
+OpConst<T> make_const(const dg_ctx* c) {
+  OpConst<T> k;
+  k.K = c->K;
+  k.E = c->geom.E;
+  k.nel = c->nel;
+  k.N = c->N;
+  const Phys& ph = c->phys;
+  k.gm1 = T(ph.gamma - 1.0);
+  k.rho_ref = T(ph.rho_ref);
+  k.theta_ref = T(ph.theta_ref);
+  k.Hc = T(ph.Hc);
+  k.s2h = T(c->geom.two_over_h);
+  k.winv = T(c->geom.winv);
+  k.mu = T(ph.mu);
+  k.lam = T(ph.lam);
+  k.csd2 = T(ph.csd2);
+  k.lam_t = T(ph.lam_t);
+  k.les = ph.les;
+  k.drho_ref = ph.rho_ref;
+  k.dE_ref = ph.E_ref;
+  for (int i = 0; i < kMaxN1 * kMaxN1; ++i) k.D[i] = T(c->geom.D[i]);
+  return k;
+}
+
 template <typename K>
 cudaError_t set_smem(K kern, size_t smem) {
   if (smem > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaSuccess;
 }
 
+// Shared memory of the kernels (layouts in dg_kernels.cuh), including the neighbour table.
+template <int P, typename T>
+size_t gradient_smem(int E) {
+  constexpr int n = P + 1, n2 = n * n, np = n2 * n;
+  return sizeof(T) * (n2 + 4 * E * np + 4 * E * 6 * n2) + sizeof(int) * 6 * E;
+}
+
+template <int P, typename T>
+size_t flux_smem(int E) {
+  constexpr int n = P + 1, n2 = n * n, np = n2 * n;
+  constexpr int HC = kHaloComponents;
+  return sizeof(T) * (n2 + (5 + HC) * E * np + (HC + 5) * E * 6 * n2) + sizeof(int) * 6 * E;
+}
+
 template <int P, typename T, int SRC>
 cudaError_t gradient_p(const dg_ctx* c, const double* q, cudaStream_t st) {
-  constexpr int n = P + 1, np = n * n * n;
   const int E = c->geom.E;
-  const size_t smem = sizeof(T) * (n * n + 4 * E * np);
+  const size_t smem = gradient_smem<P, T>(E);
   auto kern = k_gradient<P, T, SRC>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = (c->nel + E - 1) / E;
   kern<<<grid, block_threads(P, E), smem, st>>>(q, c->qn32, c->dlt, static_cast<T*>(c->qf),
-                                                SRC == 0 ? c->qn32 : nullptr, static_cast<T*>(c->vis), c->geom,
-                                                c->phys);
+                                                SRC == 0 ? c->qn32 : nullptr, static_cast<T*>(c->vis),
+                                                make_const<T>(c));
   return cudaGetLastError();
 }
 
-template <int P, typename T, int MODE, typename GT>
-cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, const RkArgs& rk, cudaStream_t st) {
-  constexpr int n = P + 1, np = n * n * n;
+template <int P, typename T, int MODE>
+cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, const RkArgs<T>& rk,
+                   cudaStream_t st) {
   const int E = c->geom.E;
-  const size_t smem = sizeof(T) * (n * n + 5 * E * np);
-  auto kern = k_flux<P, T, MODE, GT>;
+  const size_t smem = flux_smem<P, T>(E);
+  auto kern = k_flux<P, T, MODE>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = (c->nel + E - 1) / E;
   kern<<<grid, block_threads(P, E), smem, st>>>(q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt,
-                                                static_cast<GT*>(c->g), c->dlt, f, c->geom, c->phys, rk);
+                                                static_cast<T*>(c->g), c->dlt, f, make_const<T>(c), rk);
   return cudaGetLastError();
 }
 
 // FP64 operator: modes 0 (dq/dt) and 1 (FP64 RK stage).  FP32 operator: modes 0, 2, 3, 4.
 template <int P, typename T>
 cudaError_t flux_dispatch_mode(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode,
-                               const RkArgs& rk, cudaStream_t st) {
-  using GT = T;  // RK register in the operator precision
+                               const RkArgs<T>& rk, cudaStream_t st) {
   switch (mode) {
-    case 0: return flux_p<P, T, 0, GT>(c, q, dqdt, f, rk, st);
-    case 1: return flux_p<P, T, 1, GT>(c, q, dqdt, f, rk, st);
-    case 2: return flux_p<P, T, 2, GT>(c, q, dqdt, f, rk, st);
-    case 3: return flux_p<P, T, 3, GT>(c, q, dqdt, f, rk, st);
-    case 4: return flux_p<P, T, 4, GT>(c, q, dqdt, f, rk, st);
+    case 0: return flux_p<P, T, 0>(c, q, dqdt, f, rk, st);
+    case 1: return flux_p<P, T, 1>(c, q, dqdt, f, rk, st);
+    case 2: return flux_p<P, T, 2>(c, q, dqdt, f, rk, st);
+    case 3: return flux_p<P, T, 3>(c, q, dqdt, f, rk, st);
+    case 4: return flux_p<P, T, 4>(c, q, dqdt, f, rk, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -89,8 +126,9 @@ cudaError_t gradient_t(const dg_ctx* c, const double* q, int src, cudaStream_t s
 }
 
 template <typename T>
-cudaError_t flux_t(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, const RkArgs& rk,
-                   cudaStream_t st) {
+cudaError_t flux_t(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                   double dt, double invB1, cudaStream_t st) {
+  const RkArgs<T> rk{T(A), T(B), T(dt), T(invB1)};
 #define DG_F(PP) flux_dispatch_mode<PP, T>(c, q, dqdt, f, mode, rk, st)
   DG_FOR_EACH_P(DG_F)
 #undef DG_F

@@ -9,6 +9,7 @@
 
 #include "../../include/dgnn_nn.h"
 #include "dg_common.h"
+#include "dg_device.cuh"
 #include "nn_bridge.h"
 #include "nn_gemm.h"
 
@@ -40,6 +41,12 @@ struct nn_model {
   double* loss_host = nullptr;  // pinned
   int* err = nullptr;           // device error flag of the tensor-core kernels
   int maxdim = 0;
+  // input means for scaling network inputs taken from solver states: in FP64 (FP64 state)
+  // and shifted by the reference state of an FP32 context (cached for one reference)
+  double* mean_in_d = nullptr;
+  float* mean_shift = nullptr;
+  double shift_rho = -1.0, shift_E = -1.0;
+  std::vector<float> h_mean_in;
 };
 
 namespace dgnn {
@@ -70,7 +77,7 @@ __global__ void k_prep_features(const float* __restrict__ X, const int64_t* __re
 
 // act0[e][slot * np + node] from the FP64 state q[var][elem][node] of elements e0 .. e0 + rows.
 __global__ void k_prep_state(const double* __restrict__ q, long long N, int np, int first_var, int n_vars, int e0,
-                             int rows, int ld, const float* __restrict__ mean, const float* __restrict__ sd,
+                             int rows, int ld, const double* __restrict__ mean, const float* __restrict__ sd,
                              bf16* __restrict__ out) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)rows * ld) return;
@@ -79,26 +86,24 @@ __global__ void k_prep_state(const double* __restrict__ q, long long N, int np, 
   if (f < n_vars * np) {
     const int slot = f / np, node = f - slot * np;
     const double x = q[(long long)(first_var + slot) * N + (long long)(e0 + r) * np + node];
-    v = ((float)x - mean[f]) / sd[f];
+    v = d2f_rn(x - mean[f]) / sd[f];   // difference before rounding: near-constant features keep their digits
   }
   out[t] = __float2bfloat16_rn(v);
 }
 
-// Same from the FP32 reference-shifted stage state qf[var][elem][node] of an FP32 context.
+// Same from the FP32 reference-shifted stage state qf[var][elem][node] of an FP32 context;
+// mshift = mean - reference, formed on the host in FP64.
 __global__ void k_prep_state_f32(const float* __restrict__ qf, long long N, int np, int first_var, int n_vars, int e0,
-                                 int rows, int ld, float rho_ref, float E_ref, const float* __restrict__ mean,
-                                 const float* __restrict__ sd, bf16* __restrict__ out) {
+                                 int rows, int ld, const float* __restrict__ mshift, const float* __restrict__ sd,
+                                 bf16* __restrict__ out) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)rows * ld) return;
   const int r = (int)(t / ld), f = (int)(t - (long long)r * ld);
   float v = 0.f;
   if (f < n_vars * np) {
     const int slot = f / np, node = f - slot * np;
-    const int var = first_var + slot;
-    float x = qf[(long long)var * N + (long long)(e0 + r) * np + node];
-    if (var == 0) x += rho_ref;
-    if (var == 4) x += E_ref;
-    v = (x - mean[f]) / sd[f];
+    const float x = qf[(long long)(first_var + slot) * N + (long long)(e0 + r) * np + node];
+    v = (x - mshift[f]) / sd[f];
   }
   out[t] = __float2bfloat16_rn(v);
 }
@@ -295,6 +300,7 @@ void free_model(nn_model* m) {
   cudaFree(m->mean_in); cudaFree(m->std_in); cudaFree(m->mean_out); cudaFree(m->std_out);
   cudaFree(m->y); cudaFree(m->dy); cudaFree(m->dx); cudaFree(m->dyb); cudaFree(m->dyT);
   cudaFree(m->loss_part); cudaFree(m->loss_dev); cudaFree(m->err);
+  cudaFree(m->mean_in_d); cudaFree(m->mean_shift);
   if (m->loss_host) cudaFreeHost(m->loss_host);
   delete m;
 }
@@ -351,6 +357,8 @@ int alloc_model(const nn_desc* d, nn_model** out) {
   A((void**)&m->dx, B * m->maxdim * 4);
   A((void**)&m->dyb, B * round_up(m->maxdim, 64) * 2);
   A((void**)&m->dyT, (size_t)m->maxdim * m->bpad * 2);
+  A((void**)&m->mean_in_d, d->n_in * 8);
+  A((void**)&m->mean_shift, d->n_in * 4);
   A((void**)&m->loss_part, kLossBlocks * 8);
   A((void**)&m->loss_dev, 8);
   A((void**)&m->err, 4);
@@ -362,7 +370,34 @@ int alloc_model(const nn_desc* d, nn_model** out) {
   std::vector<float> ones(std::max(d->n_in, d->n_out), 1.f);
   cudaMemcpy(m->std_in, ones.data(), d->n_in * 4, cudaMemcpyHostToDevice);
   cudaMemcpy(m->std_out, ones.data(), d->n_out * 4, cudaMemcpyHostToDevice);
+  m->h_mean_in.assign(d->n_in, 0.f);
   *out = m;
+  return DG_OK;
+}
+
+// After the input means change: refresh their FP64 device copy and drop the shifted cache.
+int means_changed(nn_model* m) {
+  m->h_mean_in.resize(m->d.n_in);
+  DG_CUDA(cudaMemcpy(m->h_mean_in.data(), m->mean_in, m->d.n_in * 4, cudaMemcpyDeviceToHost));
+  std::vector<double> md(m->h_mean_in.begin(), m->h_mean_in.end());
+  DG_CUDA(cudaMemcpy(m->mean_in_d, md.data(), m->d.n_in * 8, cudaMemcpyHostToDevice));
+  m->shift_rho = m->shift_E = -1.0;
+  return DG_OK;
+}
+
+// Means shifted by the reference state of an FP32 context (rho - rho_ref, rho e - E_ref).
+int ensure_shift(nn_model* m, const dg_ctx* c) {
+  if (m->shift_rho == c->phys.rho_ref && m->shift_E == c->phys.E_ref) return DG_OK;
+  const int np = c->np;
+  std::vector<float> sh(m->d.n_in);
+  for (int f = 0; f < m->d.n_in; ++f) {
+    const int var = m->d.first_var + f / np;
+    const double ref = var == 0 ? c->phys.rho_ref : var == 4 ? c->phys.E_ref : 0.0;
+    sh[f] = (float)((double)m->h_mean_in[f] - ref);
+  }
+  DG_CUDA(cudaMemcpy(m->mean_shift, sh.data(), m->d.n_in * 4, cudaMemcpyHostToDevice));
+  m->shift_rho = c->phys.rho_ref;
+  m->shift_E = c->phys.E_ref;
   return DG_OK;
 }
 
@@ -387,13 +422,14 @@ int nn_forcing_on_state(const nn_model* m, const dg_ctx* c, const double* q, flo
     const long long tot = (long long)rows * m->pad[0];
     if (c->opts.precision == DG_PREC_FP32) {
       // the stage state of the FP32 operator is the reference-shifted copy written by phase A
+      int rc = ensure_shift(const_cast<nn_model*>(m), c);
+      if (rc) return rc;
       k_prep_state_f32<<<blocks_for(tot, 256), 256, 0, st>>>(static_cast<const float*>(c->qf), c->N, c->np,
                                                              m->d.first_var, m->d.n_vars, e0, rows, m->pad[0],
-                                                             (float)c->phys.rho_ref, (float)c->phys.E_ref,
-                                                             m->mean_in, m->std_in, m->act[0]);
+                                                             m->mean_shift, m->std_in, m->act[0]);
     } else {
       k_prep_state<<<blocks_for(tot, 256), 256, 0, st>>>(q, c->N, c->np, m->d.first_var, m->d.n_vars, e0, rows,
-                                                         m->pad[0], m->mean_in, m->std_in, m->act[0]);
+                                                         m->pad[0], m->mean_in_d, m->std_in, m->act[0]);
     }
     DG_CUDA(cudaGetLastError());
     int rc = forward_layers(m, rows, s + (long long)e0 * feat, st);
@@ -463,7 +499,7 @@ int nn_set_scalers(nn_model* m, const float* mi, const float* si, const float* m
   DG_CUDA(cudaMemcpy(m->std_in, si, m->d.n_in * 4, cudaMemcpyHostToDevice));
   DG_CUDA(cudaMemcpy(m->mean_out, mo, m->d.n_out * 4, cudaMemcpyHostToDevice));
   DG_CUDA(cudaMemcpy(m->std_out, so, m->d.n_out * 4, cudaMemcpyHostToDevice));
-  return DG_OK;
+  return means_changed(m);
 }
 
 int nn_get_scalers(const nn_model* m, float* mi, float* si, float* mo, float* so) {
@@ -508,7 +544,7 @@ int nn_compute_scalers(nn_model* m, const float* X, const float* Y, int64_t rows
     DG_CUDA(cudaMemcpy(which ? m->mean_out : m->mean_in, mean.data(), n * 4, cudaMemcpyHostToDevice));
     DG_CUDA(cudaMemcpy(which ? m->std_out : m->std_in, sd.data(), n * 4, cudaMemcpyHostToDevice));
   }
-  return DG_OK;
+  return means_changed(m);
 }
 
 int nn_forward(const nn_model* m, const float* X, float* S, int rows, void* stream) {
@@ -776,6 +812,8 @@ extern "C" int nn_load(const char* path, int max_batch, nn_model** out) {
     if (rc) { free_model(m); return rc; }
   }
   DG_CUDA(cudaDeviceSynchronize());
+  rc = means_changed(m);
+  if (rc) { free_model(m); return rc; }
   *out = m;
   return DG_OK;
 }

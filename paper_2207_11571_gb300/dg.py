@@ -66,6 +66,7 @@ _SIGS = {
     "dg_stable_dt": [_P, _P, _D, ctypes.POINTER(_D), _P],
     "dg_make_pairs": [_P, _P, _P, _P, _D, _I, _I, _P, _P, _P],
     "dg_check_conversions": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P],
+    "dg_autotune": [_P, _P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P],
     "dg_profile_rk3": [_P, _P, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I),
                        ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D), _P],
 }
@@ -249,6 +250,15 @@ def dg_profile_rk3(ctx, q, dt, nsteps=1, stream=None):
                                ctypes.byref(gb), stream_ptr(stream)))
     return {"ms_gradient": tg.value, "ms_flux": tf.value, "launches_gradient": lg.value,
             "launches_flux": lf.value, "flux_bytes_per_launch": fb.value, "gradient_bytes_per_launch": gb.value}
+
+
+def dg_autotune(ctx, q, dt, stream=None):
+    """Picks the fastest elements-per-block for the context; returns (E, ms per RK3 step)."""
+    _check_state(ctx, q, "q")
+    E, ms = ctypes.c_int(), ctypes.c_double()
+    check(lib().dg_autotune(ctypes.c_void_p(ctx), ptr(q), float(dt), ctypes.byref(E), ctypes.byref(ms),
+                            stream_ptr(stream)))
+    return E.value, ms.value
 
 
 def dg_check_conversions(x, stream=None):

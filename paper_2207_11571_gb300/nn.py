@@ -170,11 +170,13 @@ def nn_load(path, max_batch=4096):
     return h.value
 
 
-def nn_gemm_bf16(A, B, bias=None, relu=False, stream=None):
-    """C = A B^T (+ bias, ReLU) for bf16 CUDA tensors A (M x K) and B (N x K); returns float32 C."""
+def nn_gemm_bf16(A, B, bias=None, relu=False, K=None, stream=None):
+    """C = A[:, :K] B[:, :K]^T (+ bias, ReLU) for row-major bf16 CUDA tensors A (M x lda) and
+    B (N x ldb); K defaults to A's width.  Returns float32 C (M x N)."""
     import torch
     dg = _dg()
-    M, K = A.shape
+    M = A.shape[0]
+    K = A.shape[1] if K is None else int(K)
     N = B.shape[0]
     C = torch.empty((M, N), dtype=torch.float32, device=A.device)
     dg.check(dg.lib().nn_gemm_bf16(M, N, K, dg.ptr(A), A.stride(0), dg.ptr(B), B.stride(0), dg.ptr(bias),

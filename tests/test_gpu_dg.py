@@ -69,7 +69,7 @@ class Ctx:
 
 CASES = [  # K, P, les, elems_per_block (0 = default)
     (4, 3, False, 0), (4, 3, True, 0), (3, 3, False, 4),   # 27 elements in blocks of 4: ragged tail
-    (3, 2, True, 0), (3, 6, False, 0), (2, 8, True, 0), (1, 3, False, 0), (2, 1, False, 0), (2, 5, False, 2),
+    (3, 2, True, 0), (3, 6, False, 0), (2, 8, True, 0), (1, 3, False, 0), (3, 1, False, 0), (2, 5, False, 2),
 ]
 
 
@@ -90,7 +90,8 @@ def test_rhs_fp64_matches_oracle_on_tgv(dg, K, P, les, E):
     assert err < 1e-12, err
 
 
-@pytest.mark.parametrize("K,P,les,E", [(3, 3, True, 4), (2, 6, False, 0), (2, 2, True, 0), (1, 4, True, 0)])
+@pytest.mark.parametrize("K,P,les,E", [(3, 3, True, 4), (2, 6, False, 0), (2, 2, True, 0), (1, 4, True, 0),
+                                       (3, 1, False, 1), (3, 1, False, 8), (3, 1, True, 32)])
 def test_rhs_fp64_matches_oracle_on_rough_state(dg, K, P, les, E):
     """Random per-node states (every interface jumps): exercises Roe and BR1 face terms."""
     c = Ctx(dg, K, P, Re=50.0, Mach=0.3, les=les, elems_per_block=E)
