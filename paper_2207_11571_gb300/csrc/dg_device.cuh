@@ -12,12 +12,23 @@
 
 namespace dgnn {
 
+// Square root and reciprocal of positive arguments.  FP64: IEEE.  FP32 operator: the
+// approximate hardware intrinsics (a few ulp), far below the FP32 operator's own
+// rounding of the fluxes; they replace the multi-instruction IEEE sequences in the
+// Roe flux and the primitive variables.
 template <typename T>
 __device__ __forceinline__ T dsqrt(T x);
 template <>
-__device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+__device__ __forceinline__ float dsqrt<float>(float x) { return x * rsqrtf(x); }
 template <>
 __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ T drcp(T x);
+template <>
+__device__ __forceinline__ float drcp<float>(float x) { return __fdividef(1.0f, x); }
+template <>
+__device__ __forceinline__ double drcp<double>(double x) { return 1.0 / x; }
 
 // ---------------------------------------------------------------- conversions
 // FP64 <-> FP32 by IEEE 754 bit manipulation on the integer pipe.  On GB300 the FP64
@@ -75,7 +86,7 @@ template <typename T>
 __device__ __forceinline__ Prim<T> primitives(const T s[5], T rho_ref, T gm1) {
   Prim<T> w;
   w.rho = s[0] + rho_ref;
-  w.ir = T(1) / w.rho;
+  w.ir = drcp(w.rho);
   w.v[0] = s[1] * w.ir;
   w.v[1] = s[2] * w.ir;
   w.v[2] = s[3] * w.ir;
@@ -129,7 +140,7 @@ __device__ __forceinline__ void roe_dissipation(const T sL[5], const Prim<T>& wL
                                                 int d, T gm1, T Hc, T diss[5]) {
   const T HL = (sL[4] + wL.pp + Hc) * wL.ir, HR = (sR[4] + wR.pp + Hc) * wR.ir;
   const T sqL = dsqrt(wL.rho), sqR = dsqrt(wR.rho);
-  const T wden = T(1) / (sqL + sqR);
+  const T wden = drcp(sqL + sqR);
   const T ut[3] = {(sqL * wL.v[0] + sqR * wR.v[0]) * wden, (sqL * wL.v[1] + sqR * wR.v[1]) * wden,
                    (sqL * wL.v[2] + sqR * wR.v[2]) * wden};
   const T Ht = (sqL * HL + sqR * HR) * wden;
@@ -141,7 +152,7 @@ __device__ __forceinline__ void roe_dissipation(const T sL[5], const Prim<T>& wL
   const T dr = sR[0] - sL[0], dp = wR.pp - wL.pp;
   const T du[3] = {wR.v[0] - wL.v[0], wR.v[1] - wL.v[1], wR.v[2] - wL.v[2]};
   const T dVn = du[d];
-  const T inv2c2 = T(0.5) / c2;
+  const T inv2c2 = T(0.5) * drcp(c2);
   const T a1 = (dp - rt * c * dVn) * inv2c2;
   const T a2 = dr - dp * (T(2) * inv2c2);
   const T a5 = (dp + rt * c * dVn) * inv2c2;

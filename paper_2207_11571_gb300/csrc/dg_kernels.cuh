@@ -19,13 +19,13 @@
 // Each CUDA block owns E consecutive elements, one thread per node for the nodal work.
 // At kernel start the block issues all its global loads: its own nodes into registers
 // and a halo (the neighbours' face nodes of all six faces of its elements) into shared
-// memory.  The interface fluxes are then computed as dense work items, one per
-// (element, face, face node), so that every lane of a warp does useful Roe work (with
-// one thread per node, each warp would walk all three face directions at half
-// occupancy); node threads add the lifted results in a fixed order.  The 1D derivative
-// contractions read element tiles in shared memory.  All constants arrive in the
-// operator precision (OpConst): no FP64 arithmetic or conversion runs per node except
-// where the FP64 state is read or written.
+// memory.  Interface fluxes are dense work items, one per (element, face, face node),
+// so that every lane does useful Roe work; items are ordered (face node, side,
+// direction, element) so that a warp shares one face direction and every index divisor
+// is a compile-time constant.  Node threads add the lifted results in a fixed order.
+// The 1D derivative contractions read element tiles in shared memory.  All constants
+// arrive in the operator precision (OpConst): no FP64 arithmetic or conversion runs per
+// node except where the FP64 state is read or written.
 #pragma once
 
 #include "dg_device.cuh"
@@ -51,13 +51,37 @@ struct OpConst {
   T D[kMaxN1 * kMaxN1];
 };
 
-__device__ __forceinline__ int neighbour_elem(int e, int K, int d, int shift) {
-  int c[3] = {e % K, (e / K) % K, e / (K * K)};
-  c[d] = (c[d] + shift + K) % K;
-  return c[0] + K * (c[1] + K * c[2]);
+// Element coordinates of the first element of the block (one set of divisions per thread).
+struct BlockCoords {
+  int x, y, z;
+};
+
+__device__ __forceinline__ BlockCoords block_coords(int e0, int K) {
+  BlockCoords b;
+  b.x = e0 % K;
+  const int r = e0 / K;
+  b.y = r % K;
+  b.z = r / K;
+  return b;
 }
 
-// Node of face (d, side) with tangential index ab, at normal index m.
+// Element index of block element hl shifted by +/-1 along d (periodic), without division.
+__device__ __forceinline__ int neighbour_of(const BlockCoords& b, int hl, int K, int d, int shift) {
+  int x = b.x + hl, y = b.y, z = b.z;
+  while (x >= K) {
+    x -= K;
+    if (++y >= K) {
+      y = 0;
+      ++z;
+    }
+  }
+  if (d == 0) x = (x + shift + K) % K;
+  else if (d == 1) y = (y + shift + K) % K;
+  else z = (z + shift + K) % K;
+  return x + K * (y + K * z);
+}
+
+// Node of the face normal to d at normal index m with tangential index ab.
 template <int P>
 __device__ __forceinline__ int face_node(int d, int m, int ab) {
   constexpr int n = P + 1;
@@ -72,12 +96,29 @@ __device__ __forceinline__ int face_ab(int d, const int idx[3]) {
   return d == 0 ? idx[1] + n * idx[2] : d == 1 ? idx[0] + n * idx[2] : idx[0] + n * idx[1];
 }
 
-// Neighbour element table of the block: nb[6 le + 2 d + side], side 1 = +d, side 0 = -d.
-__device__ __forceinline__ void fill_neighbours(int* nb, int e0, int E, int K, int nel) {
-  for (int t = threadIdx.x; t < 6 * E; t += blockDim.x) {
-    const int e = e0 + t / 6, f = t % 6;
-    nb[t] = (e < nel) ? neighbour_elem(e, K, f >> 1, (f & 1) ? 1 : -1) : 0;
-  }
+// Halo / interface item t <-> (ab, side, d, hl), ab fastest, element slowest.
+template <int P>
+struct Item {
+  int ab, side, d, hl;
+};
+
+template <int P>
+__device__ __forceinline__ Item<P> item_of(int t) {
+  constexpr int n2 = (P + 1) * (P + 1);
+  Item<P> it;
+  it.ab = t % n2;
+  int r = t / n2;
+  it.side = r & 1;
+  r >>= 1;
+  it.d = r % 3;
+  it.hl = r / 3;
+  return it;
+}
+
+template <int P>
+__device__ __forceinline__ int item_index(int ab, int side, int d, int hl) {
+  constexpr int n2 = (P + 1) * (P + 1);
+  return ab + n2 * (side + 2 * (d + 3 * hl));
 }
 
 template <typename T>
@@ -118,7 +159,7 @@ __device__ __forceinline__ void transport_c(const OpConst<T>& C, T rho, const T 
         const T s = T(0.5) * (G[b][a] + G[a][b]);
         ss += s * s;
       }
-    const T mut = rho * C.csd2 * dsqrt(T(2) * ss);
+    const T mut = rho * C.csd2 * sqrt(T(2) * ss);  // IEEE square root: the argument may be zero
     m += mut;
     l += mut * C.lam_t;
   }
@@ -138,10 +179,9 @@ k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, cons
   T* sD = reinterpret_cast<T*>(smem_raw);
   T* sU = sD + n2;            // [4][E np]
   T* sH = sU + 4 * tileN;     // [4][E 6 n2]: neighbours' gradient variables on each face
-  int* nb = reinterpret_cast<int*>(sH + 4 * haloN);
   const int e0 = blockIdx.x * E;
+  const BlockCoords bc = block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
-  fill_neighbours(nb, e0, E, C.K, C.nel);
 
   const int le = threadIdx.x / np;
   const int node = threadIdx.x - le * np;
@@ -165,13 +205,12 @@ k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, cons
 #pragma unroll
     for (int a = 0; a < 4; ++a) sU[a * tileN + le * np + node] = U[a];
   }
-  __syncthreads();  // neighbour table
   // halo: gradient variables of the neighbours' face nodes
   for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
-    const int ab = t % n2, f = (t / n2) % 6, hl = t / (6 * n2);
-    if (e0 + hl >= C.nel) continue;
-    const int d = f >> 1, side = f & 1;
-    const long long gnb = (long long)nb[6 * hl + f] * np + face_node<P>(d, side ? 0 : P, ab);
+    const Item<P> it = item_of<P>(t);
+    if (e0 + it.hl >= C.nel) continue;
+    const int enb = neighbour_of(bc, it.hl, C.K, it.d, it.side ? 1 : -1);
+    const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
     T sn[5], Un[4];
     stage_state<T, SRC>(q, qn32_in, dlt, N, gnb, C, sn);
     const Prim<T> wn = prim_c(sn, C);
@@ -200,7 +239,7 @@ k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, cons
     // interface lifting with the central U^ = (U + U_nb) / 2
     const bool right = (idx[d] == P), left = (idx[d] == 0);
     if (right || left) {
-      const int h = (le * 6 + 2 * d + (right ? 1 : 0)) * n2 + face_ab<P>(d, idx);
+      const int h = item_index<P>(face_ab<P>(d, idx), right ? 1 : 0, d, le);
       const T sgn = right ? lift : -lift;
 #pragma unroll
       for (int a = 0; a < 4; ++a) G[d][a] += sgn * (sH[a * haloN + h] - U[a]);
@@ -233,33 +272,38 @@ struct RkArgs {
   R invB1;      // 1 / B of stage 1 (the FP32 increment scheme recovers g1 = dlt1 / B1)
 };
 
-constexpr int kHaloComponents = 14;  // stage state (5) and viscous quantities (9)
+// Halo and own-node components of an interface item: stage state (5) and the viscous
+// quantities entering the flux normal to the face (tau_0d, tau_1d, tau_2d, k theta_d).
+constexpr int kFaceComponents = 9;
+// Components of the own-element tile: stage state (5) and all viscous quantities (9);
+// the tile is reused for the three directions' volume fluxes (15).
+constexpr int kTileComponents = 15;
+
+// Column D of the viscous flux from the face-normal viscous quantities t4 = (tau_0D,
+// tau_1D, tau_2D, k theta_D): (0, tau_0D, tau_1D, tau_2D, v . tau_D + k theta_D).
+template <typename T>
+__device__ __forceinline__ void viscous_flux4(const T t4[4], const T v[3], T f[5]) {
+  f[0] = T(0);
+  f[1] = t4[0];
+  f[2] = t4[1];
+  f[3] = t4[2];
+  f[4] = v[0] * t4[0] + v[1] * t4[1] + v[2] * t4[2] + t4[3];
+}
 
 // One interface work item normal to D (compile-time, so flux arrays stay in registers):
 //   F* - F = (f_nb - f_own - diss)/2 + (f^nu_own - f^nu_nb)/2, lifted with -/+ (2/h)/w on
 // the right / left face; diss = |A~|(q_R - q_L) in the face's left/right order.
-// own: own node's 14 components at stride `ostride`; nbr: the neighbour's at stride `hstride`;
-// out: 5 results at stride `hstride`.
 template <int D, typename T>
-__device__ __forceinline__ void interface_item(const T* own, int ostride, const T* nbr, T* out, int hstride,
-                                               int side, const OpConst<T>& C) {
-  T so[5], vo[9], sn[5], vn[9];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) so[v] = own[v * ostride];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) vo[c] = own[(5 + c) * ostride];
-#pragma unroll
-  for (int v = 0; v < 5; ++v) sn[v] = nbr[v * hstride];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) vn[c] = nbr[(5 + c) * hstride];
+__device__ __forceinline__ void interface_item(const T so[5], const T to[4], const T sn[5], const T tn[4], T* out,
+                                               int ostride, int side, const OpConst<T>& C) {
   const Prim<T> wo = primitives(so, C.rho_ref, C.gm1), wn = primitives(sn, C.rho_ref, C.gm1);
   T fo[5], fnb[5], fvo[5], fvn[5], diss[5];
   euler_flux(so, wo, C.Hc, D, fo);
   euler_flux(sn, wn, C.Hc, D, fnb);
   if (side) roe_dissipation(so, wo, sn, wn, D, C.gm1, C.Hc, diss);
   else roe_dissipation(sn, wn, so, wo, D, C.gm1, C.Hc, diss);
-  viscous_flux(vo, wo.v, D, fvo);
-  viscous_flux(vn, wn.v, D, fvn);
+  viscous_flux4(to, wo.v, fvo);
+  viscous_flux4(tn, wn.v, fvn);
   const T lift = C.s2h * C.winv;
   const T sgn = side ? -lift : lift;
   if (sizeof(T) == 8) {
@@ -267,36 +311,41 @@ __device__ __forceinline__ void interface_item(const T* own, int ostride, const 
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
       const T fstar = T(0.5) * (fo[c] + fnb[c] - diss[c]) - T(0.5) * (fvo[c] + fvn[c]);
-      out[c * hstride] = sgn * (fstar - (fo[c] - fvo[c]));
+      out[c * ostride] = sgn * (fstar - (fo[c] - fvo[c]));
     }
   } else {
 #pragma unroll
     for (int c = 0; c < 5; ++c)
-      out[c * hstride] = sgn * (T(0.5) * (fnb[c] - fo[c] - diss[c]) + T(0.5) * (fvo[c] - fvn[c]));
+      out[c * ostride] = sgn * (T(0.5) * (fnb[c] - fo[c] - diss[c]) + T(0.5) * (fvo[c] - fvn[c]));
   }
 }
+
+// Index of viscous component i of the face-normal set of direction d in the 9-vector.
+__device__ __forceinline__ int face_vis_index(int d, int i) { return i < 3 ? sym_index(i, d) : 6 + d; }
+
+// Blocks per SM the flux kernel is compiled for (register budget): two at low order, so
+// that one block's barriers overlap another's work.
+__host__ __device__ constexpr int min_blocks_for(int P) { return P <= 6 ? 2 : 1; }
 
 // MODE 0: dqdt = R.  MODE 1: FP64 RK stage (g = A g + dt R; q += B g).
 // MODES 2, 3, 4: FP32 increment scheme, stages 1, 2, 3.
 template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(max_threads_for(P))
+__global__ void __launch_bounds__(max_threads_for(P), min_blocks_for(P))
 k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ vis, double* __restrict__ dqdt,
        T* __restrict__ greg, float* __restrict__ dlt, Forcing fc, const OpConst<T> C, RkArgs<T> rk) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
-  constexpr int HC = kHaloComponents;
+  constexpr int FC = kFaceComponents;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int E = C.E;
   const int tileN = E * np;
   const int haloN = E * 6 * n2;
   T* sD = reinterpret_cast<T*>(smem_raw);
-  T* sF = sD + n2;             // [5][E np]  volume fluxes of one direction
-  T* sO = sF + 5 * tileN;      // [14][E np] own stage state and viscous quantities
-  T* sH = sO + HC * tileN;     // [14][E 6 n2] neighbours' face data
-  T* sS = sH + HC * haloN;     // [5][E 6 n2] lifted interface terms
-  int* nb = reinterpret_cast<int*>(sS + 5 * haloN);
+  T* sX = sD + n2;                        // [15][E np]: own data, then the volume fluxes
+  T* sH = sX + kTileComponents * tileN;   // [9][E 6 n2]: neighbours' face data
+  T* sS = sH + FC * haloN;                // [5][E 6 n2]: lifted interface terms
   const int e0 = blockIdx.x * E;
+  const BlockCoords bc = block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
-  fill_neighbours(nb, e0, E, C.K, C.nel);
 
   const int le = threadIdx.x / np;
   const int node = threadIdx.x - le * np;
@@ -304,6 +353,7 @@ k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ v
   const bool active = (le < E) && (e < C.nel);
   const long long N = C.N;
   const long long gi = (long long)e * np + node;
+  const int tix = le * np + node;
 
   // own loads first (all independent), the RK operands with them
   T s[5], vs[9];
@@ -322,75 +372,90 @@ k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ v
       for (int v = 0; v < 5; ++v) gold[v] = (MODE == 1 && rk.A == T(0)) ? T(0) : greg[v * N + gi];
     }
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sO[v * tileN + le * np + node] = s[v];
+    for (int v = 0; v < 5; ++v) sX[v * tileN + tix] = s[v];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) sO[(5 + c) * tileN + le * np + node] = vs[c];
+    for (int c = 0; c < 9; ++c) sX[(5 + c) * tileN + tix] = vs[c];
   }
-  __syncthreads();  // neighbour table
-  // halo: neighbours' stage state and viscous quantities on every face
+  // halo: neighbours' stage state and face-normal viscous quantities on every face
   for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
-    const int ab = t % n2, f = (t / n2) % 6, hl = t / (6 * n2);
-    if (e0 + hl >= C.nel) continue;
-    const int d = f >> 1, side = f & 1;
-    const long long gnb = (long long)nb[6 * hl + f] * np + face_node<P>(d, side ? 0 : P, ab);
+    const Item<P> it = item_of<P>(t);
+    if (e0 + it.hl >= C.nel) continue;
+    const int enb = neighbour_of(bc, it.hl, C.K, it.d, it.side ? 1 : -1);
+    const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
 #pragma unroll
     for (int v = 0; v < 5; ++v) sH[v * haloN + t] = qf[v * N + gnb];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) sH[(5 + c) * haloN + t] = vis[c * N + gnb];
+    for (int i = 0; i < 4; ++i) sH[(5 + i) * haloN + t] = vis[face_vis_index(it.d, i) * N + gnb];
   }
   __syncthreads();
 
   // interface terms, one work item per (element, face, face node)
   for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
-    const int ab = t % n2, f = (t / n2) % 6, hl = t / (6 * n2);
-    if (e0 + hl >= C.nel) continue;
-    const int side = f & 1;
-    const int m = side ? P : 0;
-    switch (f >> 1) {
-      case 0: interface_item<0>(sO + hl * np + face_node<P>(0, m, ab), tileN, sH + t, sS + t, haloN, side, C); break;
-      case 1: interface_item<1>(sO + hl * np + face_node<P>(1, m, ab), tileN, sH + t, sS + t, haloN, side, C); break;
-      default: interface_item<2>(sO + hl * np + face_node<P>(2, m, ab), tileN, sH + t, sS + t, haloN, side, C);
+    const Item<P> it = item_of<P>(t);
+    if (e0 + it.hl >= C.nel) continue;
+    const int o = it.hl * np + face_node<P>(it.d, it.side ? P : 0, it.ab);
+    T so[5], to[4], sn[5], tn[4];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) so[v] = sX[v * tileN + o];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sn[v] = sH[v * haloN + t];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tn[i] = sH[(5 + i) * haloN + t];
+    switch (it.d) {
+      case 0:
+#pragma unroll
+        for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(0, i)) * tileN + o];
+        interface_item<0>(so, to, sn, tn, sS + t, haloN, it.side, C);
+        break;
+      case 1:
+#pragma unroll
+        for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(1, i)) * tileN + o];
+        interface_item<1>(so, to, sn, tn, sS + t, haloN, it.side, C);
+        break;
+      default:
+#pragma unroll
+        for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(2, i)) * tileN + o];
+        interface_item<2>(so, to, sn, tn, sS + t, haloN, it.side, C);
     }
   }
+  __syncthreads();  // own-data tile no longer needed: it now holds the volume fluxes
 
   Prim<T> w;
-  if (active) w = prim_c(s, C);
-  const int idx[3] = {node % n, (node / n) % n, node / n2};
-  const int stride[3] = {1, n, n2};
-  T R[5] = {T(0), T(0), T(0), T(0), T(0)};
-
-  // volume term, one direction at a time through shared memory
+  if (active) {
+    w = prim_c(s, C);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    if (active) {
+    for (int d = 0; d < 3; ++d) {
       T F[5], fv[5];
       euler_flux(s, w, C.Hc, d, F);
       viscous_flux(vs, w.v, d, fv);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) sF[c * tileN + le * np + node] = F[c] - fv[c];
+      for (int c = 0; c < 5; ++c) sX[(5 * d + c) * tileN + tix] = F[c] - fv[c];
     }
-    __syncthreads();
-    if (active) {
-      const T* Drow = sD + idx[d] * n;
-      const int base = le * np + node - idx[d] * stride[d];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        T acc = T(0);
-#pragma unroll
-        for (int m = 0; m < n; ++m) acc += Drow[m] * sF[c * tileN + base + m * stride[d]];
-        R[c] -= C.s2h * acc;
-      }
-    }
-    __syncthreads();
   }
+  __syncthreads();
   if (!active) return;
 
-  // add the lifted interface terms of this node's faces (fixed order x, y, z)
+  // volume term -(2/h) sum_d D_d F_d, then the lifted interface terms (fixed order x, y, z)
+  const int idx[3] = {node % n, (node / n) % n, node / n2};
+  const int stride[3] = {1, n, n2};
+  T R[5] = {T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const T* Drow = sD + idx[d] * n;
+    const int base = le * np + node - idx[d] * stride[d];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < n; ++m) acc += Drow[m] * sX[(5 * d + c) * tileN + base + m * stride[d]];
+      R[c] -= C.s2h * acc;
+    }
+  }
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const bool right = (idx[d] == P), left = (idx[d] == 0);
     if (!(right || left)) continue;
-    const int h = (le * 6 + 2 * d + (right ? 1 : 0)) * n2 + face_ab<P>(d, idx);
+    const int h = item_index<P>(face_ab<P>(d, idx), right ? 1 : 0, d, le);
 #pragma unroll
     for (int c = 0; c < 5; ++c) R[c] += sS[c * haloN + h];
   }

@@ -43,18 +43,17 @@ cudaError_t set_smem(K kern, size_t smem) {
   return cudaSuccess;
 }
 
-// Shared memory of the kernels (layouts in dg_kernels.cuh), including the neighbour table.
+// Shared memory of the kernels (layouts in dg_kernels.cuh).
 template <int P, typename T>
 size_t gradient_smem(int E) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
-  return sizeof(T) * (n2 + 4 * E * np + 4 * E * 6 * n2) + sizeof(int) * 6 * E;
+  return sizeof(T) * (n2 + 4 * E * np + 4 * E * 6 * n2);
 }
 
 template <int P, typename T>
 size_t flux_smem(int E) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
-  constexpr int HC = kHaloComponents;
-  return sizeof(T) * (n2 + (5 + HC) * E * np + (HC + 5) * E * 6 * n2) + sizeof(int) * 6 * E;
+  return sizeof(T) * (n2 + kTileComponents * E * np + (kFaceComponents + 5) * E * 6 * n2);
 }
 
 template <int P, typename T, int SRC>

@@ -36,7 +36,33 @@ def to_np(t, K, n):
 
 
 def rel_l2(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+    a = np.asarray(a, np.longdouble)
+    b = np.asarray(b, np.longdouble)
+    return float(np.sqrt(np.sum((a - b) ** 2)) / np.sqrt(np.sum(b ** 2)))
+
+
+def oracle_rhs_extended(q, mesh, flow):
+    """The oracle operator evaluated in extended precision (np.longdouble) on the same
+    FP64 tables: the reference for the FP64 rounding floor of a case."""
+    m = dgsem.Mesh(mesh.K, mesh.P)
+    m.w, m.xi, m.D = (np.asarray(a, np.longdouble) for a in (mesh.w, mesh.xi, mesh.D))
+    m.h = np.longdouble(mesh.h)
+    return dgsem.rhs(np.asarray(q, np.longdouble), m, flow)
+
+
+def assert_fp64_parity(R_gpu, q, mesh, flow, bar=1e-12):
+    """GPU FP64 operator against the FP64 oracle within `bar` relative L2.  Where the FP64
+    arithmetic floor of the case itself exceeds the bar (Mach 0.1 at high P: the oracle is
+    up to ~1e-11 from the exact operator), both are compared with the extended-precision
+    oracle and the GPU must be no farther from it than the FP64 oracle (x 1.5)."""
+    R64 = dgsem.rhs(q, mesh, flow)
+    direct = rel_l2(R_gpu, R64)
+    if direct < bar:
+        return direct
+    Rx = oracle_rhs_extended(q, mesh, flow)
+    e_gpu, e_or = rel_l2(R_gpu, Rx), rel_l2(R64, Rx)
+    assert e_or > bar and e_gpu <= 1.5 * e_or, (direct, e_gpu, e_or)
+    return direct
 
 
 class Ctx:
@@ -85,9 +111,7 @@ def test_rhs_fp64_matches_oracle_on_tgv(dg, K, P, les, E):
     c = Ctx(dg, K, P, les=les, elems_per_block=E)
     q, q_or = c.tgv()
     # feed both sides the same state: the oracle's initial field
-    q = to_dev(q_or)
-    err = rel_l2(c.rhs(q), dgsem.rhs(q_or, c.mesh, c.flow))
-    assert err < 1e-12, err
+    assert_fp64_parity(c.rhs(to_dev(q_or)), q_or, c.mesh, c.flow)
 
 
 @pytest.mark.parametrize("K,P,les,E", [(3, 3, True, 4), (2, 6, False, 0), (2, 2, True, 0), (1, 4, True, 0),
@@ -96,8 +120,7 @@ def test_rhs_fp64_matches_oracle_on_rough_state(dg, K, P, les, E):
     """Random per-node states (every interface jumps): exercises Roe and BR1 face terms."""
     c = Ctx(dg, K, P, Re=50.0, Mach=0.3, les=les, elems_per_block=E)
     q_or = inputs.random_conserved((K,) * 3 + (P + 1,) * 3, seed=100 + P, rhoE=(1 / (1.4 * 0.09) / 0.4, 1.0))
-    err = rel_l2(c.rhs(to_dev(q_or)), dgsem.rhs(q_or, c.mesh, c.flow))
-    assert err < 1e-12, err
+    assert_fp64_parity(c.rhs(to_dev(q_or)), q_or, c.mesh, c.flow)
 
 
 @pytest.mark.parametrize("K,P,les", [(4, 3, False), (3, 3, True), (2, 6, True), (2, 8, False), (8, 3, False)])
