@@ -111,6 +111,21 @@ int dg_init_tgv(dg_ctx* ctx, double* q, const double* perturbation, void* stream
  * forcing when forcing != NULL (Eq. 4).  q, dqdt: device, 5 N doubles. */
 int dg_rhs(dg_ctx* ctx, const double* q, double* dqdt, const nn_model* forcing, void* stream);
 
+/* dqdt = p(q) like dg_rhs, without any device allocation and without a context (the
+ * paper has no counterpart: this is a service for callers that may not allocate device
+ * memory, e.g. an in-situ hook inside another code's time loop whose device memory is
+ * fixed at start-up, or work recorded into a CUDA stream capture, where allocation calls
+ * are not allowed).  The mesh and flow are given as in dg_create (default dg_opts apart
+ * from precision, no forcing).  q, dqdt: DEVICE, 5 N doubles, N = K^3 (P+1)^3.
+ * The two intermediate fields of the operator live in one scratch array inside the
+ * library's device image (3.7 MB, kept by every GPU that loads the library until exit):
+ * N may be at most 32768 nodes, larger meshes return DG_ERR_INVALID_ARG.  The first call
+ * on a device (with that device current) looks up the array's device address; make it
+ * before any stream capture.  All calls share the array: calls that overlap on the GPU
+ * (other streams or host threads) race and must be serialised by the caller. */
+int dg_rhs_noalloc(int K, int P, double Re, double Mach, double Pr, int closure, int precision,
+                   const double* q, double* dqdt, void* stream);
+
 /* Advances q in place by nsteps low-storage RK3 steps of size dt (Sec. 2, Eq. 6 with
  * the third-order Runge-Kutta scheme of Sec. 3.1; Williamson 2N coefficients).  When
  * forcing != NULL the network forcing s(q_k) is evaluated on every stage state and

@@ -67,6 +67,7 @@ _SIGS = {
     "dg_make_pairs": [_P, _P, _P, _P, _D, _I, _I, _P, _P, _P],
     "dg_check_conversions": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P],
     "dg_autotune": [_P, _P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P],
+    "dg_rhs_noalloc": [_I, _I, _D, _D, _D, _I, _I, _P, _P, _P],
     "dg_profile_rk3": [_P, _P, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I),
                        ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D), _P],
 }
@@ -259,6 +260,18 @@ def dg_autotune(ctx, q, dt, stream=None):
     check(lib().dg_autotune(ctypes.c_void_p(ctx), ptr(q), float(dt), ctypes.byref(E), ctypes.byref(ms),
                             stream_ptr(stream)))
     return E.value, ms.value
+
+
+def dg_rhs_noalloc(K, P, Re, Mach, Pr, closure, precision, q, dqdt, stream=None):
+    """dqdt = p(q) without device allocation (for callers that may not allocate, such as
+    an in-situ hook with a fixed memory budget or work inside a stream capture); at most
+    32768 nodes; calls share one scratch array, so overlapping calls must be serialised."""
+    nodes = K ** 3 * (P + 1) ** 3
+    for t, nm in ((q, "q"), (dqdt, "dqdt")):
+        if t.numel() != 5 * nodes or str(t.dtype) != "torch.float64" or not t.is_cuda:
+            raise ValueError(f"{nm} must be a CUDA float64 tensor of 5 * {nodes} values")
+    check(lib().dg_rhs_noalloc(int(K), int(P), float(Re), float(Mach), float(Pr), int(closure), int(precision),
+                               ptr(q), ptr(dqdt), stream_ptr(stream)))
 
 
 def dg_check_conversions(x, stream=None):
