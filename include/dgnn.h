@@ -133,6 +133,52 @@ int dg_rhs_noalloc(int K, int P, double Re, double Mach, double Pr, int closure,
 int dg_rk3_step(dg_ctx* ctx, double* q, double dt, int nsteps, const nn_model* forcing,
                 void* stream);
 
+/* ---- Batches of independent solvers (no counterpart in the paper: a throughput service
+ * for many small flows at once, e.g. a sweep over Re, mesh and order).  Every member
+ * computes exactly what dg_rk3_step computes for it alone. ---- */
+typedef struct dg_batch dg_batch;
+
+/* One member: mesh, order and flow as the arguments of dg_create. */
+typedef struct {
+  int K;
+  int P;
+  double Re;
+  double Mach;
+  double Pr;
+  int closure;
+} dg_instance_desc;
+
+#define DG_BATCH_MAX 16
+#define DG_BATCH_NO_GRAPH 1 /* dg_batch_rk3_step flag: launch directly, no graph replay */
+
+/* Creates n (1..DG_BATCH_MAX) members from desc (host array of n), all with the same
+ * opts (NULL = defaults; the precision and elements-per-block apply to every member).
+ * Each member owns the workspace of a dg_create context.  Errors of a member's creation
+ * return that member's status with its index in dg_last_error(). */
+int dg_create_batch(const dg_instance_desc* desc, int n, const dg_opts* opts, dg_batch** out);
+int dg_batch_destroy(dg_batch* batch);
+int dg_batch_size(const dg_batch* batch, int* n);
+
+/* Context of member i, borrowed: usable with every dg_* call that takes a context
+ * (dg_init_tgv, dg_diagnostics, dg_stable_dt, dg_rk3_step, ...), released only by
+ * dg_batch_destroy (dg_destroy on it returns DG_ERR_INVALID_ARG). */
+int dg_batch_member(dg_batch* batch, int i, dg_ctx** out);
+
+/* Advances every member i in place by nsteps RK3 steps of size dt[i], with the same
+ * arithmetic as dg_rk3_step (no forcing).  q: HOST array of n DEVICE pointers, member i's
+ * state (5 N_i doubles, distinct buffers); dt: HOST array of n step sizes.  Members of one
+ * order share one launch per kernel phase and stage; members of different orders run as
+ * parallel branches.  Unless flags has DG_BATCH_NO_GRAPH, one step is recorded as a CUDA
+ * graph on the batch's private streams (the first call, and again whenever the q
+ * pointers, dt values or elements-per-block change) and replayed nsteps times on stream;
+ * the call must then not be made while that stream is being captured. */
+int dg_batch_rk3_step(dg_batch* batch, double* const* q, const double* dt, int nsteps, int flags,
+                      void* stream);
+
+/* Picks elements-per-block for each order present: dg_autotune on the largest member
+ * of that order (q, dt: as in dg_batch_rk3_step), applied to all members of the order. */
+int dg_batch_autotune(dg_batch* batch, double* const* q, const double* dt, void* stream);
+
 /* Same as dg_rk3_step but q_host is a HOST array (pageable or pinned, 5 N doubles):
  * copies it to the device, advances, copies it back, and fills *diag (host, may be
  * NULL) for the final state.  Synchronises the stream. */

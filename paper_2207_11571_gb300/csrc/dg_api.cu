@@ -244,6 +244,7 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
 
 int dg_destroy(dg_ctx* c) {
   if (!c) return fail(DG_ERR_INVALID_ARG, "dg_destroy: NULL");
+  if (c->borrowed) return fail(DG_ERR_INVALID_ARG, "dg_destroy: the context belongs to a batch (dg_batch_destroy)");
   cudaFree(c->qf);
   cudaFree(c->vis);
   cudaFree(c->g);

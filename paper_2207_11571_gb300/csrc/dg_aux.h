@@ -51,4 +51,15 @@ cudaError_t flux_f32(const dg_ctx* c, double* q, double* dqdt, const Forcing& f,
 cudaError_t flux_f64(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
                      double dt, double invB1, cudaStream_t st);
 
+// Batched RK stage k for n instances of order P sharing precision and elements per block
+// (dg_batch_f32.cu / dg_batch_f64.cu): q[i] is instance i's FP64 state, dt[i] its step.
+cudaError_t batch_stage_f32(int P, dg_ctx* const* ctx, double* const* q, const double* dt, int n, int k, double A,
+                            double B, double invB1, cudaStream_t st);
+// Sets the kernels' shared-memory attributes for order P at E elements per block; call
+// before batch_stage_* (never inside a stream capture).
+cudaError_t batch_prepare_f32(int P, int E);
+cudaError_t batch_prepare_f64(int P, int E);
+cudaError_t batch_stage_f64(int P, dg_ctx* const* ctx, double* const* q, const double* dt, int n, int k, double A,
+                            double B, double invB1, cudaStream_t st);
+
 }  // namespace dgnn

@@ -98,6 +98,7 @@ struct dg_ctx {
   double* q_dev = nullptr;     // device state for dg_advance_host
   float* s_buf = nullptr;      // forcing buffer [nel][5 n^3]
   double* filter_dev[dgnn::kMaxP + 1] = {};  // filter G to each lower order (dg_project)
+  bool borrowed = false;       // member of a dg_batch: released by dg_batch_destroy only
 };
 
 namespace dgnn {

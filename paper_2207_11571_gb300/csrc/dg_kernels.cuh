@@ -167,10 +167,12 @@ __device__ __forceinline__ void transport_c(const OpConst<T>& C, T rho, const T 
   *lam = l;
 }
 
+// Phase A of block `blk` of one mesh (the body of k_gradient and k_gradient_batch).
 template <int P, typename T, int SRC>
-__global__ void __launch_bounds__(max_threads_for(P))
-k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, const float* __restrict__ dlt,
-           T* __restrict__ qf, float* __restrict__ qn32_out, T* __restrict__ vis, const OpConst<T> C) {
+__device__ __forceinline__ void gradient_block(int blk, const double* __restrict__ q,
+                                               const float* __restrict__ qn32_in, const float* __restrict__ dlt,
+                                               T* __restrict__ qf, float* __restrict__ qn32_out,
+                                               T* __restrict__ vis, const OpConst<T>& C) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int E = C.E;
@@ -179,7 +181,7 @@ k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, cons
   T* sD = reinterpret_cast<T*>(smem_raw);
   T* sU = sD + n2;            // [4][E np]
   T* sH = sU + 4 * tileN;     // [4][E 6 n2]: neighbours' gradient variables on each face
-  const int e0 = blockIdx.x * E;
+  const int e0 = blk * E;
   const BlockCoords bc = block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
 
@@ -265,6 +267,13 @@ k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, cons
   for (int c = 0; c < 9; ++c) vis[c * N + gi] = out[c];
 }
 
+template <int P, typename T, int SRC>
+__global__ void __launch_bounds__(max_threads_for(P))
+k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, const float* __restrict__ dlt,
+           T* __restrict__ qf, float* __restrict__ qn32_out, T* __restrict__ vis, const OpConst<T> C) {
+  gradient_block<P, T, SRC>(blockIdx.x, q, qn32_in, dlt, qf, qn32_out, vis, C);
+}
+
 // Per-launch RK data of phase B in the arithmetic of the update.
 template <typename R>
 struct RkArgs {
@@ -329,10 +338,12 @@ __host__ __device__ constexpr int min_blocks_for(int P) { return P <= 6 ? 2 : 1;
 
 // MODE 0: dqdt = R.  MODE 1: FP64 RK stage (g = A g + dt R; q += B g).
 // MODES 2, 3, 4: FP32 increment scheme, stages 1, 2, 3.
+// Phase B of block `blk` of one mesh (the body of k_flux and k_flux_batch).
 template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(max_threads_for(P), min_blocks_for(P))
-k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ vis, double* __restrict__ dqdt,
-       T* __restrict__ greg, float* __restrict__ dlt, Forcing fc, const OpConst<T> C, RkArgs<T> rk) {
+__device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, const T* __restrict__ qf,
+                                           const T* __restrict__ vis, double* __restrict__ dqdt,
+                                           T* __restrict__ greg, float* __restrict__ dlt, const Forcing& fc,
+                                           const OpConst<T>& C, const RkArgs<T>& rk) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
   constexpr int FC = kFaceComponents;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -343,7 +354,7 @@ k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ v
   T* sX = sD + n2;                        // [15][E np]: own data, then the volume fluxes
   T* sH = sX + kTileComponents * tileN;   // [9][E 6 n2]: neighbours' face data
   T* sS = sH + FC * haloN;                // [5][E 6 n2]: lifted interface terms
-  const int e0 = blockIdx.x * E;
+  const int e0 = blk * E;
   const BlockCoords bc = block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
 
@@ -500,6 +511,56 @@ k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ v
       }
     }
   }
+}
+
+template <int P, typename T, int MODE>
+__global__ void __launch_bounds__(max_threads_for(P), min_blocks_for(P))
+k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ vis, double* __restrict__ dqdt,
+       T* __restrict__ greg, float* __restrict__ dlt, Forcing fc, const OpConst<T> C, RkArgs<T> rk) {
+  flux_block<P, T, MODE>(blockIdx.x, q, qf, vis, dqdt, greg, dlt, fc, C, rk);
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched launches: independent meshes of the same order P (different K, Re, closure,
+// dt) share one launch.  Block b belongs to the instance whose block range holds it; the
+// table travels as one kernel parameter, so its per-instance constants are read from the
+// constant bank like the single-mesh kernels' own.
+constexpr int kMaxBatch = 16;
+
+template <typename T>
+struct BatchTable {
+  int n;                             // instances in this launch
+  int block_start[kMaxBatch + 1];    // first block of each instance; block_start[n] = grid
+  double* q[kMaxBatch];              // FP64 states
+  float* qn32[kMaxBatch];            // FP32 operator: step-start image (NULL in FP64)
+  float* dlt[kMaxBatch];             // FP32 operator: stage increment (NULL in FP64)
+  T* qf[kMaxBatch];                  // stage state
+  T* vis[kMaxBatch];                 // viscous quantities
+  T* g[kMaxBatch];                   // RK register
+  RkArgs<T> rk[kMaxBatch];
+  OpConst<T> C[kMaxBatch];
+};
+
+__device__ __forceinline__ int batch_instance(const int* start, int n, int b) {
+  int i = 0;
+  while (i + 1 < n && b >= start[i + 1]) ++i;
+  return i;
+}
+
+template <int P, typename T, int SRC>
+__global__ void __launch_bounds__(max_threads_for(P))
+k_gradient_batch(const __grid_constant__ BatchTable<T> tb) {
+  const int i = batch_instance(tb.block_start, tb.n, blockIdx.x);
+  gradient_block<P, T, SRC>(blockIdx.x - tb.block_start[i], tb.q[i], tb.qn32[i], tb.dlt[i], tb.qf[i],
+                            SRC == 0 ? tb.qn32[i] : nullptr, tb.vis[i], tb.C[i]);
+}
+
+template <int P, typename T, int MODE>
+__global__ void __launch_bounds__(max_threads_for(P), min_blocks_for(P))
+k_flux_batch(const __grid_constant__ BatchTable<T> tb) {
+  const int i = batch_instance(tb.block_start, tb.n, blockIdx.x);
+  flux_block<P, T, MODE>(blockIdx.x - tb.block_start[i], tb.q[i], tb.qf[i], tb.vis[i], nullptr, tb.g[i],
+                         tb.dlt[i], Forcing{}, tb.C[i], tb.rk[i]);
 }
 
 }  // namespace dgnn

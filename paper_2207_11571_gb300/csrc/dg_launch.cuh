@@ -3,6 +3,8 @@
 // parallel translation units.
 #pragma once
 
+#include <type_traits>
+
 #include "dg_kernels.cuh"
 
 namespace dgnn {
@@ -131,6 +133,108 @@ cudaError_t flux_t(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, i
 #define DG_F(PP) flux_dispatch_mode<PP, T>(c, q, dqdt, f, mode, rk, st)
   DG_FOR_EACH_P(DG_F)
 #undef DG_F
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched RK stage: one phase-A and one phase-B launch for all instances of order P.
+// Instances must share the operator precision T and the elements-per-block E.
+
+template <typename T>
+void fill_batch(BatchTable<T>* tb, dg_ctx* const* ctx, double* const* q, const double* dt, int n, double A,
+                double B, double invB1) {
+  tb->n = n;
+  int blocks = 0;
+  for (int i = 0; i < n; ++i) {
+    const dg_ctx* c = ctx[i];
+    tb->block_start[i] = blocks;
+    blocks += (c->nel + c->geom.E - 1) / c->geom.E;
+    tb->q[i] = q[i];
+    tb->qn32[i] = c->qn32;
+    tb->dlt[i] = c->dlt;
+    tb->qf[i] = static_cast<T*>(c->qf);
+    tb->vis[i] = static_cast<T*>(c->vis);
+    tb->g[i] = static_cast<T*>(c->g);
+    tb->rk[i] = RkArgs<T>{T(A), T(B), T(dt[i]), T(invB1)};
+    tb->C[i] = make_const<T>(c);
+  }
+  tb->block_start[n] = blocks;
+}
+
+// Stage k of the RK3 step: the same source and mode sequence as the single-mesh path
+// (FP32 operator: sources 0, 1, 1 and modes 2, 3, 4; FP64 operator: source 0, mode 1).
+template <int P, typename T>
+cudaError_t batch_stage_p(const BatchTable<T>& tb, int E, int k, cudaStream_t st) {
+  constexpr bool f32 = std::is_same<T, float>::value;
+  const int grid = tb.block_start[tb.n];
+  const int threads = block_threads(P, E);
+  const size_t gs = gradient_smem<P, T>(E), fs = flux_smem<P, T>(E);
+  cudaError_t e;
+  void (*kg)(const BatchTable<T>);
+  void (*kf)(const BatchTable<T>);
+  if constexpr (f32) {
+    kg = k == 0 ? k_gradient_batch<P, T, 0> : k_gradient_batch<P, T, 1>;
+    kf = k == 0 ? k_flux_batch<P, T, 2> : k == 1 ? k_flux_batch<P, T, 3> : k_flux_batch<P, T, 4>;
+  } else {
+    kg = k_gradient_batch<P, T, 0>;
+    kf = k_flux_batch<P, T, 1>;
+  }
+  kg<<<grid, threads, gs, st>>>(tb);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  kf<<<grid, threads, fs, st>>>(tb);
+  return cudaGetLastError();
+}
+
+// Dynamic shared-memory attributes of the batched kernels of order P at E elements per
+// block; set before any launch (and outside stream capture).
+template <int P, typename T>
+cudaError_t batch_prepare_p(int E) {
+  const size_t gs = gradient_smem<P, T>(E), fs = flux_smem<P, T>(E);
+  cudaError_t e;
+  if constexpr (std::is_same<T, float>::value) {
+    if ((e = set_smem(k_gradient_batch<P, T, 0>, gs)) != cudaSuccess) return e;
+    if ((e = set_smem(k_gradient_batch<P, T, 1>, gs)) != cudaSuccess) return e;
+    if ((e = set_smem(k_flux_batch<P, T, 2>, fs)) != cudaSuccess) return e;
+    if ((e = set_smem(k_flux_batch<P, T, 3>, fs)) != cudaSuccess) return e;
+    return set_smem(k_flux_batch<P, T, 4>, fs);
+  } else {
+    if ((e = set_smem(k_gradient_batch<P, T, 0>, gs)) != cudaSuccess) return e;
+    return set_smem(k_flux_batch<P, T, 1>, fs);
+  }
+}
+
+template <typename T>
+cudaError_t batch_prepare_t(int P, int E) {
+  switch (P) {
+    case 1: return batch_prepare_p<1, T>(E);
+    case 2: return batch_prepare_p<2, T>(E);
+    case 3: return batch_prepare_p<3, T>(E);
+    case 4: return batch_prepare_p<4, T>(E);
+    case 5: return batch_prepare_p<5, T>(E);
+    case 6: return batch_prepare_p<6, T>(E);
+    case 7: return batch_prepare_p<7, T>(E);
+    case 8: return batch_prepare_p<8, T>(E);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t batch_stage_t(int P, dg_ctx* const* ctx, double* const* q, const double* dt, int n, int k, double A,
+                          double B, double invB1, cudaStream_t st) {
+  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  BatchTable<T> tb;
+  fill_batch<T>(&tb, ctx, q, dt, n, A, B, invB1);
+  const int E = ctx[0]->geom.E;
+  switch (P) {
+    case 1: return batch_stage_p<1, T>(tb, E, k, st);
+    case 2: return batch_stage_p<2, T>(tb, E, k, st);
+    case 3: return batch_stage_p<3, T>(tb, E, k, st);
+    case 4: return batch_stage_p<4, T>(tb, E, k, st);
+    case 5: return batch_stage_p<5, T>(tb, E, k, st);
+    case 6: return batch_stage_p<6, T>(tb, E, k, st);
+    case 7: return batch_stage_p<7, T>(tb, E, k, st);
+    case 8: return batch_stage_p<8, T>(tb, E, k, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace dgnn

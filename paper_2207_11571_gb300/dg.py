@@ -46,6 +46,14 @@ class dg_diag(ctypes.Structure):
                 "nonfinite": int(self.nonfinite)}
 
 
+class dg_instance_desc(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("P", ctypes.c_int), ("Re", ctypes.c_double), ("Mach", ctypes.c_double),
+                ("Pr", ctypes.c_double), ("closure", ctypes.c_int)]
+
+
+DG_BATCH_MAX = 16
+DG_BATCH_NO_GRAPH = 1
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -68,6 +76,12 @@ _SIGS = {
     "dg_check_conversions": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P],
     "dg_autotune": [_P, _P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P],
     "dg_rhs_noalloc": [_I, _I, _D, _D, _D, _I, _I, _P, _P, _P],
+    "dg_create_batch": [ctypes.POINTER(dg_instance_desc), _I, ctypes.POINTER(dg_opts), ctypes.POINTER(_P)],
+    "dg_batch_destroy": [_P],
+    "dg_batch_size": [_P, ctypes.POINTER(_I)],
+    "dg_batch_member": [_P, _I, ctypes.POINTER(_P)],
+    "dg_batch_rk3_step": [_P, ctypes.POINTER(_P), ctypes.POINTER(_D), _I, _I, _P],
+    "dg_batch_autotune": [_P, ctypes.POINTER(_P), ctypes.POINTER(_D), _P],
     "dg_profile_rk3": [_P, _P, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I),
                        ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D), _P],
 }
@@ -272,6 +286,55 @@ def dg_rhs_noalloc(K, P, Re, Mach, Pr, closure, precision, q, dqdt, stream=None)
             raise ValueError(f"{nm} must be a CUDA float64 tensor of 5 * {nodes} values")
     check(lib().dg_rhs_noalloc(int(K), int(P), float(Re), float(Mach), float(Pr), int(closure), int(precision),
                                ptr(q), ptr(dqdt), stream_ptr(stream)))
+
+
+def dg_create_batch(members, opts=None, **kw):
+    """members: sequence of (K, P, Re, Mach, Pr, closure).  Returns an opaque batch handle."""
+    n = len(members)
+    arr = (dg_instance_desc * max(n, 1))(*[dg_instance_desc(int(K), int(P), float(Re), float(M), float(Pr), int(c))
+                                           for K, P, Re, M, Pr, c in members])
+    o = opts if opts is not None else dg_opts_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    check(lib().dg_create_batch(arr, n, ctypes.byref(o), ctypes.byref(h)))
+    return h.value
+
+
+def dg_batch_destroy(batch):
+    check(lib().dg_batch_destroy(ctypes.c_void_p(batch)))
+
+
+def dg_batch_size(batch):
+    n = ctypes.c_int()
+    check(lib().dg_batch_size(ctypes.c_void_p(batch), ctypes.byref(n)))
+    return n.value
+
+
+def dg_batch_member(batch, i):
+    """Borrowed context of member i (owned by the batch)."""
+    h = ctypes.c_void_p()
+    check(lib().dg_batch_member(ctypes.c_void_p(batch), int(i), ctypes.byref(h)))
+    return h.value
+
+
+def _batch_arrays(batch, qs, dts):
+    n = dg_batch_size(batch)
+    if len(qs) != n or len(dts) != n:
+        raise ValueError(f"need {n} states and {n} step sizes")
+    for i, q in enumerate(qs):
+        _check_state(dg_batch_member(batch, i), q, f"q[{i}]")
+    return (ctypes.c_void_p * n)(*[q.data_ptr() for q in qs]), (ctypes.c_double * n)(*[float(d) for d in dts])
+
+
+def dg_batch_rk3_step(batch, qs, dts, nsteps=1, flags=0, stream=None):
+    qa, da = _batch_arrays(batch, qs, dts)
+    check(lib().dg_batch_rk3_step(ctypes.c_void_p(batch), qa, da, int(nsteps), int(flags), stream_ptr(stream)))
+
+
+def dg_batch_autotune(batch, qs, dts, stream=None):
+    qa, da = _batch_arrays(batch, qs, dts)
+    check(lib().dg_batch_autotune(ctypes.c_void_p(batch), qa, da, stream_ptr(stream)))
 
 
 def dg_check_conversions(x, stream=None):

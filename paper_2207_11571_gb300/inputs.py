@@ -43,3 +43,9 @@ def normal(shape, seed, scale=1.0):
 def epoch_permutation(n, seed, epoch):
     """Shuffle order of ``n`` training samples for one epoch."""
     return np.random.default_rng([seed, epoch]).permutation(n).astype(np.int64)
+
+
+def batch_members(n=12, seed=12, Re=(30.0, 200.0, 1600.0), K=(8, 12, 16), P=(3, 6)):
+    """n independent (K, P, Re) draws for a batch of Taylor-Green instances of uneven size."""
+    rng = np.random.default_rng(seed)
+    return [(int(rng.choice(K)), int(rng.choice(P)), float(rng.choice(Re))) for _ in range(n)]

@@ -67,6 +67,23 @@ def test_null_handles_are_rejected(L):
     assert L.dg_rk3_step(None, None, 1e-3, 1, None, None) == dg.DG_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("members", [[], [(4, 3, 1600.0, 0.1, 0.71, 0)] * 17, [(4, 9, 1600.0, 0.1, 0.71, 0)],
+                                     [(0, 3, 1600.0, 0.1, 0.71, 0), (4, 3, 200.0, 0.1, 0.71, 0)]])
+def test_create_batch_rejects_bad_members_before_touching_cuda(L, members):
+    from paper_2207_11571_gb300 import dg
+    with pytest.raises(dg.DGError) as e:
+        dg.dg_create_batch(members)
+    assert e.value.status == dg.DG_ERR_INVALID_ARG
+    assert b"dg_create" in L.dg_last_error()
+
+
+def test_batch_calls_reject_null_handles(L):
+    from paper_2207_11571_gb300 import dg
+    assert L.dg_batch_destroy(None) == dg.DG_ERR_INVALID_ARG
+    assert L.dg_batch_rk3_step(None, None, None, 1, 0, None) == dg.DG_ERR_INVALID_ARG
+    assert L.dg_batch_member(None, 0, None) == dg.DG_ERR_INVALID_ARG
+
+
 def test_host_basis_matches_closed_forms_and_oracle(L):
     from oracle import basis
     from paper_2207_11571_gb300 import dg
