@@ -1,0 +1,346 @@
+"""Algorithm 1 of arXiv 2207.11571 end to end on one GPU, through the C ABI.
+
+1. High-order evolution (P_HO) of the Taylor-Green vortex to the start of the training
+   window, then Algorithm 1's first loop over the window: filter (G q_HO^n), one
+   uncorrected low-order step, the matching high-order steps, filter again, and the pair
+   (G q_HO^n, (G q_HO^{n+1} - q_NN^{n+1}) / dt) of every element (dg_project,
+   dg_rk3_step, dg_make_pairs).
+2. Training of the forcing network on the pairs (nn_compute_scalers, nn_train_step),
+   shuffled mini-batches.
+3. Evaluation window (from the end of the training window, or replayed from its start):
+   the high-order run continues as the reference; from its filtered state, the corrected
+   low-order run (forcing in every RK stage) and plain runs at P = P_LO .. 6 advance in
+   lockstep.  Every sample interval
+   records -dKE/dt and KE (dg_diagnostics) and the L-inf momentum error against the
+   filtered reference (Eq. 9).  Each run's advance is timed with CUDA events.
+
+Outputs a JSON summary: per run the relative L2 error of the dissipation history
+against the reference, the mean e_n, and the wall time; plus the corrected-vs-plain
+speed-up at equal dissipation error (log-log interpolation over the plain orders).
+
+    python -m paper_2207_11571_gb300.experiment --out result.json [--K 16 --Re 1600 ...]
+"""
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import dg, inputs, nn
+
+
+def make_ctx(K, P, args, les=False, precision=None):
+    prec = dg.DG_PREC_FP32 if precision is None else precision
+    return dg.dg_create(K, P, args.Re, args.Mach, args.Pr, int(les), precision=prec)
+
+
+def new_state(ctx):
+    return torch.empty(5 * dg.dg_sizes(ctx)[0], dtype=torch.float64, device="cuda")
+
+
+class Run:
+    """One solver run advancing in lockstep with the others, with its own timer.  A run
+    whose state turns non-finite is marked diverged and stops advancing.
+
+    With `guard`, a corrected run falls back to the uncorrected solver (forcing off for
+    the rest of the run) at the first sample where its kinetic energy grows: the decaying
+    Taylor-Green flow has dKE/dt < 0, so growth means the network injects energy."""
+
+    def __init__(self, name, P, ctx, q, dt_max, net=None, guard=False):
+        self.name, self.P, self.ctx, self.q, self.net = name, P, ctx, q, net
+        self.dt_max = dt_max
+        self.guard = guard
+        self.ms = 0.0
+        self.steps = 0
+        self.t = []
+        self.dke = []
+        self.ke = []
+        self.einf = []
+        self.diverged_at = None
+        self.fallback_at = None
+
+    def advance(self, interval):
+        if self.diverged_at is not None:
+            return
+        n = max(1, math.ceil(interval / self.dt_max - 1e-9))
+        dt = interval / n
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        dg.dg_rk3_step(self.ctx, self.q, dt, n, forcing=self.net)
+        b.record()
+        b.synchronize()
+        self.ms += a.elapsed_time(b)
+        self.steps += n
+
+    def sample(self, t, qref=None):
+        if self.diverged_at is not None:
+            return None
+        try:
+            d = dg.dg_diagnostics(self.ctx, self.q, q_ref=qref, forcing=self.net)
+        except dg.DGError as e:
+            if e.status != dg.DG_ERR_NONFINITE:
+                raise
+            self.diverged_at = t
+            return None
+        self.t.append(t)
+        self.dke.append(d["dke_dt"])
+        self.ke.append(d["ke"])
+        self.einf.append(max(d["e_inf"]) if qref is not None else None)
+        if self.guard and self.net is not None and d["dke_dt"] > 0:
+            self.net = None
+            self.fallback_at = t
+        return d
+
+
+def stable_dt(ctx, q, cfl):
+    return dg.dg_stable_dt(ctx, q, cfl)
+
+
+def generate_pairs(args, ctx_hi, q_hi, ctx_lo, dt_lo, ratio, n_steps, first_var, n_vars):
+    """Algorithm 1, first loop: returns device tensors X, Y (n_steps K^3 rows)."""
+    nodes_lo, elems = dg.dg_sizes(ctx_lo)
+    feat = n_vars * (args.P_lo + 1) ** 3
+    X = torch.empty((n_steps * elems, feat), dtype=torch.float32, device="cuda")
+    Y = torch.empty_like(X)
+    qbar = new_state(ctx_lo)
+    qnn = new_state(ctx_lo)
+    qbar1 = new_state(ctx_lo)
+    dt_hi = dt_lo / ratio
+    for n in range(n_steps):
+        dg.dg_project(ctx_hi, ctx_lo, q_hi, qbar)                 # q_NN^n = G q_HO^n
+        qnn.copy_(qbar)
+        dg.dg_rk3_step(ctx_lo, qnn, dt_lo, 1)                     # uncorrected LO step
+        dg.dg_rk3_step(ctx_hi, q_hi, dt_hi, ratio)               # HO steps over dt_lo
+        dg.dg_project(ctx_hi, ctx_lo, q_hi, qbar1)                # G q_HO^{n+1}
+        dg.dg_make_pairs(ctx_lo, qbar, qnn, qbar1, dt_lo, first_var, n_vars,
+                         X[n * elems:(n + 1) * elems], Y[n * elems:(n + 1) * elems])
+    return X, Y
+
+
+def train(args, X, Y, first_var, n_vars):
+    feat = X.shape[1]
+    dims = [feat] + [args.width] * args.hidden + [feat]
+    net = nn.nn_create(feat, feat, args.width, args.hidden, first_var, n_vars, args.batch,
+                       inputs.uniform_draws(dims, args.seed))
+    nn.nn_compute_scalers(net, X, Y)
+    rows = X.shape[0]
+    losses = []
+    t0 = time.perf_counter()
+    for epoch in range(args.epochs):
+        perm = torch.from_numpy(inputs.epoch_permutation(rows, args.seed, epoch)).cuda()
+        ep = []
+        for b0 in range(0, rows - args.batch + 1, args.batch):
+            ep.append(nn.nn_train_step(net, X, Y, perm[b0:b0 + args.batch], lr=args.lr,
+                                       want_loss=(b0 + args.batch > rows - args.batch)))
+        losses.append(ep[-1])
+    torch.cuda.synchronize()
+    return net, losses, time.perf_counter() - t0
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def run_errors(run, ref_t, ref_dke, ref_ke, bar_ke):
+    """Error histories of one run over the sampled times (infinite if it diverged):
+    dke: -dKE/dt from the operator against the high-order run's (the benchmark metric);
+    ke: KE(t) against the high-order run's; dke_filtered: centred differences of KE(t)
+    against those of the filtered high-order field (what the forcing is trained on)."""
+    if run.diverged_at is not None:
+        return {"dke": float("inf"), "ke": float("inf"), "dke_filtered": float("inf")}
+    t = np.asarray(ref_t)
+    return {"dke": rel_l2(-np.asarray(run.dke), -np.asarray(ref_dke)),
+            "ke": rel_l2(run.ke, ref_ke),
+            "dke_filtered": rel_l2(-np.gradient(np.asarray(run.ke), t), -np.gradient(np.asarray(bar_ke), t))}
+
+
+def speedup_at_equal_error(corr, plain, key):
+    """Cost of the plain-order curve interpolated (log-log) at the corrected run's error,
+    over the corrected run's cost.  Below the smallest plain error the curve is not
+    extrapolated and the result is a lower bound."""
+    pts = sorted([(r["errors"][key], r["ms"]) for r in plain if math.isfinite(r["errors"][key])])
+    e = corr["errors"][key]
+    if not pts or not math.isfinite(e):
+        return None, None
+    le = np.log([p[0] for p in pts])
+    lc = np.log([p[1] for p in pts])
+    cost = float(math.exp(np.interp(math.log(e), le, lc)))
+    return cost / corr["ms"], bool(math.log(e) < le.min())
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser(description="Algorithm 1: pairs, training, corrected vs plain runs")
+    ap.add_argument("--K", type=int, default=16)
+    ap.add_argument("--P_hi", type=int, default=8)
+    ap.add_argument("--P_lo", type=int, default=3)
+    ap.add_argument("--plain", type=str, default="3,4,5,6")
+    ap.add_argument("--Re", type=float, default=1600.0)
+    ap.add_argument("--Mach", type=float, default=0.1)
+    ap.add_argument("--Pr", type=float, default=0.71)
+    ap.add_argument("--les_hi", action="store_true")
+    ap.add_argument("--les_lo", action="store_true")
+    ap.add_argument("--cfl", type=float, default=0.7)
+    ap.add_argument("--t_train", type=float, default=4.0)
+    ap.add_argument("--t_train_end", type=float, default=5.0)
+    ap.add_argument("--window_precision", choices=["fp32", "fp64"], default="fp64")
+    ap.add_argument("--t_end", type=float, default=14.0)
+    ap.add_argument("--sample", type=float, default=0.1)
+    ap.add_argument("--no_guard", action="store_true",
+                    help="keep the forcing on even when the corrected flow gains kinetic energy")
+    ap.add_argument("--eval_start", choices=["window_end", "window_start"], default="window_end",
+                    help="start of the corrected and plain runs: after the training window "
+                         "(extrapolation) or at its start (as in the paper's Table 1 cases)")
+    ap.add_argument("--io", choices=["all", "momentum"], default="all")
+    ap.add_argument("--width", type=int, default=512)
+    ap.add_argument("--hidden", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=2207)
+    ap.add_argument("--out", type=str, default="experiment.json")
+    return ap.parse_args(argv)
+
+
+def run(args):
+    """Runs the three phases; returns the summary dict (also written to args.out if set)."""
+    first_var, n_vars = (1, 3) if args.io == "momentum" else (0, 5)
+    dg.lib()
+    K = args.K
+    wall0 = time.perf_counter()
+
+    # 1. high-order evolution to the training window
+    ctx_hi = make_ctx(K, args.P_hi, args, args.les_hi)
+    q_hi = new_state(ctx_hi)
+    nodes_hi = dg.dg_sizes(ctx_hi)[0]
+    dg.dg_init_tgv(ctx_hi, q_hi, torch.from_numpy(inputs.perturbation((5, nodes_hi)).ravel()).cuda())
+    dt_hi = stable_dt(ctx_hi, q_hi, args.cfl)
+    t = 0.0
+    while t < args.t_train - 1e-12:
+        interval = min(1.0, args.t_train - t)
+        n = max(1, math.ceil(interval / dt_hi))
+        dg.dg_rk3_step(ctx_hi, q_hi, interval / n, n)
+        t += interval
+        try:
+            dt_hi = stable_dt(ctx_hi, q_hi, args.cfl)
+        except dg.DGError as e:
+            raise RuntimeError(f"the P={args.P_hi} run failed before t={t:g}: {e}") from e
+    torch.cuda.synchronize()
+    t_ho_initial = time.perf_counter() - wall0
+
+    # 2. pairs over the training window (Algorithm 1, first loop)
+    ctx_lo = make_ctx(K, args.P_lo, args, args.les_lo)
+    qtmp = new_state(ctx_lo)
+    dg.dg_project(ctx_hi, ctx_lo, q_hi, qtmp)
+    dt_lo_cfl = stable_dt(ctx_lo, qtmp, args.cfl)
+    window = args.t_train_end - args.t_train
+    n_pairs = max(1, math.ceil(window / dt_lo_cfl))
+    dt_lo = window / n_pairs
+    ratio = max(1, math.ceil(dt_lo / dt_hi - 1e-9))
+    q_hi_start = q_hi.clone() if args.eval_start == "window_start" else None
+    t1 = time.perf_counter()
+    if args.window_precision == "fp64":   # the training window in an FP64 operator
+        w_hi = make_ctx(K, args.P_hi, args, args.les_hi, dg.DG_PREC_FP64)
+        w_lo = make_ctx(K, args.P_lo, args, args.les_lo, dg.DG_PREC_FP64)
+    else:
+        w_hi, w_lo = ctx_hi, ctx_lo
+    X, Y = generate_pairs(args, w_hi, q_hi, w_lo, dt_lo, ratio, n_pairs, first_var, n_vars)
+    torch.cuda.synchronize()
+    t_pairs = time.perf_counter() - t1
+    if args.window_precision == "fp64":
+        dg.dg_destroy(w_hi)
+        dg.dg_destroy(w_lo)
+
+    # 3. training
+    net, losses, t_train = train(args, X, Y, first_var, n_vars)
+    del X, Y
+    torch.cuda.empty_cache()
+
+    # 4. evaluation window: reference HO, corrected LO, plain LO at several orders
+    t0 = args.t_train_end
+    if q_hi_start is not None:            # replay the window: the runs start where training did
+        q_hi.copy_(q_hi_start)
+        del q_hi_start
+        t0 = args.t_train
+    ref = Run(f"P{args.P_hi} reference", args.P_hi, ctx_hi, q_hi, stable_dt(ctx_hi, q_hi, args.cfl))
+    runs = []
+    q_c = new_state(ctx_lo)
+    dg.dg_project(ctx_hi, ctx_lo, q_hi, q_c)
+    runs.append(Run(f"P{args.P_lo}+NN", args.P_lo, ctx_lo, q_c, stable_dt(ctx_lo, q_c, args.cfl), net=net,
+                    guard=not args.no_guard))
+    plain_ctx = {}
+    for P in [int(p) for p in args.plain.split(",")]:
+        c = make_ctx(K, P, args, args.les_lo)
+        plain_ctx[P] = c
+        qp = new_state(c)
+        dg.dg_project(ctx_hi, c, q_hi, qp)
+        runs.append(Run(f"P{P}", P, c, qp, stable_dt(c, qp, args.cfl)))
+    # filtered reference at the corrected order, for e_n (Eq. 9)
+    qbar = new_state(ctx_lo)
+    bar_ke = []
+    ref.sample(t0)
+    dg.dg_project(ctx_hi, ctx_lo, q_hi, qbar)
+    bar_ke.append(dg.dg_diagnostics(ctx_lo, qbar)["ke"])
+    for r in runs:
+        r.sample(t0, qbar if r.P == args.P_lo else None)
+    n_samples = round((args.t_end - t0) / args.sample)
+    for j in range(1, n_samples + 1):
+        tj = t0 + j * args.sample
+        ref.advance(args.sample)
+        ref.sample(tj)
+        dg.dg_project(ctx_hi, ctx_lo, q_hi, qbar)
+        bar_ke.append(dg.dg_diagnostics(ctx_lo, qbar)["ke"])
+        for r in runs:
+            r.advance(args.sample)
+            r.sample(tj, qbar if r.P == args.P_lo else None)
+
+    out = {"config": vars(args), "dt_lo": dt_lo, "ratio_hi_per_lo": ratio, "n_pairs": n_pairs,
+           "pairs_rows": n_pairs * K ** 3, "train_loss": losses, "train_seconds": t_train,
+           "pairs_seconds": t_pairs, "ho_to_window_seconds": t_ho_initial,
+           "reference": {"name": ref.name, "ms": ref.ms, "steps": ref.steps}, "runs": []}
+    for r in runs:
+        rec = {"name": r.name, "P": r.P, "ms": r.ms, "steps": r.steps,
+               "errors": run_errors(r, ref.t, ref.dke, ref.ke, bar_ke),
+               "diverged_at": r.diverged_at, "fallback_at": r.fallback_at}
+        rec["dke_error"] = rec["errors"]["dke"]
+        if r.P == args.P_lo:
+            rec["einf_mean"] = (float(np.mean([e for e in r.einf if e is not None]))
+                                if r.diverged_at is None else float("inf"))
+        out["runs"].append(rec)
+    corr, plain = out["runs"][0], out["runs"][1:]
+    out["speedup_vs_plain_at_equal_error"] = {}
+    for key in ("dke", "ke", "dke_filtered"):
+        sp, lower = speedup_at_equal_error(corr, plain, key)
+        out["speedup_vs_plain_at_equal_error"][key] = {"speedup": sp, "lower_bound": lower}
+    p6 = [r for r in plain if r["P"] == 6]
+    if p6:
+        out["speedup_vs_P6"] = p6[0]["ms"] / corr["ms"]
+        out["corrected_error_over_P6_error"] = {k: corr["errors"][k] / p6[0]["errors"][k]
+                                                for k in corr["errors"]}
+    out["history"] = {"t": ref.t, "ref_dke": ref.dke, "ref_ke": ref.ke, "filtered_ke": bar_ke,
+                      **{r.name + "_ke": r.ke for r in runs},
+                      **{r.name + "_dke": r.dke for r in runs},
+                      **{r.name + "_einf": r.einf for r in runs if r.P == args.P_lo}}
+    out["total_seconds"] = time.perf_counter() - wall0
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(out, f, indent=1)
+    nn.nn_destroy(net)
+    for c in list(plain_ctx.values()) + [ctx_lo, ctx_hi]:
+        dg.dg_destroy(c)
+    return out
+
+
+def main(argv=None):
+    out = run(parse(argv))
+    summary = {k: out[k] for k in ("speedup_vs_plain_at_equal_error", "n_pairs", "train_seconds")}
+    summary["runs"] = [(r["name"], {k: round(v, 4) for k, v in r["errors"].items()}, round(r["ms"], 1),
+                        r["diverged_at"], r["fallback_at"]) for r in out["runs"]]
+    summary["speedup_vs_P6"] = out.get("speedup_vs_P6")
+    print(json.dumps(summary))
+
+
+if __name__ == "__main__":
+    main()
