@@ -332,13 +332,31 @@ __device__ __forceinline__ void interface_item(const T so[5], const T to[4], con
 // Index of viscous component i of the face-normal set of direction d in the 9-vector.
 __device__ __forceinline__ int face_vis_index(int d, int i) { return i < 3 ? sym_index(i, d) : 6 + d; }
 
-// Blocks per SM the flux kernel is compiled for (register budget): two at low order, so
-// that one block's barriers overlap another's work.
-__host__ __device__ constexpr int min_blocks_for(int P) { return P <= 6 ? 2 : 1; }
+// Nodes per thread of the flux kernel.  At P >= 6 one element has 343 to 729 nodes; two
+// nodes per thread halve the block so that more blocks fit an SM's registers and one
+// block's barriers overlap the others' work.
+__host__ __device__ constexpr int flux_npt(int P) { return P >= 6 ? 2 : 1; }
+
+// Maximum threads per flux block.
+__host__ __device__ constexpr int flux_max_threads(int P) {
+  return flux_npt(P) == 1 ? max_threads_for(P) : ((max_threads_for(P) / 2 + 31) / 32) * 32;
+}
+
+// Blocks per SM the flux kernel is compiled for (register budget, about 80 registers per
+// thread in FP32): several, so that one block's barriers overlap another's work; one in
+// FP64 (the parity path), whose doubled register footprint would otherwise spill.
+__host__ __device__ constexpr int min_blocks_for(int P, int tsize) {
+  return tsize == 8 ? 1 : P == 6 ? 4 : P == 7 ? 3 : 2;
+}
 
 // MODE 0: dqdt = R.  MODE 1: FP64 RK stage (g = A g + dt R; q += B g).
 // MODES 2, 3, 4: FP32 increment scheme, stages 1, 2, 3.
 // Phase B of block `blk` of one mesh (the body of k_flux and k_flux_batch).
+//
+// Thread j-th node: tile index tix = threadIdx.x + j blockDim.x, j < NPT.  With one node
+// per thread the own state and viscous values stay in registers across the interface
+// phase and the RK operands are loaded first; with two, they are read back from the
+// tile and the RK operands are loaded after the interface phase (register budget).
 template <int P, typename T, int MODE>
 __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, const T* __restrict__ qf,
                                            const T* __restrict__ vis, double* __restrict__ dqdt,
@@ -346,6 +364,8 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
                                            const OpConst<T>& C, const RkArgs<T>& rk) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
   constexpr int FC = kFaceComponents;
+  constexpr int NPT = flux_npt(P);
+  constexpr bool kHold = (NPT == 1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int E = C.E;
   const int tileN = E * np;
@@ -357,35 +377,47 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   const int e0 = blk * E;
   const BlockCoords bc = block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
-
-  const int le = threadIdx.x / np;
-  const int node = threadIdx.x - le * np;
-  const int e = e0 + le;
-  const bool active = (le < E) && (e < C.nel);
   const long long N = C.N;
-  const long long gi = (long long)e * np + node;
-  const int tix = le * np + node;
 
-  // own loads first (all independent), the RK operands with them
-  T s[5], vs[9];
-  T gold[5], dold[5];
-  if (active) {
+  int le[NPT], node[NPT], tix[NPT];
+  long long gi[NPT];
+  bool active[NPT];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) s[v] = qf[v * N + gi];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) vs[c] = vis[c * N + gi];
+  for (int j = 0; j < NPT; ++j) {
+    tix[j] = threadIdx.x + j * blockDim.x;
+    le[j] = tix[j] / np;
+    node[j] = tix[j] - le[j] * np;
+    active[j] = (le[j] < E) && (e0 + le[j] < C.nel);
+    gi[j] = (long long)(e0 + le[j]) * np + node[j];
+  }
+
+  // RK operands of the update (loaded first with one node per thread, late with two)
+  T gold[NPT][5], dold[NPT][5];
+  auto load_rk = [&](int j) {
     if (MODE == 3 || MODE == 4) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) dold[v] = T(dlt[v * N + gi]);
+      for (int v = 0; v < 5; ++v) dold[j][v] = T(dlt[v * N + gi[j]]);
     }
     if (MODE == 4 || MODE == 1) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) gold[v] = (MODE == 1 && rk.A == T(0)) ? T(0) : greg[v * N + gi];
+      for (int v = 0; v < 5; ++v) gold[j][v] = (MODE == 1 && rk.A == T(0)) ? T(0) : greg[v * N + gi[j]];
     }
+  };
+
+  // own loads first (all independent)
+  T s[NPT][5], vs[NPT][9];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sX[v * tileN + tix] = s[v];
+  for (int j = 0; j < NPT; ++j) {
+    if (!active[j]) continue;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) sX[(5 + c) * tileN + tix] = vs[c];
+    for (int v = 0; v < 5; ++v) s[j][v] = qf[v * N + gi[j]];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) vs[j][c] = vis[c * N + gi[j]];
+    if (kHold) load_rk(j);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) sX[v * tileN + tix[j]] = s[j][v];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) sX[(5 + c) * tileN + tix[j]] = vs[j][c];
   }
   // halo: neighbours' stage state and face-normal viscous quantities on every face
   for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
@@ -431,90 +463,103 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   }
   __syncthreads();  // own-data tile no longer needed: it now holds the volume fluxes
 
-  Prim<T> w;
-  if (active) {
-    w = prim_c(s, C);
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    if (!active[j]) continue;
+    if (!kHold) {
+      load_rk(j);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s[j][v] = sX[v * tileN + tix[j]];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) vs[j][c] = sX[(5 + c) * tileN + tix[j]];
+    }
+    const Prim<T> w = prim_c(s[j], C);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       T F[5], fv[5];
-      euler_flux(s, w, C.Hc, d, F);
-      viscous_flux(vs, w.v, d, fv);
+      euler_flux(s[j], w, C.Hc, d, F);
+      viscous_flux(vs[j], w.v, d, fv);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) sX[(5 * d + c) * tileN + tix] = F[c] - fv[c];
+      for (int c = 0; c < 5; ++c) sX[(5 * d + c) * tileN + tix[j]] = F[c] - fv[c];
     }
   }
   __syncthreads();
-  if (!active) return;
 
-  // volume term -(2/h) sum_d D_d F_d, then the lifted interface terms (fixed order x, y, z)
-  const int idx[3] = {node % n, (node / n) % n, node / n2};
-  const int stride[3] = {1, n, n2};
-  T R[5] = {T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const T* Drow = sD + idx[d] * n;
-    const int base = le * np + node - idx[d] * stride[d];
+  for (int j = 0; j < NPT; ++j) {
+    if (!active[j]) continue;
+    const int nd = node[j], lj = le[j];
+    const long long g = gi[j];
+    // volume term -(2/h) sum_d D_d F_d, then the lifted interface terms (fixed order x, y, z)
+    const int idx[3] = {nd % n, (nd / n) % n, nd / n2};
+    const int stride[3] = {1, n, n2};
+    T R[5] = {T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      T acc = T(0);
+    for (int d = 0; d < 3; ++d) {
+      const T* Drow = sD + idx[d] * n;
+      const int base = lj * np + nd - idx[d] * stride[d];
 #pragma unroll
-      for (int m = 0; m < n; ++m) acc += Drow[m] * sX[(5 * d + c) * tileN + base + m * stride[d]];
-      R[c] -= C.s2h * acc;
+      for (int c = 0; c < 5; ++c) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc += Drow[m] * sX[(5 * d + c) * tileN + base + m * stride[d]];
+        R[c] -= C.s2h * acc;
+      }
     }
-  }
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const bool right = (idx[d] == P), left = (idx[d] == 0);
-    if (!(right || left)) continue;
-    const int h = item_index<P>(face_ab<P>(d, idx), right ? 1 : 0, d, le);
+    for (int d = 0; d < 3; ++d) {
+      const bool right = (idx[d] == P), left = (idx[d] == 0);
+      if (!(right || left)) continue;
+      const int h = item_index<P>(face_ab<P>(d, idx), right ? 1 : 0, d, lj);
 #pragma unroll
-    for (int c = 0; c < 5; ++c) R[c] += sS[c * haloN + h];
-  }
+      for (int c = 0; c < 5; ++c) R[c] += sS[c * haloN + h];
+    }
 
-  if (fc.s != nullptr) {
-    const long long base = (long long)e * fc.stride + node;
+    if (fc.s != nullptr) {
+      const long long base = (long long)(e0 + lj) * fc.stride + nd;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const int slot = c - fc.first_var;
-      if (slot >= 0 && slot < fc.n_vars) R[c] += T(fc.s[base + (long long)slot * np]);
+      for (int c = 0; c < 5; ++c) {
+        const int slot = c - fc.first_var;
+        if (slot >= 0 && slot < fc.n_vars) R[c] += T(fc.s[base + (long long)slot * np]);
+      }
     }
-  }
 
-  if (MODE == 0) {
+    if (MODE == 0) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) dqdt[c * N + gi] = double(R[c]);
-  } else if (MODE == 1) {
-    // FP64 operator: plain 2N update of the FP64 state
+      for (int c = 0; c < 5; ++c) dqdt[c * N + g] = double(R[c]);
+    } else if (MODE == 1) {
+      // FP64 operator: plain 2N update of the FP64 state
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const long long o = c * N + gi;
-      T gnew = rk.dt * R[c];
-      if (rk.A != T(0)) gnew = rk.A * gold[c] + gnew;
-      greg[o] = gnew;
-      q[o] = double(rk.B) * double(gnew) + q[o];
-    }
-  } else {
-    // FP32 increment scheme
+      for (int c = 0; c < 5; ++c) {
+        const long long o = c * N + g;
+        T gnew = rk.dt * R[c];
+        if (rk.A != T(0)) gnew = rk.A * gold[j][c] + gnew;
+        greg[o] = gnew;
+        q[o] = double(rk.B) * double(gnew) + q[o];
+      }
+    } else {
+      // FP32 increment scheme
 #pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      const long long o = c * N + gi;
-      if (MODE == 2) {
-        dlt[o] = float(rk.B * (rk.dt * R[c]));                 // g1 = dt R1; dlt1 = B1 g1
-      } else if (MODE == 3) {
-        const T g2 = rk.A * (dold[c] * rk.invB1) + rk.dt * R[c];
-        greg[o] = g2;
-        dlt[o] = float(dold[c] + rk.B * g2);
-      } else {
-        const T g3 = rk.A * gold[c] + rk.dt * R[c];
-        const float d3 = float(dold[c] + rk.B * g3);
-        q[o] = q[o] + f2d(d3);                                 // once per step, in FP64
+      for (int c = 0; c < 5; ++c) {
+        const long long o = c * N + g;
+        if (MODE == 2) {
+          dlt[o] = float(rk.B * (rk.dt * R[c]));                 // g1 = dt R1; dlt1 = B1 g1
+        } else if (MODE == 3) {
+          const T g2 = rk.A * (dold[j][c] * rk.invB1) + rk.dt * R[c];
+          greg[o] = g2;
+          dlt[o] = float(dold[j][c] + rk.B * g2);
+        } else {
+          const T g3 = rk.A * gold[j][c] + rk.dt * R[c];
+          const float d3 = float(dold[j][c] + rk.B * g3);
+          q[o] = q[o] + f2d(d3);                                 // once per step, in FP64
+        }
       }
     }
   }
 }
 
 template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(max_threads_for(P), min_blocks_for(P))
+__global__ void __launch_bounds__(flux_max_threads(P), min_blocks_for(P, sizeof(T)))
 k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ vis, double* __restrict__ dqdt,
        T* __restrict__ greg, float* __restrict__ dlt, Forcing fc, const OpConst<T> C, RkArgs<T> rk) {
   flux_block<P, T, MODE>(blockIdx.x, q, qf, vis, dqdt, greg, dlt, fc, C, rk);
@@ -556,7 +601,7 @@ k_gradient_batch(const __grid_constant__ BatchTable<T> tb) {
 }
 
 template <int P, typename T, int MODE>
-__global__ void __launch_bounds__(max_threads_for(P), min_blocks_for(P))
+__global__ void __launch_bounds__(flux_max_threads(P), min_blocks_for(P, sizeof(T)))
 k_flux_batch(const __grid_constant__ BatchTable<T> tb) {
   const int i = batch_instance(tb.block_start, tb.n, blockIdx.x);
   flux_block<P, T, MODE>(blockIdx.x - tb.block_start[i], tb.q[i], tb.qf[i], tb.vis[i], nullptr, tb.g[i],

@@ -14,6 +14,13 @@ inline int block_threads(int P, int E) {
   return ((E * np + 31) / 32) * 32;
 }
 
+// Threads of a flux block: flux_npt(P) nodes per thread.
+inline int flux_threads(int P, int E) {
+  const int np = (P + 1) * (P + 1) * (P + 1);
+  const int npt = flux_npt(P);
+  return (((E * np + npt - 1) / npt + 31) / 32) * 32;
+}
+
 template <typename T>
 OpConst<T> make_const(const dg_ctx* c) {
   OpConst<T> k;
@@ -81,7 +88,7 @@ cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, c
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = (c->nel + E - 1) / E;
-  kern<<<grid, block_threads(P, E), smem, st>>>(q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt,
+  kern<<<grid, flux_threads(P, E), smem, st>>>(q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt,
                                                 static_cast<T*>(c->g), c->dlt, f, make_const<T>(c), rk);
   return cudaGetLastError();
 }
@@ -180,7 +187,7 @@ cudaError_t batch_stage_p(const BatchTable<T>& tb, int E, int k, cudaStream_t st
   }
   kg<<<grid, threads, gs, st>>>(tb);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  kf<<<grid, threads, fs, st>>>(tb);
+  kf<<<grid, flux_threads(P, E), fs, st>>>(tb);
   return cudaGetLastError();
 }
 
