@@ -608,4 +608,270 @@ k_flux_batch(const __grid_constant__ BatchTable<T> tb) {
                          tb.dlt[i], Forcing{}, tb.C[i], tb.rk[i]);
 }
 
+// ---------------------------------------------------------------------------------------
+// Streamed phase B for high orders (FP32 operator, P >= 6, one element per work item).
+//
+// At P >= 6 an element's phase B is latency-bound when its loads and its arithmetic
+// alternate: the block waits for the own tile and the face halo, then computes with no
+// memory traffic in flight.  The streamed kernel is persistent: each block walks the
+// elements blockIdx.x, blockIdx.x + gridDim.x, ... and, while it computes element k,
+// copies element k + 1's tile and halo into the other half of a double buffer with
+// cp.async (4-byte copies straight to shared memory, no registers held).  The per-node
+// and per-item arithmetic is flux_block's.
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Threads of a streamed block: one per node.
+__host__ __device__ constexpr int stream_threads(int P) { return (((P + 1) * (P + 1) * (P + 1) + 31) / 32) * 32; }
+// Blocks per SM the streamed kernel is compiled for (shared memory allows two at P <= 7).
+__host__ __device__ constexpr int stream_min_blocks(int P) { return P <= 7 ? 2 : 1; }
+
+// One mesh's operands as seen by a streamed work item.
+struct StreamItem {
+  double* q;
+  const float* qf;
+  const float* vis;
+  double* dqdt;
+  float* greg;
+  float* dlt;
+  const OpConst<float>* C;
+  const RkArgs<float>* rk;
+  Forcing fc;
+  int e;  // element
+};
+
+// Shared memory of the streamed kernel, in floats: D, lifted terms, two buffers of
+// (own tile [15][np], halo [9][6 n2]).
+template <int P>
+__host__ __device__ constexpr int stream_smem_floats() {
+  return (P + 1) * (P + 1) + 5 * 6 * (P + 1) * (P + 1) +
+         2 * (15 * (P + 1) * (P + 1) * (P + 1) + kFaceComponents * 6 * (P + 1) * (P + 1));
+}
+
+template <int P, int MODE, class Src>
+__device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
+  using T = float;
+  constexpr int n = P + 1, n2 = n * n, np = n2 * n, haloN = 6 * n2;
+  constexpr int FC = kFaceComponents;
+  constexpr int kBuf = 15 * np + FC * haloN;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sD = reinterpret_cast<T*>(smem_raw);
+  T* sS = sD + n2;                 // [5][haloN]: lifted interface terms
+  T* buf0 = sS + 5 * haloN;        // two buffers: [15][np] own tile, then [9][haloN] halo
+
+  auto prefetch = [&](int item, T* b) {
+    const StreamItem m = src.at(item);
+    const long long N = m.C->N;
+    const long long e0 = (long long)m.e * np;
+    for (int nd = threadIdx.x; nd < np; nd += blockDim.x) {
+#pragma unroll
+      for (int v = 0; v < 5; ++v) cp_async4(b + v * np + nd, m.qf + v * N + e0 + nd);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) cp_async4(b + (5 + c) * np + nd, m.vis + c * N + e0 + nd);
+    }
+    const BlockCoords bc = block_coords(m.e, m.C->K);
+    T* h = b + 15 * np;
+    for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
+      const Item<P> it = item_of<P>(t);
+      const int enb = neighbour_of(bc, 0, m.C->K, it.d, it.side ? 1 : -1);
+      const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
+#pragma unroll
+      for (int v = 0; v < 5; ++v) cp_async4(h + v * haloN + t, m.qf + v * N + gnb);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) cp_async4(h + (5 + i) * haloN + t, m.vis + face_vis_index(it.d, i) * N + gnb);
+    }
+    cp_async_commit();
+  };
+
+  int item = blockIdx.x;
+  if (item >= n_items) return;
+  prefetch(item, buf0);
+  {
+    const OpConst<T>& C0 = *src.at(item).C;   // D depends on P only
+    for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C0.D[t];
+  }
+  const int node = threadIdx.x;
+  const bool active = node < np;
+  const int idx[3] = {node % n, (node / n) % n, node / n2};
+
+  for (int k = 0; item < n_items; item += gridDim.x, ++k) {
+    T* b = buf0 + (k & 1) * kBuf;
+    cp_async_wait_all();
+    __syncthreads();                       // this item's data landed; the other buffer is free
+    const int next = item + gridDim.x;
+    if (next < n_items) prefetch(next, buf0 + ((k + 1) & 1) * kBuf);
+
+    const StreamItem m = src.at(item);
+    const OpConst<T>& C = *m.C;
+    const RkArgs<T>& rk = *m.rk;
+    const long long N = C.N;
+    const long long gi = (long long)m.e * np + node;
+    T* sX = b;
+    T* sH = b + 15 * np;
+
+    // RK operands of this thread's node, loaded now and used at the end
+    T gold[5], dold[5];
+    double qold[5];
+    if (active) {
+      if (MODE == 3 || MODE == 4) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) dold[v] = m.dlt[v * N + gi];
+      }
+      if (MODE == 4) {
+#pragma unroll
+        for (int v = 0; v < 5; ++v) gold[v] = m.greg[v * N + gi];
+#pragma unroll
+        for (int v = 0; v < 5; ++v) qold[v] = m.q[v * N + gi];
+      }
+    }
+
+    // interface terms, one work item per (face, face node)
+    for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
+      const Item<P> it = item_of<P>(t);
+      const int o = face_node<P>(it.d, it.side ? P : 0, it.ab);
+      T so[5], to[4], sn[5], tn[4];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) so[v] = sX[v * np + o];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sn[v] = sH[v * haloN + t];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) tn[i] = sH[(5 + i) * haloN + t];
+      switch (it.d) {
+        case 0:
+#pragma unroll
+          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(0, i)) * np + o];
+          interface_item<0>(so, to, sn, tn, sS + t, haloN, it.side, C);
+          break;
+        case 1:
+#pragma unroll
+          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(1, i)) * np + o];
+          interface_item<1>(so, to, sn, tn, sS + t, haloN, it.side, C);
+          break;
+        default:
+#pragma unroll
+          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(2, i)) * np + o];
+          interface_item<2>(so, to, sn, tn, sS + t, haloN, it.side, C);
+      }
+    }
+    __syncthreads();  // own tile no longer needed: it now takes the volume fluxes
+
+    if (active) {
+      T s[5], vs[9];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s[v] = sX[v * np + node];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) vs[c] = sX[(5 + c) * np + node];
+      const Prim<T> w = prim_c(s, C);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T F[5], fv[5];
+        euler_flux(s, w, C.Hc, d, F);
+        viscous_flux(vs, w.v, d, fv);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) sX[(5 * d + c) * np + node] = F[c] - fv[c];
+      }
+    }
+    __syncthreads();
+    if (!active) continue;
+
+    const int stride[3] = {1, n, n2};
+    T R[5] = {T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T* Drow = sD + idx[d] * n;
+      const int base = node - idx[d] * stride[d];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        T acc = T(0);
+#pragma unroll
+        for (int mm = 0; mm < n; ++mm) acc += Drow[mm] * sX[(5 * d + c) * np + base + mm * stride[d]];
+        R[c] -= C.s2h * acc;
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const bool right = (idx[d] == P), left = (idx[d] == 0);
+      if (!(right || left)) continue;
+      const int h = item_index<P>(face_ab<P>(d, idx), right ? 1 : 0, d, 0);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) R[c] += sS[c * haloN + h];
+    }
+    if (m.fc.s != nullptr) {
+      const long long fb = (long long)m.e * m.fc.stride + node;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        const int slot = c - m.fc.first_var;
+        if (slot >= 0 && slot < m.fc.n_vars) R[c] += T(m.fc.s[fb + (long long)slot * np]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const long long o = c * N + gi;
+      if (MODE == 0) {
+        m.dqdt[o] = double(R[c]);
+      } else if (MODE == 2) {
+        m.dlt[o] = float(rk.B * (rk.dt * R[c]));
+      } else if (MODE == 3) {
+        const T g2 = rk.A * (dold[c] * rk.invB1) + rk.dt * R[c];
+        m.greg[o] = g2;
+        m.dlt[o] = float(dold[c] + rk.B * g2);
+      } else if (MODE == 4) {
+        const T g3 = rk.A * gold[c] + rk.dt * R[c];
+        const float d3 = float(dold[c] + rk.B * g3);
+        m.q[o] = qold[c] + f2d(d3);
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+// Operands of one mesh for the streamed kernel (kernel parameter).
+struct StreamMesh {
+  double* q;
+  const float* qf;
+  const float* vis;
+  double* dqdt;
+  float* greg;
+  float* dlt;
+  Forcing fc;
+  OpConst<float> C;
+  RkArgs<float> rk;
+};
+
+struct SingleSource {
+  const StreamMesh& m;
+  __device__ __forceinline__ StreamItem at(int item) const {
+    return StreamItem{m.q, m.qf, m.vis, m.dqdt, m.greg, m.dlt, &m.C, &m.rk, m.fc, item};
+  }
+};
+
+struct BatchSource {
+  const BatchTable<float>& tb;
+  __device__ __forceinline__ StreamItem at(int item) const {
+    const int i = batch_instance(tb.block_start, tb.n, item);
+    return StreamItem{tb.q[i], tb.qf[i], tb.vis[i], nullptr, tb.g[i], tb.dlt[i], &tb.C[i], &tb.rk[i], Forcing{},
+                      item - tb.block_start[i]};
+  }
+};
+
+template <int P, int MODE>
+__global__ void __launch_bounds__(stream_threads(P), stream_min_blocks(P))
+k_flux_stream(const __grid_constant__ StreamMesh mesh) {
+  flux_stream<P, MODE>(SingleSource{mesh}, mesh.C.nel);
+}
+
+// Batched streamed phase B: members of order P, one element per work item
+// (block_start counts elements).
+template <int P, int MODE>
+__global__ void __launch_bounds__(stream_threads(P), stream_min_blocks(P))
+k_flux_stream_batch(const __grid_constant__ BatchTable<float> tb) {
+  flux_stream<P, MODE>(BatchSource{tb}, tb.block_start[tb.n]);
+}
+
 }  // namespace dgnn

@@ -3,6 +3,7 @@
 // parallel translation units.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 
 #include "dg_kernels.cuh"
@@ -79,9 +80,54 @@ cudaError_t gradient_p(const dg_ctx* c, const double* q, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Grid of a persistent streamed launch: resident blocks on every SM, at most one per item.
+template <typename K>
+cudaError_t stream_grid(K kern, int threads, size_t smem, int items, int* grid) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  *grid = std::min(items, per_sm * sms);
+  return cudaSuccess;
+}
+
+// Streamed phase B (FP32 operator, P >= 6, one element per block step).
+template <int P, int MODE>
+cudaError_t flux_stream_launch(const dg_ctx* c, double* q, double* dqdt, const Forcing& f,
+                               const RkArgs<float>& rk, cudaStream_t st) {
+  const size_t smem = sizeof(float) * stream_smem_floats<P>();
+  auto kern = k_flux_stream<P, MODE>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  int grid = 0;
+  if ((e = stream_grid(kern, stream_threads(P), smem, c->nel, &grid)) != cudaSuccess) return e;
+  StreamMesh m;
+  m.q = q;
+  m.qf = static_cast<const float*>(c->qf);
+  m.vis = static_cast<const float*>(c->vis);
+  m.dqdt = dqdt;
+  m.greg = static_cast<float*>(c->g);
+  m.dlt = c->dlt;
+  m.fc = f;
+  m.C = make_const<float>(c);
+  m.rk = rk;
+  kern<<<grid, stream_threads(P), smem, st>>>(m);
+  return cudaGetLastError();
+}
+
 template <int P, typename T, int MODE>
 cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, const RkArgs<T>& rk,
                    cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value && P >= 6 && MODE != 1) {
+    if (c->geom.E == 1) return flux_stream_launch<P, MODE>(c, q, dqdt, f, rk, st);
+  }
   const int E = c->geom.E;
   const size_t smem = flux_smem<P, T>(E);
   auto kern = k_flux<P, T, MODE>;
@@ -176,6 +222,19 @@ cudaError_t batch_stage_p(const BatchTable<T>& tb, int E, int k, cudaStream_t st
   const int threads = block_threads(P, E);
   const size_t gs = gradient_smem<P, T>(E), fs = flux_smem<P, T>(E);
   cudaError_t e;
+  if constexpr (std::is_same<T, float>::value && P >= 6) {
+    if (E == 1) {
+      auto kg = k == 0 ? k_gradient_batch<P, T, 0> : k_gradient_batch<P, T, 1>;
+      auto kf = k == 0 ? k_flux_stream_batch<P, 2> : k == 1 ? k_flux_stream_batch<P, 3> : k_flux_stream_batch<P, 4>;
+      const size_t ss = sizeof(float) * stream_smem_floats<P>();
+      int sgrid = 0;
+      if ((e = stream_grid(kf, stream_threads(P), ss, grid, &sgrid)) != cudaSuccess) return e;
+      kg<<<grid, threads, gs, st>>>(tb);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      kf<<<sgrid, stream_threads(P), ss, st>>>(tb);
+      return cudaGetLastError();
+    }
+  }
   void (*kg)(const BatchTable<T>);
   void (*kf)(const BatchTable<T>);
   if constexpr (f32) {
@@ -197,6 +256,14 @@ template <int P, typename T>
 cudaError_t batch_prepare_p(int E) {
   const size_t gs = gradient_smem<P, T>(E), fs = flux_smem<P, T>(E);
   cudaError_t e;
+  if constexpr (std::is_same<T, float>::value && P >= 6) {
+    if (E == 1) {
+      const size_t ss = sizeof(float) * stream_smem_floats<P>();
+      if ((e = set_smem(k_flux_stream_batch<P, 2>, ss)) != cudaSuccess) return e;
+      if ((e = set_smem(k_flux_stream_batch<P, 3>, ss)) != cudaSuccess) return e;
+      if ((e = set_smem(k_flux_stream_batch<P, 4>, ss)) != cudaSuccess) return e;
+    }
+  }
   if constexpr (std::is_same<T, float>::value) {
     if ((e = set_smem(k_gradient_batch<P, T, 0>, gs)) != cudaSuccess) return e;
     if ((e = set_smem(k_gradient_batch<P, T, 1>, gs)) != cudaSuccess) return e;
