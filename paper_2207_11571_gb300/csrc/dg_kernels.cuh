@@ -65,6 +65,12 @@ __device__ __forceinline__ BlockCoords block_coords(int e0, int K) {
   return b;
 }
 
+// Periodic +/-1 step of a coordinate in [0, K).
+__device__ __forceinline__ int wrap_step(int x, int shift, int K) {
+  x += shift;
+  return x < 0 ? x + K : (x >= K ? x - K : x);
+}
+
 // Element index of block element hl shifted by +/-1 along d (periodic), without division.
 __device__ __forceinline__ int neighbour_of(const BlockCoords& b, int hl, int K, int d, int shift) {
   int x = b.x + hl, y = b.y, z = b.z;
@@ -75,11 +81,12 @@ __device__ __forceinline__ int neighbour_of(const BlockCoords& b, int hl, int K,
       ++z;
     }
   }
-  if (d == 0) x = (x + shift + K) % K;
-  else if (d == 1) y = (y + shift + K) % K;
-  else z = (z + shift + K) % K;
+  if (d == 0) x = wrap_step(x, shift, K);
+  else if (d == 1) y = wrap_step(y, shift, K);
+  else z = wrap_step(z, shift, K);
   return x + K * (y + K * z);
 }
+
 
 // Node of the face normal to d at normal index m with tangential index ab.
 template <int P>
@@ -332,6 +339,20 @@ __device__ __forceinline__ void interface_item(const T so[5], const T to[4], con
 // Index of viscous component i of the face-normal set of direction d in the 9-vector.
 __device__ __forceinline__ int face_vis_index(int d, int i) { return i < 3 ? sym_index(i, d) : 6 + d; }
 
+// Halo entry t of a phase-B block: the neighbour's stage state (5) and its viscous
+// quantities normal to the face (4), for a face normal to D (compile-time, so the
+// component offsets are constants).
+template <int D, typename T>
+__device__ __forceinline__ void load_face_data(const T* __restrict__ qf, const T* __restrict__ vis, long long N,
+                                               long long g, T* dst, int stride) {
+  const T* s = qf + g;
+  const T* w = vis + g;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) dst[v * stride] = s[v * N];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) dst[(5 + i) * stride] = w[face_vis_index(D, i) * N];
+}
+
 // Nodes per thread of the flux kernel.  At P >= 6 one element has 343 to 729 nodes; two
 // nodes per thread halve the block so that more blocks fit an SM's registers and one
 // block's barriers overlap the others' work.
@@ -425,10 +446,11 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
     if (e0 + it.hl >= C.nel) continue;
     const int enb = neighbour_of(bc, it.hl, C.K, it.d, it.side ? 1 : -1);
     const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
-#pragma unroll
-    for (int v = 0; v < 5; ++v) sH[v * haloN + t] = qf[v * N + gnb];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) sH[(5 + i) * haloN + t] = vis[face_vis_index(it.d, i) * N + gnb];
+    switch (it.d) {
+      case 0: load_face_data<0>(qf, vis, N, gnb, sH + t, haloN); break;
+      case 1: load_face_data<1>(qf, vis, N, gnb, sH + t, haloN); break;
+      default: load_face_data<2>(qf, vis, N, gnb, sH + t, haloN);
+    }
   }
   __syncthreads();
 
@@ -627,6 +649,18 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// load_face_data with cp.async (no registers held while the copies fly).
+template <int D>
+__device__ __forceinline__ void copy_face_data(const float* qf, const float* vis, long long N, long long g,
+                                               float* dst, int stride) {
+  const float* s = qf + g;
+  const float* w = vis + g;
+#pragma unroll
+  for (int v = 0; v < 5; ++v) cp_async4(dst + v * stride, s + v * N);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) cp_async4(dst + (5 + i) * stride, w + face_vis_index(D, i) * N);
+}
+
 // Threads of a streamed block: one per node.
 __host__ __device__ constexpr int stream_threads(int P) { return (((P + 1) * (P + 1) * (P + 1) + 31) / 32) * 32; }
 // Blocks per SM the streamed kernel is compiled for (shared memory allows two at P <= 7).
@@ -681,10 +715,11 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
       const Item<P> it = item_of<P>(t);
       const int enb = neighbour_of(bc, 0, m.C->K, it.d, it.side ? 1 : -1);
       const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
-#pragma unroll
-      for (int v = 0; v < 5; ++v) cp_async4(h + v * haloN + t, m.qf + v * N + gnb);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) cp_async4(h + (5 + i) * haloN + t, m.vis + face_vis_index(it.d, i) * N + gnb);
+      switch (it.d) {
+        case 0: copy_face_data<0>(m.qf, m.vis, N, gnb, h + t, haloN); break;
+        case 1: copy_face_data<1>(m.qf, m.vis, N, gnb, h + t, haloN); break;
+        default: copy_face_data<2>(m.qf, m.vis, N, gnb, h + t, haloN);
+      }
     }
     cp_async_commit();
   };

@@ -15,6 +15,8 @@
 
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 #include "dg_common.h"
 #include "nn_gemm.h"
@@ -308,7 +310,51 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// A tensor map only encodes an address, a shape, strides and a box, so maps are cached
+// on exactly those: a repeated GEMM (every layer of every training step and RK stage)
+// skips the driver encode.
+struct MapKey {
+  uintptr_t ptr;
+  long long rows, cols, ld;
+  int box_rows;
+  bool operator==(const MapKey& o) const {
+    return ptr == o.ptr && rows == o.rows && cols == o.cols && ld == o.ld && box_rows == o.box_rows;
+  }
+};
+struct MapKeyHash {
+  size_t operator()(const MapKey& k) const {
+    size_t h = std::hash<uintptr_t>()(k.ptr);
+    for (long long v : {k.rows, k.cols, k.ld, (long long)k.box_rows}) h = h * 1000003u ^ std::hash<long long>()(v);
+    return h;
+  }
+};
+std::mutex g_map_mu;
+std::unordered_map<MapKey, CUtensorMap, MapKeyHash> g_map_cache;
+constexpr size_t kMapCacheMax = 4096;
+
+int encode_map(CUtensorMap* map, const __nv_bfloat16* ptr, long long rows, long long cols, long long ld,
+               int box_rows);
+
 int make_map(CUtensorMap* map, const __nv_bfloat16* ptr, long long rows, long long cols, long long ld, int box_rows) {
+  const MapKey key{reinterpret_cast<uintptr_t>(ptr), rows, cols, ld, box_rows};
+  {
+    std::lock_guard<std::mutex> lock(g_map_mu);
+    auto it = g_map_cache.find(key);
+    if (it != g_map_cache.end()) {
+      *map = it->second;
+      return DG_OK;
+    }
+  }
+  int rc = encode_map(map, ptr, rows, cols, ld, box_rows);
+  if (rc) return rc;
+  std::lock_guard<std::mutex> lock(g_map_mu);
+  if (g_map_cache.size() >= kMapCacheMax) g_map_cache.clear();
+  g_map_cache.emplace(key, *map);
+  return DG_OK;
+}
+
+int encode_map(CUtensorMap* map, const __nv_bfloat16* ptr, long long rows, long long cols, long long ld,
+               int box_rows) {
   auto fn = encode_fn();
   if (!fn) return fail(DG_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   if ((reinterpret_cast<uintptr_t>(ptr) & 15) || (ld % 8)) return fail(DG_ERR_INVALID_ARG, "GEMM operand misaligned");
