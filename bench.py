@@ -103,6 +103,66 @@ def measured_traffic(kernel, workload):
     return rec.get("dram_bytes_per_launch")
 
 
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback"
+
+
+def nn_measure(stream, steps=100):
+    """Forcing network of the corrected P=3 run (5 x 64 = 320 inputs and outputs, 4 hidden
+    layers of 512, batch 4096): one training step (forward, MSE, backward, Adam) and one
+    forcing evaluation on a 16^3 P=3 state, timed with CUDA events."""
+    import torch
+
+    from paper_2207_11571_gb300 import dg, inputs, nn
+    feat, width, hidden, batch = 320, 512, 4, 4096
+    dims = [feat] + [width] * hidden + [feat]
+    flop_fwd = 2 * batch * sum(dims[i] * dims[i + 1] for i in range(len(dims) - 1))
+    net = nn.nn_create(feat, feat, width, hidden, 0, 5, batch, inputs.uniform_draws(dims, 7))
+    rows = 4 * batch
+    X = torch.from_numpy(inputs.normal((rows, feat), 8).astype("float32")).cuda()
+    Y = torch.from_numpy(inputs.normal((rows, feat), 9).astype("float32")).cuda()
+    nn.nn_compute_scalers(net, X, Y)
+    perm = torch.from_numpy(inputs.epoch_permutation(rows, 7, 0)).cuda()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(5):
+        nn.nn_train_step(net, X, Y, perm[:batch], want_loss=False, stream=stream)
+    e0.record(stream)
+    for i in range(steps):
+        j = (i % 4) * batch
+        nn.nn_train_step(net, X, Y, perm[j:j + batch], want_loss=False, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_us = e0.elapsed_time(e1) / steps * 1e3
+    c = dg.dg_create(16, 3, RE, MACH, PR, 0, precision=dg.DG_PREC_FP32)
+    N = dg.dg_sizes(c)[0]
+    q = torch.empty(5 * N, dtype=torch.float64, device="cuda")
+    dg.dg_init_tgv(c, q)
+    s = torch.empty(5 * N, dtype=torch.float32, device="cuda")
+    for i in range(5):
+        nn.nn_forcing_infer(net, c, q, s, stream)
+    e0.record(stream)
+    for i in range(steps):
+        nn.nn_forcing_infer(net, c, q, s, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    infer_us = e0.elapsed_time(e1) / steps * 1e3
+    dg.dg_destroy(c)
+    nn.nn_destroy(net)
+    peak, kind = bf16_peak()
+    tr = 3 * flop_fwd / (train_us * 1e-6) / 1e12
+    inf = flop_fwd / (infer_us * 1e-6) / 1e12
+    return {"network": "320-512x4-320, batch 4096 (16^3 elements at P=3)",
+            "train_step_us": round(train_us, 1), "train_tflops": round(tr, 1),
+            "forcing_infer_us": round(infer_us, 1), "forcing_infer_tflops": round(inf, 1),
+            "note": "forcing_infer includes the phase-A stage-state launch; tensor work is the 5 GEMMs",
+            "roofline": {"bound": "tensor", "peak": peak, "unit": "TFLOP/s", "peak_source": kind,
+                         "train_frac": round(tr / peak, 4), "infer_frac": round(inf / peak, 4)}}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -301,6 +361,8 @@ def run_ours(args, rank, ws):
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                "seconds": round(secs, 2)}
 
+    nn_line = nn_measure(stream)
+
     per_workload = {}
     for (K, P), n, p in zip(WORKLOAD, nodes, prof):
         per_workload[f"{K}^3/P{P}"] = {"nodes": n, "dof_stage_per_s_kernels":
@@ -317,7 +379,7 @@ def run_ours(args, rank, ws):
                            "nodes": nodes, "l2": "working set per mesh 190-400 MB > 129 MB L2 (no flush)",
                            "elems_per_block": tuned,
                            "parallelism": f"replicas x{ws}", "per_workload": per_workload},
-                "roofline": roofline, "kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "kernels": per_kernel, "network": nn_line, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 6 * len(WORKLOAD) * args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0

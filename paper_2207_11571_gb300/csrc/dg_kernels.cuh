@@ -316,8 +316,29 @@ __device__ __forceinline__ void interface_item(const T so[5], const T to[4], con
   T fo[5], fnb[5], fvo[5], fvn[5], diss[5];
   euler_flux(so, wo, C.Hc, D, fo);
   euler_flux(sn, wn, C.Hc, D, fnb);
-  if (side) roe_dissipation(so, wo, sn, wn, D, C.gm1, C.Hc, diss);
-  else roe_dissipation(sn, wn, so, wo, D, C.gm1, C.Hc, diss);
+  {
+    // the face's left and right states by selection, not by branching: the two sides of
+    // a face sit in one warp, and a branch would run the Roe solver twice
+    T sL[5], sR[5];
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+      sL[v] = side ? so[v] : sn[v];
+      sR[v] = side ? sn[v] : so[v];
+    }
+    Prim<T> wL, wR;
+    wL.rho = side ? wo.rho : wn.rho;
+    wR.rho = side ? wn.rho : wo.rho;
+    wL.ir = side ? wo.ir : wn.ir;
+    wR.ir = side ? wn.ir : wo.ir;
+    wL.pp = side ? wo.pp : wn.pp;
+    wR.pp = side ? wn.pp : wo.pp;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      wL.v[i] = side ? wo.v[i] : wn.v[i];
+      wR.v[i] = side ? wn.v[i] : wo.v[i];
+    }
+    roe_dissipation(sL, wL, sR, wR, D, C.gm1, C.Hc, diss);
+  }
   viscous_flux4(to, wo.v, fvo);
   viscous_flux4(tn, wn.v, fvn);
   const T lift = C.s2h * C.winv;

@@ -1,6 +1,7 @@
 // Corrective-forcing network (Sec. 2.2, Fig. 2): model state, CUDA-core kernels around
 // the tensor-core GEMMs (input scaling, loss, gradient preparation, transposes, Adam)
 // and the C ABI of include/dgnn_nn.h.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -37,6 +38,8 @@ struct nn_model {
   bf16* dyb = nullptr;          // [max_batch][pad(max dim)]
   bf16* dyT = nullptr;          // [max dim][bpad]
   double* loss_part = nullptr;  // reduction partials
+  float* gpart = nullptr;       // [bpad / 32][max dim] bias-gradient partial sums
+  float* gws = nullptr;         // [kMaxSplits][max dim]^2 split-K partial weight gradients
   double* loss_dev = nullptr;
   double* loss_host = nullptr;  // pinned
   int* err = nullptr;           // device error flag of the tensor-core kernels
@@ -53,8 +56,9 @@ namespace dgnn {
 
 namespace {
 
-constexpr int kLossBlocks = 256;
-constexpr int kLossThreads = 256;
+constexpr int kLossBlocks = 1024;
+constexpr int kMaxSplits = 8;   // split-K factor bound of the weight-gradient GEMMs
+constexpr int kLossThreads = 128;
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -112,28 +116,32 @@ __global__ void k_prep_state_f32(const float* __restrict__ qf, long long N, int 
 __global__ void k_loss(const float* __restrict__ y, const float* __restrict__ Y, const int64_t* __restrict__ idx,
                        int rows, int n, const float* __restrict__ mean, const float* __restrict__ sd,
                        float* __restrict__ dy, double* __restrict__ partial) {
-  __shared__ double sh[kLossThreads];
-  double acc = 0.0;
-  const long long total = (long long)rows * n;
-  const float g = 2.f / (float)total;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(t / n), f = (int)(t - (long long)r * n);
+  // rows over blocks, features over threads; FP32 sums of a few squares per thread, a
+  // warp-shuffle reduction, then the warps' sums added in FP64 in a fixed order
+  __shared__ float wsum[kLossThreads / 32];
+  float acc = 0.f;
+  const float g = 2.f / ((float)rows * (float)n);
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
     const long long src = idx ? idx[r] : r;
-    const float ts = (Y[src * n + f] - mean[f]) / sd[f];
-    const float diff = y[t] - ts;
-    dy[t] = g * diff;
-    acc += (double)diff * (double)diff;
+    const float* Yr = Y + src * n;
+    const long long o = (long long)r * n;
+    for (int f = threadIdx.x; f < n; f += blockDim.x) {
+      const float ts = (Yr[f] - mean[f]) / sd[f];
+      const float diff = y[o + f] - ts;
+      dy[o + f] = g * diff;
+      acc += diff * diff;
+    }
   }
-  sh[threadIdx.x] = acc;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x / 32] = acc;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kLossThreads / 32; ++w) t += (double)wsum[w];
+    partial[blockIdx.x] = t;
   }
-  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
 }
-
 __global__ void k_sum_partials(const double* __restrict__ partial, int n, double scale, double* __restrict__ out) {
   __shared__ double sh[kLossThreads];
   double acc = 0.0;
@@ -147,38 +155,62 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int n, double
   if (threadIdx.x == 0) *out = sh[0] * scale;
 }
 
-// From the FP32 gradient g[rows][n]: bf16 copy [rows][ldb] (zero padded), bf16 transpose
-// [n][ldt] (ldt = padded rows, zero padded), column sums db[n] in a fixed order.
-// One block of 32 x 8 threads per 32-column strip; rows walked in 32-row tiles.
+// Gradient of one layer's output g[rows][n] (FP32) -> bf16 copies gb[rows][ldb] (columns
+// n..ldb-1 zero) and gT[n][ldt] (rows past `rows` zero), and per-tile column sums
+// part[tile][n] of the bias gradient.  One 32 x 32 tile per block (2D grid over
+// columns and row tiles), so every SM takes part.
 __global__ void k_grad_prep(const float* __restrict__ g, int rows, int n, int ldb, int ldt, bf16* __restrict__ gb,
-                            bf16* __restrict__ gT, float* __restrict__ db) {
+                            bf16* __restrict__ gT, float* __restrict__ part) {
   __shared__ float tile[32][33];
   __shared__ float colsum[8][32];
-  const int c0 = blockIdx.x * 32;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
   float cs = 0.f;
-  const int rows_pad = ldt;
-  for (int r0 = 0; r0 < rows_pad; r0 += 32) {
-    for (int k = ty; k < 32; k += 8) {
-      const int r = r0 + k, c = c0 + tx;
-      float v = (r < rows && c < n) ? g[(long long)r * n + c] : 0.f;
-      tile[k][tx] = v;
-      if (r < rows && c < ldb) gb[(long long)r * ldb + c] = __float2bfloat16_rn(v);
-      if (r < rows && c < n) cs += v;
-    }
-    __syncthreads();
-    for (int k = ty; k < 32; k += 8) {
-      const int c = c0 + k, r = r0 + tx;
-      if (c < n && r < ldt) gT[(long long)c * ldt + r] = __float2bfloat16_rn(tile[tx][k]);
-    }
-    __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int r = r0 + k, c = c0 + tx;
+    const float v = (r < rows && c < n) ? g[(long long)r * n + c] : 0.f;
+    tile[k][tx] = v;
+    if (r < rows && c < ldb) gb[(long long)r * ldb + c] = __float2bfloat16_rn(v);
+    cs += v;
   }
   colsum[ty][tx] = cs;
   __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int c = c0 + k, r = r0 + tx;
+    if (c < n && r < ldt) gT[(long long)c * ldt + r] = __float2bfloat16_rn(tile[tx][k]);
+  }
   if (ty == 0 && c0 + tx < n) {
-    float s = 0.f;
-    for (int k = 0; k < 8; ++k) s += colsum[k][tx];
-    db[c0 + tx] = s;
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += colsum[k][tx];
+    part[(long long)blockIdx.y * n + c0 + tx] = t;
+  }
+}
+
+// out[i] = sum over splits z of part[z][i], in split order (deterministic split-K sum).
+__global__ void k_split_sum(const float* __restrict__ part, int splits, long long count, float* __restrict__ out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float s = 0.f;
+  for (int z = 0; z < splits; ++z) s += part[z * count + i];
+  out[i] = s;
+}
+
+// db[c] = sum over row tiles of part[tile][c]: 32 columns per block, each of 32 thread
+// rows sums every 32nd tile, then the 32 partial sums are added in row order
+// (deterministic).
+__global__ void k_col_sum(const float* __restrict__ part, int tiles, int n, float* __restrict__ db) {
+  __shared__ float sh[32][33];
+  const int c = blockIdx.x * 32 + threadIdx.x;
+  float s = 0.f;
+  if (c < n)
+    for (int t = threadIdx.y; t < tiles; t += 32) s += part[(long long)t * n + c];
+  sh[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < n) {
+    float t = 0.f;
+    for (int k = 0; k < 32; ++k) t += sh[k][threadIdx.x];
+    db[c] = t;
   }
 }
 
@@ -198,26 +230,45 @@ __global__ void k_transpose_bf16(const bf16* __restrict__ a, int rows, int n, in
   }
 }
 
-// Adam on one parameter tensor [out][in] (in = 1 for biases), refreshing the bf16 copies
-// Wb[out][ldb] and Wt[in][ldt] when given.
-__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                       long long count, int in, float lr, float b1, float b2, float eps, float bc1, float bc2,
-                       bf16* __restrict__ Wb, int ldb, bf16* __restrict__ Wt, int ldt) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= count) return;
-  const float gi = g[t];
-  const float mi = b1 * m[t] + (1.f - b1) * gi;
-  const float vi = b2 * v[t] + (1.f - b2) * gi * gi;
-  m[t] = mi;
-  v[t] = vi;
-  const float mh = mi / bc1, vh = vi / bc2;
-  const float w = p[t] - lr * mh / (sqrtf(vh) + eps);
-  p[t] = w;
-  if (Wb) {
-    const int o = (int)(t / in), i = (int)(t - (long long)o * in);
+// Adam (Kingma & Ba) on every parameter tensor of the network in one launch: segment j
+// is a tensor [out][in] (in = 1 for biases); weight segments also refresh their bf16
+// copies Wb[out][ldb] and Wt[in][ldt].  Blocks are assigned to segments by prefix counts.
+constexpr int kAdamMaxSeg = 18;
+struct AdamSeg {
+  float *p, *g, *m, *v;
+  long long count;
+  int in;
+  bf16* Wb;
+  int ldb;
+  bf16* Wt;
+  int ldt;
+};
+struct AdamTable {
+  int n;
+  int block_start[kAdamMaxSeg + 1];
+  AdamSeg seg[kAdamMaxSeg];
+  float lr, b1, b2, eps, bc1, bc2;
+};
+
+__global__ void k_adam(const __grid_constant__ AdamTable tb) {
+  int j = 0;
+  while (j + 1 < tb.n && (int)blockIdx.x >= tb.block_start[j + 1]) ++j;
+  const AdamSeg& S = tb.seg[j];
+  const long long t = (blockIdx.x - tb.block_start[j]) * (long long)blockDim.x + threadIdx.x;
+  if (t >= S.count) return;
+  const float gi = S.g[t];
+  const float mi = tb.b1 * S.m[t] + (1.f - tb.b1) * gi;
+  const float vi = tb.b2 * S.v[t] + (1.f - tb.b2) * gi * gi;
+  S.m[t] = mi;
+  S.v[t] = vi;
+  const float mh = mi / tb.bc1, vh = vi / tb.bc2;
+  const float w = S.p[t] - tb.lr * mh / (sqrtf(vh) + tb.eps);
+  S.p[t] = w;
+  if (S.Wb) {
+    const int o = (int)(t / S.in), i = (int)(t - (long long)o * S.in);
     const bf16 wb = __float2bfloat16_rn(w);
-    Wb[(long long)o * ldb + i] = wb;
-    Wt[(long long)i * ldt + o] = wb;
+    S.Wb[(long long)o * S.ldb + i] = wb;
+    S.Wt[(long long)i * S.ldt + o] = wb;
   }
 }
 
@@ -299,7 +350,7 @@ void free_model(nn_model* m) {
   for (int l = 0; l < 10; ++l) { cudaFree(m->act[l]); cudaFree(m->actT[l]); }
   cudaFree(m->mean_in); cudaFree(m->std_in); cudaFree(m->mean_out); cudaFree(m->std_out);
   cudaFree(m->y); cudaFree(m->dy); cudaFree(m->dx); cudaFree(m->dyb); cudaFree(m->dyT);
-  cudaFree(m->loss_part); cudaFree(m->loss_dev); cudaFree(m->err);
+  cudaFree(m->loss_part); cudaFree(m->loss_dev); cudaFree(m->err); cudaFree(m->gpart); cudaFree(m->gws);
   cudaFree(m->mean_in_d); cudaFree(m->mean_shift);
   if (m->loss_host) cudaFreeHost(m->loss_host);
   delete m;
@@ -360,6 +411,8 @@ int alloc_model(const nn_desc* d, nn_model** out) {
   A((void**)&m->mean_in_d, d->n_in * 8);
   A((void**)&m->mean_shift, d->n_in * 4);
   A((void**)&m->loss_part, kLossBlocks * 8);
+  A((void**)&m->gpart, (size_t)(m->bpad / 32) * m->maxdim * 4);
+  A((void**)&m->gws, (size_t)kMaxSplits * m->maxdim * m->maxdim * 4);
   A((void**)&m->loss_dev, 8);
   A((void**)&m->err, 4);
   if (e == cudaSuccess) e = cudaMallocHost(&m->loss_host, 8);
@@ -593,19 +646,37 @@ int nn_train_step(nn_model* m, const float* X, const float* Y, const int64_t* id
   for (int l = L - 1; l >= 0; --l) {
     const int o = m->dims[l + 1], in = m->dims[l];
     const int ldb = round_up(o, 64);
-    dim3 gp((o + 31) / 32), bt(32, 8);
-    k_grad_prep<<<gp, bt, 0, st>>>(g, batch, o, ldb, m->bpad, m->dyb, m->dyT, m->gb[l]);
+    const int tiles = m->bpad / 32;
+    dim3 gp(ldb / 32, tiles), bt(32, 8);
+    k_grad_prep<<<gp, bt, 0, st>>>(g, batch, o, ldb, m->bpad, m->dyb, m->dyT, m->gpart);
+    DG_CUDA(cudaGetLastError());
+    k_col_sum<<<(o + 31) / 32, dim3(32, 32), 0, st>>>(m->gpart, tiles, o, m->gb[l]);
     DG_CUDA(cudaGetLastError());
     dim3 gt((in + 31) / 32, (m->bpad + 31) / 32);
     k_transpose_bf16<<<gt, bt, 0, st>>>(m->act[l], batch, in, m->pad[l], m->bpad, m->actT[l]);
     DG_CUDA(cudaGetLastError());
-    // dW = g^T act : M = o, N = in, K = batch
+    // dW = g^T act : M = o, N = in, K = batch.  Few output tiles and a long K: split K
+    // so that the CTAs cover the SMs, then sum the partial products in a fixed order.
     GemmEpilogue ew;
     ew.kind = kGemmF32;
-    ew.out = m->gW[l];
     ew.ldo = in;
+    const int tiles_mn = ((o + 127) / 128) * ((in + gemm_pick_bn(o, in) - 1) / gemm_pick_bn(o, in));
+    const int kslices = (batch + 63) / 64;
+    const int splits = std::max(1, std::min({kMaxSplits, kslices, 152 / tiles_mn}));
+    if (splits > 1) {
+      ew.out = m->gws;
+      ew.splits = splits;
+      ew.split_stride = (long long)o * in;
+    } else {
+      ew.out = m->gW[l];
+    }
     rc = gemm_bf16(m->dyT, m->bpad, m->actT[l], m->bpad, o, in, batch, ew, m->err, st);
     if (rc) return rc;
+    if (splits > 1) {
+      const long long cnt = (long long)o * in;
+      k_split_sum<<<blocks_for(cnt, 256), 256, 0, st>>>(m->gws, splits, cnt, m->gW[l]);
+      DG_CUDA(cudaGetLastError());
+    }
     if (l > 0) {
       // d act = g W, masked by the ReLU of the layer that produced act[l]
       GemmEpilogue ex;
@@ -623,16 +694,28 @@ int nn_train_step(nn_model* m, const float* X, const float* Y, const int64_t* id
   ++m->adam_t;
   const float bc1 = 1.f - std::pow(a.beta1, (float)m->adam_t);
   const float bc2 = 1.f - std::pow(a.beta2, (float)m->adam_t);
+  AdamTable at{};
+  at.lr = a.lr;
+  at.b1 = a.beta1;
+  at.b2 = a.beta2;
+  at.eps = a.eps;
+  at.bc1 = bc1;
+  at.bc2 = bc2;
+  int blocks = 0;
   for (int l = 0; l < L; ++l) {
     const long long cw = (long long)m->dims[l] * m->dims[l + 1];
-    k_adam<<<blocks_for(cw, 256), 256, 0, st>>>(m->W[l], m->gW[l], m->mW[l], m->vW[l], cw, m->dims[l], a.lr, a.beta1,
-                                                a.beta2, a.eps, bc1, bc2, m->Wb[l], m->pad[l], m->Wt[l], m->pad[l + 1]);
-    DG_CUDA(cudaGetLastError());
+    at.block_start[at.n] = blocks;
+    at.seg[at.n++] = AdamSeg{m->W[l], m->gW[l], m->mW[l], m->vW[l], cw, m->dims[l], m->Wb[l], m->pad[l], m->Wt[l],
+                             m->pad[l + 1]};
+    blocks += (int)blocks_for(cw, 256);
     const long long cb = m->dims[l + 1];
-    k_adam<<<blocks_for(cb, 256), 256, 0, st>>>(m->b[l], m->gb[l], m->mb[l], m->vb[l], cb, 1, a.lr, a.beta1, a.beta2,
-                                                a.eps, bc1, bc2, nullptr, 0, nullptr, 0);
-    DG_CUDA(cudaGetLastError());
+    at.block_start[at.n] = blocks;
+    at.seg[at.n++] = AdamSeg{m->b[l], m->gb[l], m->mb[l], m->vb[l], cb, 1, nullptr, 0, nullptr, 0};
+    blocks += (int)blocks_for(cb, 256);
   }
+  at.block_start[at.n] = blocks;
+  k_adam<<<blocks, 256, 0, st>>>(at);
+  DG_CUDA(cudaGetLastError());
   if (loss_out) {
     DG_CUDA(cudaMemcpyAsync(m->loss_host, m->loss_dev, 8, cudaMemcpyDeviceToHost, st));
     rc = check_err(m, st);

@@ -172,6 +172,18 @@ __device__ __forceinline__ void epilogue_chunk(const GemmEpilogue& ep, int m, in
     return;
   }
   float* out = static_cast<float*>(ep.out) + (size_t)m * ep.ldo + n;
+  if (ep.kind == kGemmMaskF32 && full && (ep.ldm % 8 == 0)) {
+    // 16 mask values in two 16-byte loads
+    const uint4* mp = reinterpret_cast<const uint4*>(ep.mask + (size_t)m * ep.ldm + n);
+    const uint4 lo = mp[0], hi = mp[1];
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const uint32_t h = (w[i / 2] >> (16 * (i % 2))) & 0xFFFFu;
+      // bf16 > 0: sign bit clear and not +0
+      v[i] = (h != 0u && (h & 0x8000u) == 0u) ? v[i] : 0.f;
+    }
+  } else {
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
     if (n + i >= N) break;
@@ -187,6 +199,7 @@ __device__ __forceinline__ void epilogue_chunk(const GemmEpilogue& ep, int m, in
       }
     }
     v[i] = x;
+  }
   }
   if (full && (ep.ldo % 4 == 0)) {
 #pragma unroll
@@ -212,7 +225,11 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-  const int KB = (K + kBK - 1) / kBK;
+  // this CTA's run of 64-wide K slices (split-K over gridDim.z)
+  const int KBall = (K + kBK - 1) / kBK;
+  const int kb0 = (int)((long long)blockIdx.z * KBall / gridDim.z);
+  const int KB = (int)((long long)(blockIdx.z + 1) * KBall / gridDim.z) - kb0;
+  if (blockIdx.z > 0) ep.out = static_cast<float*>(ep.out) + blockIdx.z * ep.split_stride;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -243,8 +260,8 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         uint8_t* a = base + s * S::kStageBytes;
         uint8_t* b = a + S::kABytes;
         mbar_expect_tx(&full[s], S::kStageBytes);
-        tma_load_2d(a, &tmA, &full[s], kb * kBK, m0);
-        tma_load_2d(b, &tmB, &full[s], kb * kBK, n0);
+        tma_load_2d(a, &tmA, &full[s], (kb0 + kb) * kBK, m0);
+        tma_load_2d(b, &tmB, &full[s], (kb0 + kb) * kBK, n0);
         issued = kb + 1;
       }
       // drain: every issued copy must land before the CTA exits (bounded)
@@ -384,7 +401,7 @@ int launch_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb
     DG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     configured = true;
   }
-  dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN);
+  dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, ep.splits);
   kern<<<grid, kThreads, smem, st>>>(ma, mb, M, N, K, ep, err);
   DG_CUDA(cudaGetLastError());
   return DG_OK;
@@ -406,6 +423,8 @@ int gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, 
   if (!ep.out || ep.ldo < N) return fail(DG_ERR_INVALID_ARG, "gemm: bad output");
   if (ep.kind == kGemmBiasReluBf16 && (ep.ldo % 8)) return fail(DG_ERR_INVALID_ARG, "gemm: bf16 output ld % 8");
   if (ep.kind == kGemmMaskF32 && !ep.mask) return fail(DG_ERR_INVALID_ARG, "gemm: mask missing");
+  if (ep.splits < 1 || ep.splits > (K + kBK - 1) / kBK || (ep.splits > 1 && ep.kind != kGemmF32))
+    return fail(DG_ERR_INVALID_ARG, "gemm: bad split-K");
   switch (gemm_pick_bn(M, N)) {
     case 256: return launch_gemm<256>(A, lda, B, ldb, M, N, K, ep, err_flag, st);
     case 128: return launch_gemm<128>(A, lda, B, ldb, M, N, K, ep, err_flag, st);

@@ -27,6 +27,10 @@ struct GemmEpilogue {
   void* out = nullptr;
   int ldo = 0;
   int relu = 0;  // f32 kinds: apply max(., 0) after the bias
+  // Split-K (kGemmF32 only): the K range is cut into `splits` equal runs of 64-wide
+  // slices; split z writes its partial product to out + z * split_stride (elements).
+  int splits = 1;
+  long long split_stride = 0;
 };
 
 // C[M x N] = A[M x K] B[N x K]^T with the given epilogue.  A and B are row-major bf16
