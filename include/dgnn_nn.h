@@ -66,6 +66,14 @@ int nn_compute_scalers(nn_model* net, const float* X, const float* Y, int64_t ro
  * n_out (DEVICE float).  rows <= max_batch. */
 int nn_forward(const nn_model* net, const float* X, float* S, int rows, void* stream);
 
+/* Implementation switch, no counterpart in the paper: enable != 0 runs inference
+ * (nn_forward, nn_forcing_infer, forcing inside dg_rhs / dg_rk3_step) through one fused
+ * kernel that keeps every layer's activations on the SM (128 rows per CTA), when every
+ * width is a multiple of 16 in [16, 512] and n_hidden <= 8; 0 (the default) runs one
+ * tensor-core GEMM per layer.  Both compute the same network in BF16 with FP32
+ * accumulation. */
+int nn_set_fused(nn_model* net, int enable);
+
 /* s = forcing of every element of the state q of context ctx (dgnn.h layout), written as
  * rows e = 0 .. K^3 - 1 of n_vars (P+1)^3 floats (DEVICE).  Requires n_in = n_out =
  * n_vars (P+1)^3.  Elements are processed in chunks of max_batch. */

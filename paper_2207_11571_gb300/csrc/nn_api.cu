@@ -13,6 +13,7 @@
 #include "dg_device.cuh"
 #include "nn_bridge.h"
 #include "nn_gemm.h"
+#include "nn_mlp.h"
 
 using bf16 = __nv_bfloat16;
 
@@ -44,6 +45,7 @@ struct nn_model {
   double* loss_host = nullptr;  // pinned
   int* err = nullptr;           // device error flag of the tensor-core kernels
   int maxdim = 0;
+  bool fused = false;           // inference through the fused multi-layer kernel (nn_set_fused)
   // input means for scaling network inputs taken from solver states: in FP64 (FP64 state)
   // and shifted by the reference state of an FP32 context (cached for one reference)
   double* mean_in_d = nullptr;
@@ -316,6 +318,17 @@ inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) /
 // Forward through all layers for `rows` rows whose scaled inputs are in act[0].
 // last: if S != null, unscaled forcing into S (ld n_out); else scaled output into m->y.
 int forward_layers(const nn_model* m, int rows, float* S, cudaStream_t st) {
+  if (S && m->fused && mlp_fused_ok(m->dims, m->L)) {
+    // inference: all layers in one kernel, activations kept on the SM
+    const bf16* W[kMlpMaxLayers];
+    const float* B[kMlpMaxLayers];
+    for (int l = 0; l < m->L; ++l) {
+      W[l] = m->Wb[l];
+      B[l] = m->b[l];
+    }
+    return mlp_forward_fused(m->act[0], m->pad[0], W, m->pad, B, m->dims, m->L, rows, m->std_out, m->mean_out, S,
+                             m->dims[m->L], m->err, st);
+  }
   for (int l = 0; l < m->L; ++l) {
     GemmEpilogue ep;
     ep.bias = m->b[l];
@@ -598,6 +611,12 @@ int nn_compute_scalers(nn_model* m, const float* X, const float* Y, int64_t rows
     DG_CUDA(cudaMemcpy(which ? m->std_out : m->std_in, sd.data(), n * 4, cudaMemcpyHostToDevice));
   }
   return means_changed(m);
+}
+
+int nn_set_fused(nn_model* m, int enable) {
+  if (!m) return fail(DG_ERR_INVALID_ARG, "nn_set_fused: NULL model");
+  m->fused = enable != 0;
+  return DG_OK;
 }
 
 int nn_forward(const nn_model* m, const float* X, float* S, int rows, void* stream) {

@@ -41,6 +41,10 @@ struct GemmEpilogue {
 int gemm_bf16(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb, int M, int N, int K,
               const GemmEpilogue& ep, int* err_flag, cudaStream_t st);
 
+// 2D tensor map of a row-major bf16 matrix [rows][cols] (leading dimension ld elements),
+// box of 64 columns x box_rows rows with the 128-byte swizzle; cached.  Returns a dg_status.
+int make_map(CUtensorMap* map, const __nv_bfloat16* ptr, long long rows, long long cols, long long ld, int box_rows);
+
 // Tile width in N chosen for the problem (64, 128 or 256).
 int gemm_pick_bn(int M, int N);
 

@@ -28,6 +28,7 @@ _SIGS = {
     "nn_get_scalers": [_P, _P, _P, _P, _P],
     "nn_compute_scalers": [_P, _P, _P, ctypes.c_int64, _P],
     "nn_forward": [_P, _P, _P, _I, _P],
+    "nn_set_fused": [_P, _I],
     "nn_forcing_infer": [_P, _P, _P, _P, _P],
     "nn_train_step": [_P, _P, _P, _P, _I, ctypes.POINTER(nn_adam), ctypes.POINTER(ctypes.c_float), _P],
     "nn_get_params": [_P, _I, _P, _P],
@@ -111,6 +112,12 @@ def nn_compute_scalers(net, X, Y, stream=None):
 def nn_forward(net, X, S, stream=None):
     dg = _dg()
     dg.check(dg.lib().nn_forward(_h(net), dg.ptr(X), dg.ptr(S), int(X.shape[0]), dg.stream_ptr(stream)))
+
+
+def nn_set_fused(net, enable=True):
+    """Inference through the fused multi-layer kernel (default) or one GEMM per layer."""
+    dg = _dg()
+    dg.check(dg.lib().nn_set_fused(_h(net), int(bool(enable))))
 
 
 def nn_forcing_infer(net, ctx, q, s, stream=None):

@@ -92,6 +92,29 @@ def test_forward_matches_oracle(L, n_in, width, n_hidden, rows):
     nn.nn_destroy(h)
 
 
+@pytest.mark.parametrize("n_in,width,n_hidden,rows", [(320, 512, 4, 4096), (320, 256, 4, 300), (192, 512, 2, 129),
+                                                     (320, 512, 6, 512), (80, 96, 3, 257), (320, 104, 2, 200)])
+def test_fused_inference_equals_per_layer_gemms(L, n_in, width, n_hidden, rows):
+    """The fused multi-layer kernel and the one-GEMM-per-layer path compute the same network
+    (same bf16 rounding points, same K order); width 96 exercises zero-padded panels,
+    width 104 (not a multiple of 16) falls back to the per-layer path."""
+    from paper_2207_11571_gb300 import nn
+    h, _ = make_net(nn, n_in, width, n_hidden, seed=7 + width, max_batch=max(rows, 512))
+    set_random_scalers(nn, h, n_in, 3)
+    X = torch.from_numpy(inputs.normal((rows, n_in), 4).astype(np.float32)).cuda()
+    S_fused = torch.full((rows, n_in), float("nan"), dtype=torch.float32, device="cuda")
+    S_layer = torch.full_like(S_fused, float("nan"))
+    nn.nn_set_fused(h, True)
+    nn.nn_forward(h, X, S_fused)
+    nn.nn_set_fused(h, False)
+    nn.nn_forward(h, X, S_layer)
+    torch.cuda.synchronize()
+    assert torch.isfinite(S_fused).all()
+    err = ((S_fused - S_layer).norm() / S_layer.norm()).item()
+    assert err < 1e-5, err
+    nn.nn_destroy(h)
+
+
 def test_train_step_gradients_loss_and_adam_match_oracle(L):
     from paper_2207_11571_gb300 import nn
     n, width, nh, B = 320, 256, 3, 384
