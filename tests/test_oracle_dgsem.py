@@ -367,3 +367,26 @@ def test_diagnostics_dke_dt_matches_time_difference():
     ke = lambda s: dgsem.diagnostics(s, mesh, flow)['ke']
     fd = (ke(qp) - ke(qm)) / (2 * dt)
     assert abs(fd - d0['dke_dt']) < 1e-6 * abs(d0['dke_dt']) + 1e-10
+
+
+def test_operator_at_an_element_depends_only_on_elements_two_face_steps_away():
+    """The operator at element e reads its face neighbours' states and lifted gradients,
+    and those gradients read their own face neighbours: a 5^3 block of elements centred
+    on e, closed periodically, gives the same operator at e as the whole mesh (this is what
+    the full-size GPU parity tests rely on to check sampled elements)."""
+    from oracle import physics
+    from paper_2207_11571_gb300 import inputs
+    K, P = 7, 2
+    mesh = dgsem.Mesh(K, P)
+    flow = physics.Flow(Re=200.0, Mach=0.1, Pr=0.71, les=True)
+    n = P + 1
+    q = inputs.random_conserved((K, K, K, n, n, n), seed=5)
+    R = dgsem.rhs(q, mesh, flow)
+    for centre in [(0, 0, 0), (3, 6, 1), (6, 2, 4)]:
+        idx = [[(c - 2 + i) % K for i in range(5)] for c in centre]
+        qp = np.take(np.take(np.take(q, idx[0], axis=1), idx[1], axis=2), idx[2], axis=3)
+        mp = dgsem.Mesh(5, P)
+        mp.h = mesh.h
+        Rp = dgsem.rhs(qp, mp, flow)[:, 2, 2, 2]
+        ez, ey, ex = centre
+        np.testing.assert_allclose(Rp, R[:, ez, ey, ex], rtol=0, atol=1e-12 * np.abs(R).max())
