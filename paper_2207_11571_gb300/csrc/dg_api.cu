@@ -222,6 +222,14 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
   c->phys.theta_ref = c->phys.rho_ref > 0 ? c->phys.p_ref / c->phys.rho_ref : 0.0;
 
   const bool f32 = o.precision == DG_PREC_FP32;
+  if (f32) {
+    cudaError_t ec = prepare_f32_constants();
+    if (ec == cudaSuccess) ec = prepare_batch_f32_constants();
+    if (ec != cudaSuccess) {
+      delete c;
+      return cuda_fail(ec, "dg_create: constant tables");
+    }
+  }
   const size_t tsz = f32 ? sizeof(float) : sizeof(double);
   c->red_blocks = kDiagBlocks;
   cudaError_t e = cudaSuccess;

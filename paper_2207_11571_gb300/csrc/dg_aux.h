@@ -51,6 +51,11 @@ cudaError_t flux_f32(const dg_ctx* c, double* q, double* dqdt, const Forcing& f,
 cudaError_t flux_f64(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
                      double dt, double invB1, cudaStream_t st);
 
+// Derivative matrices in the constant memory of the FP32 kernels (dg_kernels_f32.cu,
+// dg_batch_f32.cu); once per device, before the first FP32 launch.
+cudaError_t prepare_f32_constants();
+cudaError_t prepare_batch_f32_constants();
+
 // Batched RK stage k for n instances of order P sharing precision and elements per block
 // (dg_batch_f32.cu / dg_batch_f64.cu): q[i] is instance i's FP64 state, dt[i] its step.
 cudaError_t batch_stage_f32(int P, dg_ctx* const* ctx, double* const* q, const double* dt, int n, int k, double A,

@@ -9,4 +9,6 @@ cudaError_t flux_f32(const dg_ctx* c, double* q, double* dqdt, const Forcing& f,
                      double dt, double invB1, cudaStream_t st) {
   return flux_t<float>(c, q, dqdt, f, mode, A, B, dt, invB1, st);
 }
+// Constant-memory tables of this unit's kernels (see upload_const_D).
+cudaError_t prepare_f32_constants() { return upload_const_D(); }
 }  // namespace dgnn

@@ -47,6 +47,26 @@ OpConst<T> make_const(const dg_ctx* c) {
   return k;
 }
 
+// Fills this translation unit's constant-memory derivative matrices (c_D32) on the
+// current device, once per device.  Synchronous: called from dg_create, outside any
+// stream capture.
+static cudaError_t upload_const_D() {
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  float h[kMaxP + 1][kMaxN1 * kMaxN1] = {};
+  for (int P = 1; P <= kMaxP; ++P) {
+    Basis1D b;
+    if (build_basis(P, &b) != 0) return cudaErrorInvalidValue;
+    for (int i = 0; i < (P + 1) * (P + 1); ++i) h[P][i] = (float)b.D[i];
+  }
+  e = cudaMemcpyToSymbol(c_D32, h, sizeof(h));
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = true;
+  return e;
+}
+
 template <typename K>
 cudaError_t set_smem(K kern, size_t smem) {
   if (smem > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -57,7 +77,9 @@ cudaError_t set_smem(K kern, size_t smem) {
 template <int P, typename T>
 size_t gradient_smem(int E) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
-  return sizeof(T) * (n2 + 4 * E * np + 4 * E * 6 * n2);
+  // FP32 at P >= 7 with one element per block adds the line-wise derivative buffer [12][np]
+  const int lines = (std::is_same<T, float>::value && P >= 7 && E == 1) ? 12 * np : 0;
+  return sizeof(T) * (n2 + 4 * E * np + 4 * E * 6 * n2 + lines);
 }
 
 template <int P, typename T>

@@ -77,6 +77,7 @@ extern "C" int dg_rhs_noalloc(int K, int P, double Re, double Mach, double Pr, i
   double* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
   if (rc) return rc;
+  if (precision == DG_PREC_FP32) DG_CUDA(prepare_f32_constants());
 
   // A solver description on the host stack, with its workspace in the scratch array.
   dg_ctx c;
