@@ -120,11 +120,21 @@ def generate_pairs(args, ctx_hi, q_hi, ctx_lo, dt_lo, ratio, n_steps, first_var,
 
 
 def train(args, X, Y, first_var, n_vars):
+    """Trains on the pairs.  With --init_net the network (weights and scalers) starts from a
+    saved one trained at another time window or Re, the paper's transfer learning
+    (retraining from earlier weights needs far fewer epochs); otherwise from seeded
+    He-uniform weights and the pairs' scalers."""
     feat = X.shape[1]
     dims = [feat] + [args.width] * args.hidden + [feat]
-    net = nn.nn_create(feat, feat, args.width, args.hidden, first_var, n_vars, args.batch,
-                       inputs.uniform_draws(dims, args.seed))
-    nn.nn_compute_scalers(net, X, Y)
+    if args.init_net:
+        net = nn.nn_load(args.init_net, args.batch)
+        d = nn.nn_get_desc(net)
+        if (d.n_in, d.n_out, d.first_var, d.n_vars) != (feat, feat, first_var, n_vars):
+            raise ValueError("--init_net does not match the features of this run")
+    else:
+        net = nn.nn_create(feat, feat, args.width, args.hidden, first_var, n_vars, args.batch,
+                           inputs.uniform_draws(dims, args.seed))
+        nn.nn_compute_scalers(net, X, Y)
     rows = X.shape[0]
     losses = []
     t0 = time.perf_counter()
@@ -200,6 +210,8 @@ def parse(argv=None):
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=2207)
+    ap.add_argument("--init_net", type=str, default="", help="start training from this saved network")
+    ap.add_argument("--save_net", type=str, default="", help="save the trained network here")
     ap.add_argument("--out", type=str, default="experiment.json")
     return ap.parse_args(argv)
 
@@ -327,6 +339,8 @@ def run(args):
     if args.out:
         with open(args.out, "w") as f:
             json.dump(out, f, indent=1)
+    if args.save_net:
+        nn.nn_save(net, args.save_net)
     nn.nn_destroy(net)
     for c in list(plain_ctx.values()) + [ctx_lo, ctx_hi]:
         dg.dg_destroy(c)

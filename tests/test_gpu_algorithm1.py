@@ -14,15 +14,23 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+COMMON = ["--K", "8", "--P_hi", "6", "--P_lo", "3", "--plain", "3", "--Re", "200", "--eval_start", "window_start",
+          "--sample", "0.05", "--width", "256", "--hidden", "4", "--batch", "1024", "--window_precision", "fp64",
+          "--out", ""]
+
+
 @pytest.fixture(scope="module")
-def experiment():
+def saved_net(tmp_path_factory):
+    return str(tmp_path_factory.mktemp("net") / "forcing.dgnn")
+
+
+@pytest.fixture(scope="module")
+def experiment(saved_net):
     from tests.libbuild import ensure_built
     ensure_built()
     from paper_2207_11571_gb300 import experiment as ex
-    args = ex.parse(["--K", "8", "--P_hi", "6", "--P_lo", "3", "--plain", "3",
-                     "--Re", "200", "--t_train", "0.5", "--t_train_end", "1.0", "--t_end", "1.0",
-                     "--eval_start", "window_start", "--sample", "0.05", "--width", "256", "--hidden", "4",
-                     "--epochs", "30", "--batch", "1024", "--window_precision", "fp64", "--out", ""])
+    args = ex.parse(COMMON + ["--t_train", "0.5", "--t_train_end", "1.0", "--t_end", "1.0", "--epochs", "30",
+                              "--save_net", saved_net])
     return ex.run(args)
 
 
@@ -36,3 +44,14 @@ def test_corrected_run_beats_plain_low_order(experiment):
     assert corr["name"] == "P3+NN" and plain["name"] == "P3"
     assert corr["diverged_at"] is None
     assert corr["einf_mean"] < 0.3 * plain["einf_mean"], (corr["einf_mean"], plain["einf_mean"])
+
+
+def test_transfer_learning_starts_from_the_saved_network(experiment, saved_net):
+    """Retraining at the next time window from the saved network (the paper's transfer
+    learning) starts far below a fresh network and stays below it for a few epochs."""
+    from paper_2207_11571_gb300 import experiment as ex
+    window = ["--t_train", "1.0", "--t_train_end", "1.5", "--t_end", "1.05", "--epochs", "3"]
+    warm = ex.run(ex.parse(COMMON + window + ["--init_net", saved_net]))
+    fresh = ex.run(ex.parse(COMMON + window))
+    assert warm["train_loss"][0] < 0.5 * fresh["train_loss"][0], (warm["train_loss"], fresh["train_loss"])
+    assert warm["train_loss"][-1] < fresh["train_loss"][-1], (warm["train_loss"], fresh["train_loss"])
