@@ -129,6 +129,23 @@ __device__ __forceinline__ void line_derivative(const float* __restrict__ f, flo
   }
 }
 
+// line_derivative in place: the line's values are all read before any is written, and
+// no other task touches the line, so the derivative may overwrite its operand.
+template <int P, int D>
+__device__ __forceinline__ void line_derivative_inplace(float* f, int ab) {
+  constexpr int n = P + 1;
+  float v[n];
+#pragma unroll
+  for (int m = 0; m < n; ++m) v[m] = f[face_node<P>(D, m, ab)];
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    float acc = 0.f;
+#pragma unroll
+    for (int m = 0; m < n; ++m) acc += c_D32[P][i * n + m] * v[m];
+    f[face_node<P>(D, i, ab)] = acc;
+  }
+}
+
 // Halo / interface item t <-> (ab, side, d, hl), ab fastest, element slowest.
 template <int P>
 struct Item {
@@ -440,6 +457,12 @@ __host__ __device__ constexpr int min_blocks_for(int P, int tsize) {
   return tsize == 8 ? 1 : P == 6 ? 4 : P == 7 ? 3 : 2;
 }
 
+// Phase B forms the volume fluxes before the interface phase, in a tile of their own
+// (FP32 at P = 4, 5, one node per thread): one barrier less for a larger shared
+// footprint.  Measured per RK3 step, 24^3/P4 408 vs 415 us, 20^3/P5 431 vs 439 us, but
+// 32^3/P3 465 vs 458 us, so P <= 3 and FP64 keep the smaller footprint.
+__host__ __device__ constexpr bool flux_early(int P, int tsize) { return tsize == 4 && (P == 4 || P == 5); }
+
 // MODE 0: dqdt = R.  MODE 1: FP64 RK stage (g = A g + dt R; q += B g).
 // MODES 2, 3, 4: FP32 increment scheme, stages 1, 2, 3.
 // Phase B of block `blk` of one mesh (the body of k_flux and k_flux_batch).
@@ -461,9 +484,15 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   const int E = C.E;
   const int tileN = E * np;
   const int haloN = E * 6 * n2;
+  // flux_early: the volume fluxes are formed right after the own loads, into their own
+  // tile, so that the interface phase and the contraction need one barrier less.
+  // Otherwise they overwrite the own tile after the interface phase (register and
+  // shared-memory budget).
+  constexpr bool kEarlyF = flux_early(P, sizeof(T));
   T* sD = reinterpret_cast<T*>(smem_raw);
-  T* sX = sD + n2;                        // [15][E np]: own data, then the volume fluxes
-  T* sH = sX + kTileComponents * tileN;   // [9][E 6 n2]: neighbours' face data
+  T* sX = sD + n2;                        // own data [14][E np] (late fluxes: [15], then the fluxes)
+  T* sF = kEarlyF ? sX + 14 * tileN : sX; // [15][E np]: volume fluxes
+  T* sH = kEarlyF ? sF + kTileComponents * tileN : sX + kTileComponents * tileN;  // [9][E 6 n2]
   T* sS = sH + FC * haloN;                // [5][E 6 n2]: lifted interface terms
   const int e0 = blk * E;
   const BlockCoords bc = block_coords(e0, C.K);
@@ -509,6 +538,17 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
     for (int v = 0; v < 5; ++v) sX[v * tileN + tix[j]] = s[j][v];
 #pragma unroll
     for (int c = 0; c < 9; ++c) sX[(5 + c) * tileN + tix[j]] = vs[j][c];
+    if (kEarlyF) {
+      const Prim<T> w = prim_c(s[j], C);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T F[5], fv[5];
+        euler_flux(s[j], w, C.Hc, d, F);
+        viscous_flux(vs[j], w.v, d, fv);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) sF[(5 * d + c) * tileN + tix[j]] = F[c] - fv[c];
+      }
+    }
   }
   // halo: neighbours' stage state and face-normal viscous quantities on every face
   for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
@@ -553,11 +593,11 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
         interface_item<2>(so, to, sn, tn, sS + t, haloN, it.side, C);
     }
   }
-  __syncthreads();  // own-data tile no longer needed: it now holds the volume fluxes
+  __syncthreads();  // own-data tile no longer needed: (late fluxes) it now takes the volume fluxes
 
 #pragma unroll
   for (int j = 0; j < NPT; ++j) {
-    if (!active[j]) continue;
+    if (kEarlyF || !active[j]) continue;
     if (!kHold) {
       load_rk(j);
 #pragma unroll
@@ -575,7 +615,7 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
       for (int c = 0; c < 5; ++c) sX[(5 * d + c) * tileN + tix[j]] = F[c] - fv[c];
     }
   }
-  __syncthreads();
+  if (!kEarlyF) __syncthreads();
 
 #pragma unroll
   for (int j = 0; j < NPT; ++j) {
@@ -594,7 +634,7 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
       for (int c = 0; c < 5; ++c) {
         T acc = T(0);
 #pragma unroll
-        for (int m = 0; m < n; ++m) acc += Drow[m] * sX[(5 * d + c) * tileN + base + m * stride[d]];
+        for (int m = 0; m < n; ++m) acc += Drow[m] * sF[(5 * d + c) * tileN + base + m * stride[d]];
         R[c] -= C.s2h * acc;
       }
     }
@@ -751,11 +791,12 @@ struct StreamItem {
 };
 
 // Shared memory of the streamed kernel, in floats: D, lifted terms, the per-direction
-// volume terms [3][5][np], and two buffers of (own tile [15][np], halo [9][6 n2]).
+// volume fluxes and then their derivatives [3][5][np], and two buffers of (own tile
+// [14][np], halo [9][6 n2]).
 template <int P>
 __host__ __device__ constexpr int stream_smem_floats() {
   return (P + 1) * (P + 1) + 5 * 6 * (P + 1) * (P + 1) + 15 * (P + 1) * (P + 1) * (P + 1) +
-         2 * (15 * (P + 1) * (P + 1) * (P + 1) + kFaceComponents * 6 * (P + 1) * (P + 1));
+         2 * (14 * (P + 1) * (P + 1) * (P + 1) + kFaceComponents * 6 * (P + 1) * (P + 1));
 }
 
 
@@ -765,12 +806,12 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
   using T = float;
   constexpr int n = P + 1, n2 = n * n, np = n2 * n, haloN = 6 * n2;
   constexpr int FC = kFaceComponents;
-  constexpr int kBuf = 15 * np + FC * haloN;
+  constexpr int kBuf = 14 * np + FC * haloN;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sD = reinterpret_cast<T*>(smem_raw);
   T* sS = sD + n2;                 // [5][haloN]: lifted interface terms
-  T* sV = sS + 5 * haloN;          // [3][5][np]: volume-term derivatives per direction
-  T* buf0 = sV + 15 * np;          // two buffers: [15][np] own tile, then [9][haloN] halo
+  T* sV = sS + 5 * haloN;          // [3][5][np]: volume fluxes, then their derivatives
+  T* buf0 = sV + 15 * np;          // two buffers: [14][np] own tile, then [9][haloN] halo
 
   auto prefetch = [&](int item, T* b) {
     const StreamItem m = src.at(item);
@@ -783,7 +824,7 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
       for (int c = 0; c < 9; ++c) cp_async4(b + (5 + c) * np + nd, m.vis + c * N + e0 + nd);
     }
     const BlockCoords bc = block_coords(m.e, m.C->K);
-    T* h = b + 15 * np;
+    T* h = b + 14 * np;
     for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
       const Item<P> it = item_of<P>(t);
       const int enb = neighbour_of(bc, 0, m.C->K, it.d, it.side ? 1 : -1);
@@ -821,7 +862,7 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
     const long long N = C.N;
     const long long gi = (long long)m.e * np + node;
     T* sX = b;
-    T* sH = b + 15 * np;
+    T* sH = b + 14 * np;
 
     // RK operands of this thread's node, loaded now and used at the end
     T gold[5], dold[5];
@@ -836,6 +877,25 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
         for (int v = 0; v < 5; ++v) gold[v] = m.greg[v * N + gi];
 #pragma unroll
         for (int v = 0; v < 5; ++v) qold[v] = m.q[v * N + gi];
+      }
+    }
+
+    // volume fluxes of this thread's node into sV (the own tile stays intact for the
+    // interface items, so no barrier separates the two)
+    if (active) {
+      T s[5], vs[9];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) s[v] = sX[v * np + node];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) vs[c] = sX[(5 + c) * np + node];
+      const Prim<T> w = prim_c(s, C);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        T F[5], fv[5];
+        euler_flux(s, w, C.Hc, d, F);
+        viscous_flux(vs, w.v, d, fv);
+#pragma unroll
+        for (int c = 0; c < 5; ++c) sV[(5 * d + c) * np + node] = F[c] - fv[c];
       }
     }
 
@@ -867,35 +927,16 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
           interface_item<2>(so, to, sn, tn, sS + t, haloN, it.side, C);
       }
     }
-    __syncthreads();  // own tile no longer needed: it now takes the volume fluxes
-
-    if (active) {
-      T s[5], vs[9];
-#pragma unroll
-      for (int v = 0; v < 5; ++v) s[v] = sX[v * np + node];
-#pragma unroll
-      for (int c = 0; c < 9; ++c) vs[c] = sX[(5 + c) * np + node];
-      const Prim<T> w = prim_c(s, C);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        T F[5], fv[5];
-        euler_flux(s, w, C.Hc, d, F);
-        viscous_flux(vs, w.v, d, fv);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) sX[(5 * d + c) * np + node] = F[c] - fv[c];
-      }
-    }
     __syncthreads();
 
-    // volume term: one task per (direction, component, line) computes the derivative at
-    // every node of the line; tasks are direction-major so that a warp shares d
+    // volume term: one task per (direction, component, line) replaces the line's fluxes
+    // by their derivative; tasks are direction-major so that a warp shares d
     for (int task = threadIdx.x; task < 15 * n2; task += blockDim.x) {
       const int dc = task / n2, ab = task - dc * n2;
-      const float* f = sX + dc * np;
-      float* o = sV + dc * np;
-      if (dc < 5) line_derivative<P, 0>(f, o, ab);
-      else if (dc < 10) line_derivative<P, 1>(f, o, ab);
-      else line_derivative<P, 2>(f, o, ab);
+      float* f = sV + dc * np;
+      if (dc < 5) line_derivative_inplace<P, 0>(f, ab);
+      else if (dc < 10) line_derivative_inplace<P, 1>(f, ab);
+      else line_derivative_inplace<P, 2>(f, ab);
     }
     __syncthreads();
     if (!active) continue;

@@ -85,7 +85,9 @@ size_t gradient_smem(int E) {
 template <int P, typename T>
 size_t flux_smem(int E) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
-  return sizeof(T) * (n2 + kTileComponents * E * np + (kFaceComponents + 5) * E * 6 * n2);
+  // early volume fluxes: own tile [14] and flux tile [15] apart
+  const int tile = flux_early(P, sizeof(T)) ? 14 + kTileComponents : kTileComponents;
+  return sizeof(T) * (n2 + tile * E * np + (kFaceComponents + 5) * E * 6 * n2);
 }
 
 template <int P, typename T, int SRC>

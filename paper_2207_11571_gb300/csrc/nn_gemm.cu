@@ -137,6 +137,11 @@ k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // Programmatic dependent launch: the next GEMM of the chain may start its prologue now
+  // (it launches once every CTA of this grid is resident); this grid's own operands are
+  // read only after the previous grid has completed and its writes are visible.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (warp == 0) {
     if (lane == 0) {
@@ -298,7 +303,17 @@ int launch_gemm(const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb
     configured = true;
   }
   dim3 grid((M + kBM - 1) / kBM, (N + BN - 1) / BN, ep.splits);
-  kern<<<grid, kThreads, smem, st>>>(ma, mb, M, N, K, ep, err);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  DG_CUDA(cudaLaunchKernelEx(&cfg, kern, ma, mb, M, N, K, ep, err));
   DG_CUDA(cudaGetLastError());
   return DG_OK;
 }

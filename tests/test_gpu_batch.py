@@ -13,9 +13,10 @@ from paper_2207_11571_gb300 import inputs
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# (K, P, Re, Mach, Pr, closure): orders 3 and 6 with several meshes, Re in {30, 200, 1600}
+# (K, P, Re, Mach, Pr, closure): orders 3, 4 and 6 with several meshes, Re in {30, 200, 1600}
 MEMBERS = [(3, 3, 30.0, 0.1, 0.71, 0), (2, 6, 200.0, 0.1, 0.71, 0), (4, 3, 1600.0, 0.1, 0.71, 1),
-           (2, 3, 200.0, 0.1, 0.71, 0), (3, 6, 1600.0, 0.1, 0.71, 0), (5, 3, 1600.0, 0.1, 0.71, 0)]
+           (2, 3, 200.0, 0.1, 0.71, 0), (3, 6, 1600.0, 0.1, 0.71, 0), (5, 3, 1600.0, 0.1, 0.71, 0),
+           (3, 4, 200.0, 0.1, 0.71, 1)]
 
 
 @pytest.fixture(scope="module")

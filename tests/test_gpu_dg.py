@@ -123,7 +123,8 @@ def test_rhs_fp64_matches_oracle_on_rough_state(dg, K, P, les, E):
     assert_fp64_parity(c.rhs(to_dev(q_or)), q_or, c.mesh, c.flow)
 
 
-@pytest.mark.parametrize("K,P,les", [(4, 3, False), (3, 3, True), (2, 6, True), (2, 8, False), (8, 3, False)])
+@pytest.mark.parametrize("K,P,les", [(4, 3, False), (3, 3, True), (2, 6, True), (2, 8, False), (8, 3, False),
+                                     (3, 4, False), (2, 5, True)])
 def test_rhs_fp32_error_against_fp64_oracle(dg, K, P, les):
     c = Ctx(dg, K, P, les=les, precision=1)
     _, q_or = c.tgv()
