@@ -367,6 +367,7 @@ def run_ours(args, rank, ws):
     for (K, P), n, p in zip(WORKLOAD, nodes, prof):
         per_workload[f"{K}^3/P{P}"] = {"nodes": n, "dof_stage_per_s_kernels":
                                        3 * 3 * n / ((p["ms_gradient"] + p["ms_flux"]) / 1e3)}
+    shapes = ["cube 2x2x2" if dg.dg_blocking(c)[1] else "row" for c in ctxs]
     for c in ctxs:
         dg.dg_destroy(c)
 
@@ -378,6 +379,7 @@ def run_ours(args, rank, ws):
                 "config": {"workload": WORKLOAD_NAME, "meshes": [f"{K}^3/P{P}" for K, P in WORKLOAD],
                            "nodes": nodes, "l2": "working set per mesh 190-400 MB > 129 MB L2 (no flush)",
                            "elems_per_block": tuned,
+                           "block_shape": shapes,
                            "parallelism": f"replicas x{ws}", "per_workload": per_workload},
                 "roofline": roofline, "kernels": per_kernel, "network": nn_line, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 6 * len(WORKLOAD) * args.steps, "clocks": clk}

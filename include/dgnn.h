@@ -64,6 +64,10 @@ typedef struct {
   double Prt;         /* turbulent Prandtl number, default 0.9 */
   double les_delta;   /* LES filter width; <= 0 selects h/(P+1) (default) */
   int elems_per_block;/* elements per CUDA block; <= 0 selects the tuned default for P */
+  int block_shape;    /* 0: blocks of elems_per_block consecutive elements (default);
+                         1: 2 x 2 x 2 cubes of elements (P <= 3 and even K only, else
+                         DG_ERR_INVALID_ARG): a cube's twelve internal faces need no halo
+                         and their interface fluxes are formed once for both sides */
 } dg_opts;
 
 /* Integral diagnostics (Sec. 2.4 Eq. 9 and kinetic-energy budget), FP64. */
@@ -226,9 +230,15 @@ int dg_profile_rk3(dg_ctx* ctx, double* q, double dt, int nsteps, double* ms_gra
 
 /* Autotuner: times one RK3 step (on a scratch copy of the DEVICE state q; q is not
  * modified) for every elements-per-block value E = 1, 2, 4, ... that fits the block size
- * and shared memory of this P, and keeps the fastest for the context.  best_E (HOST,
- * may be NULL) receives it, best_ms (HOST, may be NULL) its time per step.  Synchronises. */
+ * and shared memory of this P, and for 2 x 2 x 2 cube blocks where allowed (P <= 3, even
+ * K, not a batch member), and keeps the fastest for the context.  best_E (HOST, may be
+ * NULL) receives its elements per block (8 for cubes; dg_blocking tells the shape),
+ * best_ms (HOST, may be NULL) its time per step.  Synchronises. */
 int dg_autotune(dg_ctx* ctx, const double* q, double dt, int* best_E, double* best_ms, void* stream);
+
+/* The blocking the context's kernels use: elements per block and block shape (0: rows
+ * of consecutive elements, 1: 2 x 2 x 2 cubes).  HOST pointers, either may be NULL. */
+int dg_blocking(const dg_ctx* ctx, int* elems_per_block, int* block_shape);
 
 /* Self-check of the integer-pipe FP64 <-> FP32 conversions the FP32 operator uses:
  * counts the n DEVICE inputs x where the round-to-nearest-even FP64 -> FP32 conversion

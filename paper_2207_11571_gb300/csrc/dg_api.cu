@@ -175,6 +175,9 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
   if (!(o.gamma > 1.0)) return fail(DG_ERR_INVALID_ARG, "dg_create: gamma must be > 1");
   if (o.elems_per_block > max_elems_per_block(P))
     return fail(DG_ERR_INVALID_ARG, "dg_create: elems_per_block exceeds the block size limit for this P");
+  if (o.block_shape != 0 && o.block_shape != 1) return fail(DG_ERR_INVALID_ARG, "dg_create: block_shape must be 0 or 1");
+  if (o.block_shape == 1 && (!cube_ok(P) || K % 2 != 0))
+    return fail(DG_ERR_INVALID_ARG, "dg_create: cube blocks need P <= 3 and an even K");
 
   dg_ctx* c = new dg_ctx();
   c->K = K;
@@ -198,6 +201,8 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
   c->geom.nel = c->nel;
   c->geom.N = c->N;
   c->geom.E = o.elems_per_block > 0 ? o.elems_per_block : default_elems_per_block(P);
+  c->geom.cube = o.block_shape;
+  if (c->geom.cube) c->geom.E = kCubeElems;
   c->geom.two_over_h = 2.0 / h;
   c->geom.winv = 1.0 / c->basis.w[0];
   std::memset(c->geom.D, 0, sizeof(c->geom.D));
@@ -432,11 +437,17 @@ extern "C" int dg_autotune(dg_ctx* c, const double* q, double dt, int* best_E, d
   cudaEvent_t a = nullptr, b = nullptr;
   cudaError_t e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
-  const int E0 = c->geom.E;
-  int bestE = E0;
+  const int E0 = c->geom.E, cube0 = c->geom.cube;
+  int bestE = E0, bestCube = cube0;
   double best = 1e300;
-  for (int E = 1; e == cudaSuccess && E <= max_elems_per_block(c->P); E *= 2) {
-    c->geom.E = E;
+  // candidates: rows of E = 1, 2, 4, ... elements, then (where allowed) cubes
+  std::vector<std::pair<int, int>> cand;  // (E, cube)
+  for (int E = 1; E <= max_elems_per_block(c->P); E *= 2) cand.push_back({E, 0});
+  if (cube_ok(c->P) && c->K % 2 == 0 && !c->borrowed) cand.push_back({kCubeElems, 1});
+  for (const auto& ce : cand) {
+    if (e != cudaSuccess) break;
+    c->geom.E = ce.first;
+    c->geom.cube = ce.second;
     e = cudaMemcpyAsync(work, q, bytes, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) break;
     if (rk3_steps(c, work, dt, 1, nullptr, st) != DG_OK) {  // shared memory too large for this E: skip
@@ -455,15 +466,25 @@ extern "C" int dg_autotune(dg_ctx* c, const double* q, double dt, int* best_E, d
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
     if (e == cudaSuccess && ms / reps < best) {
       best = ms / reps;
-      bestE = E;
+      bestE = c->geom.E;
+      bestCube = c->geom.cube;
     }
   }
   c->geom.E = (best < 1e300) ? bestE : E0;
+  c->geom.cube = (best < 1e300) ? bestCube : cube0;
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
   cudaFree(work);
   if (e != cudaSuccess) return cuda_fail(e, "dg_autotune");
   if (best_E) *best_E = c->geom.E;
   if (best_ms) *best_ms = best;
+  return DG_OK;
+}
+
+extern "C" int dg_blocking(const dg_ctx* c, int* elems_per_block, int* block_shape) {
+  using namespace dgnn;
+  if (!c) return fail(DG_ERR_INVALID_ARG, "dg_blocking: NULL context");
+  if (elems_per_block) *elems_per_block = c->geom.E;
+  if (block_shape) *block_shape = c->geom.cube;
   return DG_OK;
 }

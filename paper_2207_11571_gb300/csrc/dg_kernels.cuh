@@ -16,7 +16,9 @@
 // stage 2 stores it.  In the FP64 operator every stage updates q in FP64 (the plain
 // 2N scheme).
 //
-// Each CUDA block owns E consecutive elements, one thread per node for the nodal work.
+// Each CUDA block owns E consecutive elements (or, at P <= 3 on even K, a 2 x 2 x 2 cube
+// of elements whose twelve internal faces need no halo and whose internal interface
+// fluxes are computed once for both sides), one thread per node for the nodal work.
 // At kernel start the block issues all its global loads: its own nodes into registers
 // and a halo (the neighbours' face nodes of all six faces of its elements) into shared
 // memory.  Interface fluxes are dense work items, one per (element, face, face node),
@@ -89,6 +91,36 @@ __device__ __forceinline__ int neighbour_of(const BlockCoords& b, int hl, int K,
   return x + K * (y + K * z);
 }
 
+
+// 2 x 2 x 2 element blocks ("cubes", even K): block b covers the elements 2 c + l,
+// l in {0, 1}^3, of the (K/2)^3 grid of cubes; local element hl = lx + 2 ly + 4 lz.
+// Each local element has one external face per direction (on side (hl >> d) & 1) and
+// shares the other with local element hl ^ (1 << d).
+constexpr int kCubeElems = 8;
+__host__ __device__ constexpr bool cube_ok(int P) { return P <= 3; }
+
+__device__ __forceinline__ BlockCoords cube_coords(int b, int K) {
+  const int h = K >> 1;
+  BlockCoords c;
+  c.x = 2 * (b % h);
+  const int r = b / h;
+  c.y = 2 * (r % h);
+  c.z = 2 * (r / h);
+  return c;
+}
+
+__device__ __forceinline__ int cube_element(const BlockCoords& c, int hl, int K) {
+  return (c.x + (hl & 1)) + K * ((c.y + ((hl >> 1) & 1)) + K * (c.z + (hl >> 2)));
+}
+
+// Element index of local element hl shifted by +/-1 along d (periodic).
+__device__ __forceinline__ int cube_neighbour(const BlockCoords& c, int hl, int K, int d, int shift) {
+  int x = c.x + (hl & 1), y = c.y + ((hl >> 1) & 1), z = c.z + (hl >> 2);
+  if (d == 0) x = wrap_step(x, shift, K);
+  else if (d == 1) y = wrap_step(y, shift, K);
+  else z = wrap_step(z, shift, K);
+  return x + K * (y + K * z);
+}
 
 // Node of the face normal to d at normal index m with tangential index ab.
 template <int P>
@@ -171,6 +203,32 @@ __device__ __forceinline__ int item_index(int ab, int side, int d, int hl) {
   return ab + n2 * (side + 2 * (d + 3 * hl));
 }
 
+// External face items of a cube, t <-> (ab, hl, d), ab fastest, direction slowest (a warp
+// shares d); the face lies on side (hl >> d) & 1 of local element hl.
+template <int P>
+__device__ __forceinline__ Item<P> cube_item_of(int t) {
+  constexpr int n2 = (P + 1) * (P + 1);
+  Item<P> it;
+  it.ab = t % n2;
+  const int r = t / n2;
+  it.hl = r % kCubeElems;
+  it.d = r / kCubeElems;
+  it.side = (it.hl >> it.d) & 1;
+  return it;
+}
+
+template <int P>
+__device__ __forceinline__ int cube_item_index(int ab, int d, int hl) {
+  constexpr int n2 = (P + 1) * (P + 1);
+  return ab + n2 * (hl + kCubeElems * d);
+}
+
+// Internal faces of a cube, u <-> (ab, p, d): face p (0..3) normal to d joins the local
+// elements hlL (bit d clear) and hlL | 1 << d.
+__device__ __forceinline__ int cube_left_of_pair(int p, int d) {
+  return ((p >> d) << (d + 1)) | (p & ((1 << d) - 1));
+}
+
 template <typename T>
 __device__ __forceinline__ Prim<T> prim_c(const T s[5], const OpConst<T>& C) {
   return primitives(s, C.rho_ref, C.gm1);
@@ -218,27 +276,29 @@ __device__ __forceinline__ void transport_c(const OpConst<T>& C, T rho, const T 
 }
 
 // Phase A of block `blk` of one mesh (the body of k_gradient and k_gradient_batch).
-template <int P, typename T, int SRC>
+// CUBE: the block is a 2 x 2 x 2 cube of elements; the halo holds only the external
+// faces, internal faces take the neighbour's values from the own tile.
+template <int P, typename T, int SRC, bool CUBE = false>
 __device__ __forceinline__ void gradient_block(int blk, const double* __restrict__ q,
                                                const float* __restrict__ qn32_in, const float* __restrict__ dlt,
                                                T* __restrict__ qf, float* __restrict__ qn32_out,
                                                T* __restrict__ vis, const OpConst<T>& C) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int E = C.E;
+  const int E = CUBE ? kCubeElems : C.E;
   const int tileN = E * np;
-  const int haloN = E * 6 * n2;
+  const int haloN = CUBE ? 3 * kCubeElems * n2 : E * 6 * n2;
   T* sD = reinterpret_cast<T*>(smem_raw);
   T* sU = sD + n2;            // [4][E np]
-  T* sH = sU + 4 * tileN;     // [4][E 6 n2]: neighbours' gradient variables on each face
+  T* sH = sU + 4 * tileN;     // [4][haloN]: neighbours' gradient variables on the (external) faces
   const int e0 = blk * E;
-  const BlockCoords bc = block_coords(e0, C.K);
+  const BlockCoords bc = CUBE ? cube_coords(blk, C.K) : block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
 
   const int le = threadIdx.x / np;
   const int node = threadIdx.x - le * np;
-  const int e = e0 + le;
-  const bool active = (le < E) && (e < C.nel);
+  const int e = CUBE ? cube_element(bc, le, C.K) : e0 + le;
+  const bool active = CUBE ? (le < kCubeElems) : (le < E) && (e < C.nel);
   const long long N = C.N;
   const long long gi = (long long)e * np + node;
 
@@ -259,9 +319,10 @@ __device__ __forceinline__ void gradient_block(int blk, const double* __restrict
   }
   // halo: gradient variables of the neighbours' face nodes
   for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
-    const Item<P> it = item_of<P>(t);
-    if (e0 + it.hl >= C.nel) continue;
-    const int enb = neighbour_of(bc, it.hl, C.K, it.d, it.side ? 1 : -1);
+    const Item<P> it = CUBE ? cube_item_of<P>(t) : item_of<P>(t);
+    if (!CUBE && e0 + it.hl >= C.nel) continue;
+    const int enb = CUBE ? cube_neighbour(bc, it.hl, C.K, it.d, it.side ? 1 : -1)
+                         : neighbour_of(bc, it.hl, C.K, it.d, it.side ? 1 : -1);
     const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
     T sn[5], Un[4];
     stage_state<T, SRC>(q, qn32_in, dlt, N, gnb, C, sn);
@@ -314,10 +375,19 @@ __device__ __forceinline__ void gradient_block(int blk, const double* __restrict
     // interface lifting with the central U^ = (U + U_nb) / 2
     const bool right = (idx[d] == P), left = (idx[d] == 0);
     if (right || left) {
-      const int h = item_index<P>(face_ab<P>(d, idx), right ? 1 : 0, d, le);
+      const int ab = face_ab<P>(d, idx);
       const T sgn = right ? lift : -lift;
+      const T* nb;  // the neighbour's four values, stride st
+      int st;
+      if (CUBE && (right ? 1 : 0) != ((le >> d) & 1)) {
+        nb = sU + (le ^ (1 << d)) * np + face_node<P>(d, right ? 0 : P, ab);   // internal face
+        st = tileN;
+      } else {
+        nb = sH + (CUBE ? cube_item_index<P>(ab, d, le) : item_index<P>(ab, right ? 1 : 0, d, le));
+        st = haloN;
+      }
 #pragma unroll
-      for (int a = 0; a < 4; ++a) G[d][a] += sgn * (sH[a * haloN + h] - U[a]);
+      for (int a = 0; a < 4; ++a) G[d][a] += sgn * (nb[a * st] - U[a]);
     }
   }
 
@@ -340,11 +410,11 @@ __device__ __forceinline__ void gradient_block(int blk, const double* __restrict
   for (int c = 0; c < 9; ++c) vis[c * N + gi] = out[c];
 }
 
-template <int P, typename T, int SRC>
+template <int P, typename T, int SRC, bool CUBE = false>
 __global__ void __launch_bounds__(max_threads_for(P))
 k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, const float* __restrict__ dlt,
            T* __restrict__ qf, float* __restrict__ qn32_out, T* __restrict__ vis, const OpConst<T> C) {
-  gradient_block<P, T, SRC>(blockIdx.x, q, qn32_in, dlt, qf, qn32_out, vis, C);
+  gradient_block<P, T, SRC, CUBE>(blockIdx.x, q, qn32_in, dlt, qf, qn32_out, vis, C);
 }
 
 // Per-launch RK data of phase B in the arithmetic of the update.
@@ -423,6 +493,36 @@ __device__ __forceinline__ void interface_item(const T so[5], const T to[4], con
   }
 }
 
+// Both sides of an internal face of a cube at once: the Roe dissipation, fluxes and
+// primitives are formed once; each side's lifted term is the expression interface_item
+// evaluates for it (own = left element on its side 1, own = right element on its side 0).
+template <int D, typename T>
+__device__ __forceinline__ void interface_pair(const T sl[5], const T tl[4], const T sr[5], const T tr[4], T* outL,
+                                               T* outR, int ostride, const OpConst<T>& C) {
+  const Prim<T> wl = primitives(sl, C.rho_ref, C.gm1), wr = primitives(sr, C.rho_ref, C.gm1);
+  T fl[5], fr[5], fvl[5], fvr[5], diss[5];
+  euler_flux(sl, wl, C.Hc, D, fl);
+  euler_flux(sr, wr, C.Hc, D, fr);
+  roe_dissipation(sl, wl, sr, wr, D, C.gm1, C.Hc, diss);
+  viscous_flux4(tl, wl.v, fvl);
+  viscous_flux4(tr, wr.v, fvr);
+  const T lift = C.s2h * C.winv;
+  if (sizeof(T) == 8) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const T fstar = T(0.5) * (fl[c] + fr[c] - diss[c]) - T(0.5) * (fvl[c] + fvr[c]);
+      outL[c * ostride] = -lift * (fstar - (fl[c] - fvl[c]));
+      outR[c * ostride] = lift * (fstar - (fr[c] - fvr[c]));
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      outL[c * ostride] = -lift * (T(0.5) * (fr[c] - fl[c] - diss[c]) + T(0.5) * (fvl[c] - fvr[c]));
+      outR[c * ostride] = lift * (T(0.5) * (fl[c] - fr[c] - diss[c]) + T(0.5) * (fvr[c] - fvl[c]));
+    }
+  }
+}
+
 // Index of viscous component i of the face-normal set of direction d in the 9-vector.
 __device__ __forceinline__ int face_vis_index(int d, int i) { return i < 3 ? sym_index(i, d) : 6 + d; }
 
@@ -471,7 +571,9 @@ __host__ __device__ constexpr bool flux_early(int P, int tsize) { return tsize =
 // per thread the own state and viscous values stay in registers across the interface
 // phase and the RK operands are loaded first; with two, they are read back from the
 // tile and the RK operands are loaded after the interface phase (register budget).
-template <int P, typename T, int MODE>
+// CUBE: the block is a 2 x 2 x 2 cube of elements; the halo holds only the external
+// faces, and each internal face is one work item that writes both sides' lifted terms.
+template <int P, typename T, int MODE, bool CUBE = false>
 __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, const T* __restrict__ qf,
                                            const T* __restrict__ vis, double* __restrict__ dqdt,
                                            T* __restrict__ greg, float* __restrict__ dlt, const Forcing& fc,
@@ -481,9 +583,10 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   constexpr int NPT = flux_npt(P);
   constexpr bool kHold = (NPT == 1);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int E = C.E;
+  const int E = CUBE ? kCubeElems : C.E;
   const int tileN = E * np;
-  const int haloN = E * 6 * n2;
+  const int faceN = E * 6 * n2;                          // lifted terms: every face of every element
+  const int haloN = CUBE ? 3 * kCubeElems * n2 : faceN;  // neighbours' face data: external faces
   // flux_early: the volume fluxes are formed right after the own loads, into their own
   // tile, so that the interface phase and the contraction need one barrier less.
   // Otherwise they overwrite the own tile after the interface phase (register and
@@ -495,7 +598,7 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   T* sH = kEarlyF ? sF + kTileComponents * tileN : sX + kTileComponents * tileN;  // [9][E 6 n2]
   T* sS = sH + FC * haloN;                // [5][E 6 n2]: lifted interface terms
   const int e0 = blk * E;
-  const BlockCoords bc = block_coords(e0, C.K);
+  const BlockCoords bc = CUBE ? cube_coords(blk, C.K) : block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
   const long long N = C.N;
 
@@ -507,8 +610,8 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
     tix[j] = threadIdx.x + j * blockDim.x;
     le[j] = tix[j] / np;
     node[j] = tix[j] - le[j] * np;
-    active[j] = (le[j] < E) && (e0 + le[j] < C.nel);
-    gi[j] = (long long)(e0 + le[j]) * np + node[j];
+    active[j] = CUBE ? (le[j] < kCubeElems) : (le[j] < E) && (e0 + le[j] < C.nel);
+    gi[j] = (long long)(CUBE ? cube_element(bc, le[j], C.K) : e0 + le[j]) * np + node[j];
   }
 
   // RK operands of the update (loaded first with one node per thread, late with two)
@@ -552,9 +655,10 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   }
   // halo: neighbours' stage state and face-normal viscous quantities on every face
   for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
-    const Item<P> it = item_of<P>(t);
-    if (e0 + it.hl >= C.nel) continue;
-    const int enb = neighbour_of(bc, it.hl, C.K, it.d, it.side ? 1 : -1);
+    const Item<P> it = CUBE ? cube_item_of<P>(t) : item_of<P>(t);
+    if (!CUBE && e0 + it.hl >= C.nel) continue;
+    const int enb = CUBE ? cube_neighbour(bc, it.hl, C.K, it.d, it.side ? 1 : -1)
+                         : neighbour_of(bc, it.hl, C.K, it.d, it.side ? 1 : -1);
     const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
     switch (it.d) {
       case 0: load_face_data<0>(qf, vis, N, gnb, sH + t, haloN); break;
@@ -564,33 +668,72 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   }
   __syncthreads();
 
-  // interface terms, one work item per (element, face, face node)
-  for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
-    const Item<P> it = item_of<P>(t);
-    if (e0 + it.hl >= C.nel) continue;
-    const int o = it.hl * np + face_node<P>(it.d, it.side ? P : 0, it.ab);
-    T so[5], to[4], sn[5], tn[4];
+  // interface terms, one work item per (element, face, face node); in a cube, the
+  // external faces first, then one item per internal face node for both sides
+  const int nItems = CUBE ? haloN + 12 * n2 : haloN;
+  for (int t = threadIdx.x; t < nItems; t += blockDim.x) {
+    if (!CUBE || t < haloN) {
+      const Item<P> it = CUBE ? cube_item_of<P>(t) : item_of<P>(t);
+      if (!CUBE && e0 + it.hl >= C.nel) continue;
+      const int o = it.hl * np + face_node<P>(it.d, it.side ? P : 0, it.ab);
+      T* out = sS + (CUBE ? item_index<P>(it.ab, it.side, it.d, it.hl) : t);
+      T so[5], to[4], sn[5], tn[4];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) so[v] = sX[v * tileN + o];
+      for (int v = 0; v < 5; ++v) so[v] = sX[v * tileN + o];
 #pragma unroll
-    for (int v = 0; v < 5; ++v) sn[v] = sH[v * haloN + t];
+      for (int v = 0; v < 5; ++v) sn[v] = sH[v * haloN + t];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) tn[i] = sH[(5 + i) * haloN + t];
-    switch (it.d) {
-      case 0:
+      for (int i = 0; i < 4; ++i) tn[i] = sH[(5 + i) * haloN + t];
+      switch (it.d) {
+        case 0:
 #pragma unroll
-        for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(0, i)) * tileN + o];
-        interface_item<0>(so, to, sn, tn, sS + t, haloN, it.side, C);
-        break;
-      case 1:
+          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(0, i)) * tileN + o];
+          interface_item<0>(so, to, sn, tn, out, faceN, it.side, C);
+          break;
+        case 1:
 #pragma unroll
-        for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(1, i)) * tileN + o];
-        interface_item<1>(so, to, sn, tn, sS + t, haloN, it.side, C);
-        break;
-      default:
+          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(1, i)) * tileN + o];
+          interface_item<1>(so, to, sn, tn, out, faceN, it.side, C);
+          break;
+        default:
 #pragma unroll
-        for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(2, i)) * tileN + o];
-        interface_item<2>(so, to, sn, tn, sS + t, haloN, it.side, C);
+          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(2, i)) * tileN + o];
+          interface_item<2>(so, to, sn, tn, out, faceN, it.side, C);
+      }
+    } else {
+      const int u = t - haloN;
+      const int ab = u % n2, r = u / n2, d = r >> 2;
+      const int hlL = cube_left_of_pair(r & 3, d), hlR = hlL | (1 << d);
+      const int oL = hlL * np + face_node<P>(d, P, ab), oR = hlR * np + face_node<P>(d, 0, ab);
+      T* outL = sS + item_index<P>(ab, 1, d, hlL);
+      T* outR = sS + item_index<P>(ab, 0, d, hlR);
+      T sl[5], tl[4], sr[5], tr[4];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sl[v] = sX[v * tileN + oL];
+#pragma unroll
+      for (int v = 0; v < 5; ++v) sr[v] = sX[v * tileN + oR];
+      switch (d) {
+        case 0:
+#pragma unroll
+          for (int i = 0; i < 4; ++i) tl[i] = sX[(5 + face_vis_index(0, i)) * tileN + oL];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) tr[i] = sX[(5 + face_vis_index(0, i)) * tileN + oR];
+          interface_pair<0>(sl, tl, sr, tr, outL, outR, faceN, C);
+          break;
+        case 1:
+#pragma unroll
+          for (int i = 0; i < 4; ++i) tl[i] = sX[(5 + face_vis_index(1, i)) * tileN + oL];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) tr[i] = sX[(5 + face_vis_index(1, i)) * tileN + oR];
+          interface_pair<1>(sl, tl, sr, tr, outL, outR, faceN, C);
+          break;
+        default:
+#pragma unroll
+          for (int i = 0; i < 4; ++i) tl[i] = sX[(5 + face_vis_index(2, i)) * tileN + oL];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) tr[i] = sX[(5 + face_vis_index(2, i)) * tileN + oR];
+          interface_pair<2>(sl, tl, sr, tr, outL, outR, faceN, C);
+      }
     }
   }
   __syncthreads();  // own-data tile no longer needed: (late fluxes) it now takes the volume fluxes
@@ -644,11 +787,11 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
       if (!(right || left)) continue;
       const int h = item_index<P>(face_ab<P>(d, idx), right ? 1 : 0, d, lj);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) R[c] += sS[c * haloN + h];
+      for (int c = 0; c < 5; ++c) R[c] += sS[c * faceN + h];
     }
 
     if (fc.s != nullptr) {
-      const long long base = (long long)(e0 + lj) * fc.stride + nd;
+      const long long base = (g / np) * fc.stride + nd;
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         const int slot = c - fc.first_var;
@@ -690,11 +833,11 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   }
 }
 
-template <int P, typename T, int MODE>
+template <int P, typename T, int MODE, bool CUBE = false>
 __global__ void __launch_bounds__(flux_max_threads(P), min_blocks_for(P, sizeof(T)))
 k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ vis, double* __restrict__ dqdt,
        T* __restrict__ greg, float* __restrict__ dlt, Forcing fc, const OpConst<T> C, RkArgs<T> rk) {
-  flux_block<P, T, MODE>(blockIdx.x, q, qf, vis, dqdt, greg, dlt, fc, C, rk);
+  flux_block<P, T, MODE, CUBE>(blockIdx.x, q, qf, vis, dqdt, greg, dlt, fc, C, rk);
 }
 
 // ---------------------------------------------------------------------------------------

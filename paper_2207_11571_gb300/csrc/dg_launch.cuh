@@ -82,6 +82,20 @@ size_t gradient_smem(int E) {
   return sizeof(T) * (n2 + 4 * E * np + 4 * E * 6 * n2 + lines);
 }
 
+// Cube blocks: eight elements, halo of the 24 external faces only, lifted terms of all 48.
+template <int P, typename T>
+size_t gradient_smem_cube() {
+  constexpr int n = P + 1, n2 = n * n, np = n2 * n;
+  return sizeof(T) * (n2 + 4 * kCubeElems * np + 4 * 3 * kCubeElems * n2);
+}
+
+template <int P, typename T>
+size_t flux_smem_cube() {
+  constexpr int n = P + 1, n2 = n * n, np = n2 * n;
+  const int tile = flux_early(P, sizeof(T)) ? 14 + kTileComponents : kTileComponents;
+  return sizeof(T) * (n2 + tile * kCubeElems * np + kFaceComponents * 3 * kCubeElems * n2 + 5 * kCubeElems * 6 * n2);
+}
+
 template <int P, typename T>
 size_t flux_smem(int E) {
   constexpr int n = P + 1, n2 = n * n, np = n2 * n;
@@ -92,6 +106,19 @@ size_t flux_smem(int E) {
 
 template <int P, typename T, int SRC>
 cudaError_t gradient_p(const dg_ctx* c, const double* q, cudaStream_t st) {
+  if constexpr (cube_ok(P)) {
+    if (c->geom.cube) {
+      const size_t smem = gradient_smem_cube<P, T>();
+      auto kern = k_gradient<P, T, SRC, true>;
+      cudaError_t e = set_smem(kern, smem);
+      if (e != cudaSuccess) return e;
+      const int h = c->K / 2;
+      kern<<<h * h * h, block_threads(P, kCubeElems), smem, st>>>(
+          q, c->qn32, c->dlt, static_cast<T*>(c->qf), SRC == 0 ? c->qn32 : nullptr, static_cast<T*>(c->vis),
+          make_const<T>(c));
+      return cudaGetLastError();
+    }
+  }
   const int E = c->geom.E;
   const size_t smem = gradient_smem<P, T>(E);
   auto kern = k_gradient<P, T, SRC>;
@@ -151,6 +178,19 @@ cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, c
                    cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value && P >= 6 && MODE != 1) {
     if (c->geom.E == 1) return flux_stream_launch<P, MODE>(c, q, dqdt, f, rk, st);
+  }
+  if constexpr (cube_ok(P)) {
+    if (c->geom.cube) {
+      const size_t smem = flux_smem_cube<P, T>();
+      auto kern = k_flux<P, T, MODE, true>;
+      cudaError_t e = set_smem(kern, smem);
+      if (e != cudaSuccess) return e;
+      const int h = c->K / 2;
+      kern<<<h * h * h, flux_threads(P, kCubeElems), smem, st>>>(
+          q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt, static_cast<T*>(c->g), c->dlt, f,
+          make_const<T>(c), rk);
+      return cudaGetLastError();
+    }
   }
   const int E = c->geom.E;
   const size_t smem = flux_smem<P, T>(E);

@@ -32,7 +32,7 @@ class DGError(RuntimeError):
 class dg_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("Cs", ctypes.c_double), ("Prt", ctypes.c_double),
-                ("les_delta", ctypes.c_double), ("elems_per_block", ctypes.c_int)]
+                ("les_delta", ctypes.c_double), ("elems_per_block", ctypes.c_int), ("block_shape", ctypes.c_int)]
 
 
 class dg_diag(ctypes.Structure):
@@ -75,6 +75,7 @@ _SIGS = {
     "dg_make_pairs": [_P, _P, _P, _P, _D, _I, _I, _P, _P, _P],
     "dg_check_conversions": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P],
     "dg_autotune": [_P, _P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P],
+    "dg_blocking": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "dg_rhs_noalloc": [_I, _I, _D, _D, _D, _I, _I, _P, _P, _P],
     "dg_create_batch": [ctypes.POINTER(dg_instance_desc), _I, ctypes.POINTER(dg_opts), ctypes.POINTER(_P)],
     "dg_batch_destroy": [_P],
@@ -274,6 +275,14 @@ def dg_autotune(ctx, q, dt, stream=None):
     check(lib().dg_autotune(ctypes.c_void_p(ctx), ptr(q), float(dt), ctypes.byref(E), ctypes.byref(ms),
                             stream_ptr(stream)))
     return E.value, ms.value
+
+
+def dg_blocking(ctx):
+    """(elements per block, block shape) the context's kernels use; shape 0 = rows of
+    consecutive elements, 1 = 2 x 2 x 2 cubes."""
+    E, shape = ctypes.c_int(), ctypes.c_int()
+    check(lib().dg_blocking(ctypes.c_void_p(ctx), ctypes.byref(E), ctypes.byref(shape)))
+    return E.value, shape.value
 
 
 def dg_rhs_noalloc(K, P, Re, Mach, Pr, closure, precision, q, dqdt, stream=None):

@@ -49,7 +49,8 @@ def test_opts_defaults(L):
 
 
 @pytest.mark.parametrize("bad", [dict(K=0), dict(K=300), dict(P=0), dict(P=9), dict(Re=-1.0),
-                                 dict(Mach=0.0), dict(closure=2)])
+                                 dict(Mach=0.0), dict(closure=2), dict(block_shape=2),
+                                 dict(block_shape=1, K=5), dict(block_shape=1, P=4)])
 def test_create_rejects_bad_arguments_before_touching_cuda(L, bad):
     from paper_2207_11571_gb300 import dg
     args = dict(K=4, P=3, Re=1600.0, Mach=0.1, Pr=0.71, closure=0)
@@ -75,6 +76,14 @@ def test_create_batch_rejects_bad_members_before_touching_cuda(L, members):
         dg.dg_create_batch(members)
     assert e.value.status == dg.DG_ERR_INVALID_ARG
     assert b"dg_create" in L.dg_last_error()
+
+
+def test_batch_rejects_cube_blocks_before_touching_cuda(L):
+    from paper_2207_11571_gb300 import dg
+    with pytest.raises(dg.DGError) as e:
+        dg.dg_create_batch([(4, 3, 1600.0, 0.1, 0.71, 0)], block_shape=1)
+    assert e.value.status == dg.DG_ERR_INVALID_ARG
+    assert L.dg_blocking(None, None, None) == dg.DG_ERR_INVALID_ARG
 
 
 def test_batch_calls_reject_null_handles(L):

@@ -138,6 +138,58 @@ def test_rhs_fp32_error_against_fp64_oracle(dg, K, P, les):
     assert np.linalg.norm(R[0] - Ro[0]) < FP32_RTOL_MOMENTUM * np.linalg.norm(Ro[1]), per_var
 
 
+# 2 x 2 x 2 cube blocks (P <= 3, even K): K = 2 is one cube whose external faces wrap
+# onto its own elements
+CUBE_CASES = [(4, 3, False), (2, 3, True), (4, 2, True), (2, 1, False), (6, 3, False)]
+
+
+@pytest.mark.parametrize("K,P,les", CUBE_CASES)
+def test_cube_blocks_fp64_match_oracle(dg, K, P, les):
+    c = Ctx(dg, K, P, les=les, block_shape=1)
+    assert dg.dg_blocking(c.h) == (8, 1)
+    _, q_or = c.tgv()
+    assert_fp64_parity(c.rhs(to_dev(q_or)), q_or, c.mesh, c.flow)
+    # random per-node states: every internal and external interface jumps
+    r = Ctx(dg, K, P, Re=50.0, Mach=0.3, les=les, block_shape=1)
+    q_r = inputs.random_conserved((K,) * 3 + (P + 1,) * 3, seed=200 + P, rhoE=(1 / (1.4 * 0.09) / 0.4, 1.0))
+    assert_fp64_parity(r.rhs(to_dev(q_r)), q_r, r.mesh, r.flow)
+
+
+@pytest.mark.parametrize("K,P,les", [(4, 3, False), (4, 2, True)])
+def test_cube_blocks_fp32_match_oracle_and_rows(dg, K, P, les):
+    """FP32 operator with cube blocks: the same per-variable bounds against the FP64 oracle
+    as rows of elements, and within FP32 rounding of the rows' result; RK3 steps agree."""
+    cube = Ctx(dg, K, P, les=les, precision=1, block_shape=1)
+    rows = Ctx(dg, K, P, les=les, precision=1)
+    _, q_or = cube.tgv()
+    Rc, Rr = cube.rhs(to_dev(q_or)), rows.rhs(to_dev(q_or))
+    Ro = dgsem.rhs(q_or, cube.mesh, cube.flow)
+    per_var = [rel_l2(Rc[v], Ro[v]) for v in range(5)]
+    assert max(per_var[1:4]) < FP32_RTOL_MOMENTUM, per_var
+    assert per_var[4] < FP32_RTOL_ENERGY, per_var
+    for v in range(1, 5):
+        assert rel_l2(Rc[v], Rr[v]) < 1e-5, (v, rel_l2(Rc[v], Rr[v]))
+    qc, qr = to_dev(q_or), to_dev(q_or)
+    dg.dg_rk3_step(cube.h, qc, 1e-3, 5)
+    dg.dg_rk3_step(rows.h, qr, 1e-3, 5)
+    d = (qc - qr).abs().max().item()
+    incr = (qr - to_dev(q_or)).abs().max().item()
+    assert d < 1e-5 * incr, (d, incr)
+
+
+def test_autotune_may_pick_cube_blocks_and_keeps_results(dg):
+    c = Ctx(dg, 8, 3, precision=1)
+    q, _ = c.tgv()
+    before = q.clone()
+    dg.dg_rk3_step(c.h, before, 1e-3, 2)
+    E, _ = dg.dg_autotune(c.h, q, 1e-3)
+    assert dg.dg_blocking(c.h)[0] == E
+    after = q.clone()
+    dg.dg_rk3_step(c.h, after, 1e-3, 2)
+    d = (after - before).abs().max().item()
+    assert d < 1e-5 * (before - q).abs().max().item()
+
+
 def record_fp32_error(K, P, les, whole, per_var):
     import json
     import os

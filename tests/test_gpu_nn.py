@@ -211,8 +211,10 @@ def test_forcing_infer_matches_oracle_on_element_features(L, prec):
     dg.dg_destroy(ctx)
 
 
-def test_rhs_and_rk3_with_forcing_match_oracle(L):
-    """dq/dt = p_LO(q) + s(q) (Eq. 4) and RK3 with s in every stage, FP64 operator."""
+@pytest.mark.parametrize("block_shape", [0, 1])
+def test_rhs_and_rk3_with_forcing_match_oracle(L, block_shape):
+    """dq/dt = p_LO(q) + s(q) (Eq. 4) and RK3 with s in every stage, FP64 operator, with
+    rows of elements and with 2 x 2 x 2 cube blocks."""
     from paper_2207_11571_gb300 import dg, nn
     K, P = 2, 3
     flow = physics.Flow(Re=200.0, Mach=0.1)
@@ -220,7 +222,7 @@ def test_rhs_and_rk3_with_forcing_match_oracle(L):
     N = K ** 3 * 64
     pert = inputs.perturbation((5, N))
     q_or = dgsem.tgv_state(mesh, flow, pert)
-    ctx = dg.dg_create(K, P, 200.0, 0.1, 0.71, 0)
+    ctx = dg.dg_create(K, P, 200.0, 0.1, 0.71, 0, block_shape=block_shape)
     q = torch.from_numpy(q_or.reshape(5, -1).copy()).cuda()
     h, params = make_net(nn, 320, 128, 2, seed=8, max_batch=8)
     feats = dgsem.element_features(q_or)
