@@ -189,6 +189,19 @@ int dg_batch_autotune(dg_batch* batch, double* const* q, const double* dt, void*
 int dg_advance_host(dg_ctx* ctx, double* q_host, double dt, int nsteps,
                     const nn_model* forcing, dg_diag* diag, void* stream);
 
+/* dg_advance_host in two calls, so that several contexts on several streams overlap
+ * their copies with each other's kernels.  dg_advance_host_async enqueues on stream the
+ * copy of q_host (HOST, 5 N doubles; pinned for the copies to run asynchronously) to
+ * the context's device state, nsteps RK3 steps (as dg_rk3_step), the copy back into
+ * q_host and, if want_diag != 0, the diagnostics of the final state into the context's
+ * pinned buffer; it returns without waiting.  q_host must not be touched until
+ * dg_advance_host_wait(ctx, diag, stream) returns: it synchronises stream and fills
+ * *diag (HOST, may be NULL; non-NULL requires want_diag in the preceding async call,
+ * else DG_ERR_INVALID_ARG).  One pending advance per context. */
+int dg_advance_host_async(dg_ctx* ctx, double* q_host, double dt, int nsteps,
+                          const nn_model* forcing, int want_diag, void* stream);
+int dg_advance_host_wait(dg_ctx* ctx, dg_diag* diag, void* stream);
+
 /* q_lo = G q_hi: the filter of Eq. 2, per element nodal(P_hi) -> Legendre modes ->
  * truncation to degree P_lo per direction -> nodal(P_lo) (Sec. 2.6), FP64.  Both
  * contexts must share K and P_lo <= P_hi.  q_hi, q_lo: device. */

@@ -116,8 +116,10 @@ static int rk3_steps(dg_ctx* c, double* q, double dt, int nsteps, const nn_model
   return DG_OK;
 }
 
-static int diagnostics_into(dg_ctx* c, const double* q, const double* qref, const nn_model* net, bool with_rhs,
-                            dg_diag* out, cudaStream_t st) {
+// Diagnostics in two parts: the reductions and the copy of their result into the
+// context's pinned buffer are enqueued on st; diag_collect waits for st and fills out.
+static int diag_enqueue(dg_ctx* c, const double* q, const double* qref, const nn_model* net, bool with_rhs,
+                        cudaStream_t st) {
   const double* R = nullptr;
   if (with_rhs) {
     int rc = rhs_into(c, q, c->rhs_tmp, net, st);
@@ -127,6 +129,10 @@ static int diagnostics_into(dg_ctx* c, const double* q, const double* qref, cons
   double* dev_out = c->red + (size_t)c->red_blocks * kDiagLen;
   DG_CUDA(launch_diagnostics(c, q, R, qref, c->red, c->red_blocks, dev_out, st));
   DG_CUDA(cudaMemcpyAsync(c->red_host, dev_out, kDiagLen * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return DG_OK;
+}
+
+static int diag_collect(dg_ctx* c, bool with_rhs, bool with_ref, dg_diag* out, cudaStream_t st) {
   DG_CUDA(cudaStreamSynchronize(st));
   const double* r = c->red_host;
   const double vol = 8.0 * M_PI * M_PI * M_PI;
@@ -137,9 +143,16 @@ static int diagnostics_into(dg_ctx* c, const double* q, const double* qref, cons
   out->ke = r[5] / vol;
   out->dke_dt = with_rhs ? r[6] / vol : 0.0;
   out->nonfinite = (int64_t)r[kDiagNonfinite];
-  for (int i = 0; i < 3; ++i) out->e_inf[i] = qref ? r[8 + i] : 0.0;
+  for (int i = 0; i < 3; ++i) out->e_inf[i] = with_ref ? r[8 + i] : 0.0;
   out->max_wave = r[11];
   return out->nonfinite ? fail(DG_ERR_NONFINITE, "state holds non-finite values") : DG_OK;
+}
+
+static int diagnostics_into(dg_ctx* c, const double* q, const double* qref, const nn_model* net, bool with_rhs,
+                            dg_diag* out, cudaStream_t st) {
+  int rc = diag_enqueue(c, q, qref, net, with_rhs, st);
+  if (rc) return rc;
+  return diag_collect(c, with_rhs, qref != nullptr, out, st);
 }
 
 }  // namespace dgnn
@@ -311,10 +324,10 @@ int dg_rk3_step(dg_ctx* c, double* q, double dt, int nsteps, const nn_model* for
   return rk3_steps(c, q, dt, nsteps, forcing, (cudaStream_t)stream);
 }
 
-int dg_advance_host(dg_ctx* c, double* q_host, double dt, int nsteps, const nn_model* forcing, dg_diag* diag,
-                    void* stream) {
-  if (!c || !q_host) return fail(DG_ERR_INVALID_ARG, "dg_advance_host: NULL argument");
-  if (nsteps < 0 || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_advance_host: bad nsteps or dt");
+int dg_advance_host_async(dg_ctx* c, double* q_host, double dt, int nsteps, const nn_model* forcing, int want_diag,
+                          void* stream) {
+  if (!c || !q_host) return fail(DG_ERR_INVALID_ARG, "dg_advance_host_async: NULL argument");
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_advance_host_async: bad nsteps or dt");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = 5 * c->N * sizeof(double);
   if (!c->q_dev) DG_CUDA(cudaMalloc(&c->q_dev, bytes));
@@ -322,9 +335,29 @@ int dg_advance_host(dg_ctx* c, double* q_host, double dt, int nsteps, const nn_m
   int rc = rk3_steps(c, c->q_dev, dt, nsteps, forcing, st);
   if (rc) return rc;
   DG_CUDA(cudaMemcpyAsync(q_host, c->q_dev, bytes, cudaMemcpyDeviceToHost, st));
-  if (diag) return diagnostics_into(c, c->q_dev, nullptr, forcing, false, diag, st);
-  DG_CUDA(cudaStreamSynchronize(st));
+  c->host_diag_pending = want_diag != 0;
+  if (want_diag) return diag_enqueue(c, c->q_dev, nullptr, forcing, false, st);
   return DG_OK;
+}
+
+int dg_advance_host_wait(dg_ctx* c, dg_diag* diag, void* stream) {
+  if (!c) return fail(DG_ERR_INVALID_ARG, "dg_advance_host_wait: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool pending = c->host_diag_pending;
+  c->host_diag_pending = false;
+  if (diag && pending) return diag_collect(c, false, false, diag, st);
+  DG_CUDA(cudaStreamSynchronize(st));
+  if (diag) return fail(DG_ERR_INVALID_ARG, "dg_advance_host_wait: no diagnostics were requested");
+  return DG_OK;
+}
+
+int dg_advance_host(dg_ctx* c, double* q_host, double dt, int nsteps, const nn_model* forcing, dg_diag* diag,
+                    void* stream) {
+  if (!c || !q_host) return fail(DG_ERR_INVALID_ARG, "dg_advance_host: NULL argument");
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_advance_host: bad nsteps or dt");
+  int rc = dg_advance_host_async(c, q_host, dt, nsteps, forcing, diag != nullptr, stream);
+  if (rc) return rc;
+  return dg_advance_host_wait(c, diag, stream);
 }
 
 int dg_project(const dg_ctx* hi, const dg_ctx* lo, const double* q_hi, double* q_lo, void* stream) {

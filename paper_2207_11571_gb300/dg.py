@@ -69,6 +69,8 @@ _SIGS = {
     "dg_rhs": [_P, _P, _P, _P, _P],
     "dg_rk3_step": [_P, _P, _D, _I, _P, _P],
     "dg_advance_host": [_P, _P, _D, _I, _P, ctypes.POINTER(dg_diag), _P],
+    "dg_advance_host_async": [_P, _P, _D, _I, _P, _I, _P],
+    "dg_advance_host_wait": [_P, ctypes.POINTER(dg_diag), _P],
     "dg_project": [_P, _P, _P, _P, _P],
     "dg_diagnostics": [_P, _P, _P, _P, ctypes.POINTER(dg_diag), _P],
     "dg_stable_dt": [_P, _P, _D, ctypes.POINTER(_D), _P],
@@ -154,6 +156,17 @@ def _check_state(ctx, t, name, dtype="float64"):
         raise ValueError(f"{name} must be a CUDA tensor")
 
 
+def _check_host_state(ctx, a, name):
+    n = dg_sizes(ctx)[0]
+    size = a.numel() if hasattr(a, "numel") else a.size
+    if size != 5 * n:
+        raise ValueError(f"{name} must hold 5 * {n} values, got {size}")
+    if str(a.dtype).split(".")[-1] != "float64":
+        raise TypeError(f"{name} must be float64")
+    if hasattr(a, "is_cuda") and a.is_cuda:
+        raise ValueError(f"{name} must be a host array")
+
+
 # ----------------------------------------------------------------------------- entry points
 
 def dg_opts_default():
@@ -219,6 +232,22 @@ def dg_advance_host(ctx, q_host, dt, nsteps=1, forcing=None, stream=None, want_d
     d = dg_diag()
     check(lib().dg_advance_host(ctypes.c_void_p(ctx), ptr(q_host), float(dt), int(nsteps), _net(forcing),
                                 ctypes.byref(d) if want_diag else None, stream_ptr(stream)))
+    return d.as_dict() if want_diag else None
+
+
+def dg_advance_host_async(ctx, q_host, dt, nsteps=1, forcing=None, stream=None, want_diag=True):
+    """Enqueues dg_advance_host on stream without waiting; q_host (pinned CPU tensor or
+    numpy float64) must stay untouched until dg_advance_host_wait returns."""
+    _check_host_state(ctx, q_host, "q_host")
+    check(lib().dg_advance_host_async(ctypes.c_void_p(ctx), ptr(q_host), float(dt), int(nsteps), _net(forcing),
+                                      int(bool(want_diag)), stream_ptr(stream)))
+
+
+def dg_advance_host_wait(ctx, stream=None, want_diag=True):
+    """Waits for the advance enqueued by dg_advance_host_async; returns its diagnostics."""
+    d = dg_diag()
+    check(lib().dg_advance_host_wait(ctypes.c_void_p(ctx), ctypes.byref(d) if want_diag else None,
+                                     stream_ptr(stream)))
     return d.as_dict() if want_diag else None
 
 

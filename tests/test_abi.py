@@ -84,6 +84,8 @@ def test_batch_rejects_cube_blocks_before_touching_cuda(L):
         dg.dg_create_batch([(4, 3, 1600.0, 0.1, 0.71, 0)], block_shape=1)
     assert e.value.status == dg.DG_ERR_INVALID_ARG
     assert L.dg_blocking(None, None, None) == dg.DG_ERR_INVALID_ARG
+    assert L.dg_advance_host_async(None, None, 1e-3, 1, None, 0, None) == dg.DG_ERR_INVALID_ARG
+    assert L.dg_advance_host_wait(None, None, None) == dg.DG_ERR_INVALID_ARG
 
 
 def test_batch_calls_reject_null_handles(L):

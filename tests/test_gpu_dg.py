@@ -300,6 +300,35 @@ def test_advance_host_equals_device_path(dg):
     assert d["mass"] == pytest.approx((2 * math.pi) ** 3, rel=1e-7)
 
 
+def test_advance_host_async_on_two_streams_equals_device_path(dg):
+    """Two contexts advanced from pinned host states on two streams at once (copies of one
+    overlapping the other's kernels) give what dg_rk3_step gives, diagnostics included."""
+    ctxs = [Ctx(dg, 4, 3, precision=1), Ctx(dg, 3, 6, precision=1)]
+    dev, host = [], []
+    for c in ctxs:
+        q, _ = c.tgv()
+        dev.append(q)
+        h = torch.empty(q.numel(), dtype=torch.float64, pin_memory=True)
+        h.copy_(q)
+        host.append(h)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for _ in range(2):
+        for c, h, s in zip(ctxs, host, streams):
+            dg.dg_advance_host_async(c.h, h, 1e-3, 2, None, s)
+        diags = [dg.dg_advance_host_wait(c.h, s) for c, s in zip(ctxs, streams)]
+    for c, q, h, d in zip(ctxs, dev, host, diags):
+        dg.dg_rk3_step(c.h, q, 1e-3, 4)
+        np.testing.assert_array_equal(h.numpy(), q.cpu().numpy())
+        ref = dg.dg_diagnostics(c.h, q)
+        assert d["mass"] == ref["mass"] and d["ke"] == ref["ke"]
+    with pytest.raises(dg.DGError) as e:   # diagnostics asked for but not enqueued
+        dg.dg_advance_host_async(ctxs[0].h, host[0], 1e-3, 1, None, streams[0], want_diag=False)
+        dg.dg_advance_host_wait(ctxs[0].h, streams[0], want_diag=True)
+    assert e.value.status == dg.DG_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        dg.dg_advance_host_async(ctxs[0].h, dev[0], 1e-3, 1)
+
+
 def test_rhs_rejects_aliasing_and_size_mismatch(dg):
     c = Ctx(dg, 2, 3)
     q, _ = c.tgv()
