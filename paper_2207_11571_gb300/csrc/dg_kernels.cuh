@@ -915,7 +915,17 @@ __device__ __forceinline__ void copy_face_data(const float* qf, const float* vis
 }
 
 // Threads of a streamed block: one per node.
-__host__ __device__ constexpr int stream_threads(int P) { return (((P + 1) * (P + 1) * (P + 1) + 31) / 32) * 32; }
+// One warp more where that saves a round of the 15 (P+1)^2 line-derivative tasks (P = 6:
+// 735 tasks take two rounds of 384 threads instead of three of 352).
+__host__ __device__ constexpr int stream_threads(int P) {
+  return ((15 * (P + 1) * (P + 1) + ((((P + 1) * (P + 1) * (P + 1) + 31) / 32) * 32) - 1) /
+              ((((P + 1) * (P + 1) * (P + 1) + 31) / 32) * 32) >
+          (15 * (P + 1) * (P + 1) + ((((P + 1) * (P + 1) * (P + 1) + 31) / 32) * 32 + 32) - 1) /
+              ((((P + 1) * (P + 1) * (P + 1) + 31) / 32) * 32 + 32))
+             ? ((((P + 1) * (P + 1) * (P + 1) + 31) / 32) * 32 + 32)
+             : ((((P + 1) * (P + 1) * (P + 1) + 31) / 32) * 32);
+}
+static_assert(stream_threads(6) == 384 && stream_threads(7) == 512 && stream_threads(8) == 736, "stream block sizes");
 // Blocks per SM the streamed kernel is compiled for (shared memory allows two at P <= 7).
 __host__ __device__ constexpr int stream_min_blocks(int P) { return P <= 7 ? 2 : 1; }
 
