@@ -249,6 +249,17 @@ int dg_profile_rk3(dg_ctx* ctx, double* q, double dt, int nsteps, double* ms_gra
  * best_ms (HOST, may be NULL) its time per step.  Synchronises. */
 int dg_autotune(dg_ctx* ctx, const double* q, double dt, int* best_E, double* best_ms, void* stream);
 
+/* Where dg_rk3_step and dg_advance_host(_async) apply a network forcing (Sec. 2 Eq. 4,
+ * Algorithm 1):
+ *   DG_FORCING_STAGE (default): s(q_k) is added to the operator at every RK stage state
+ *     q_k, i.e. Eq. 4 integrated by the RK3 scheme;
+ *   DG_FORCING_POST: Algorithm 1's third loop read literally: s is evaluated once on q^n,
+ *     the uncorrected RK3 step is taken, and q^{n+1} += dt s(q^n).
+ * The two agree to O(dt^2).  dg_rhs always returns p(q) + s(q).  Returns
+ * DG_ERR_INVALID_ARG on a NULL context or an unknown mode. */
+enum { DG_FORCING_STAGE = 0, DG_FORCING_POST = 1 };
+int dg_set_forcing_mode(dg_ctx* ctx, int mode);
+
 /* The blocking the context's kernels use: elements per block and block shape (0: rows
  * of consecutive elements, 1: 2 x 2 x 2 cubes).  HOST pointers, either may be NULL. */
 int dg_blocking(const dg_ctx* ctx, int* elems_per_block, int* block_shape);

@@ -102,17 +102,30 @@ static int rhs_into(dg_ctx* c, const double* q, double* out, const nn_model* net
   return DG_OK;
 }
 
+// With a network forcing: DG_FORCING_STAGE adds s(q_k) to the operator in every stage
+// (Eq. 4 integrated by RK3); DG_FORCING_POST evaluates s once on q^n (the stage-1 state),
+// takes the uncorrected step and adds dt s(q^n) (Algorithm 1, third loop).
 static int rk3_steps(dg_ctx* c, double* q, double dt, int nsteps, const nn_model* net, cudaStream_t st) {
-  for (int s = 0; s < nsteps; ++s)
+  const bool post = net && c->forcing_mode == DG_FORCING_POST;
+  for (int s = 0; s < nsteps; ++s) {
+    Forcing fpost;
     for (int k = 0; k < 3; ++k) {
       int src, mode;
       stage_plan(c, k, &src, &mode);
       DG_CUDA(launch_gradient(c, q, src, st));
       Forcing f;
-      int rc = forcing_for(c, q, net, &f, st);
-      if (rc) return rc;
+      if (!post || k == 0) {
+        int rc = forcing_for(c, q, net, &f, st);
+        if (rc) return rc;
+      }
+      if (post) {
+        if (k == 0) fpost = f;
+        f = Forcing{};
+      }
       DG_CUDA(launch_flux(c, q, nullptr, f, mode, kRkA[k], kRkB[k], dt, st));
     }
+    if (post) DG_CUDA(launch_add_forcing(c, q, fpost, dt, st));
+  }
   return DG_OK;
 }
 
@@ -511,6 +524,15 @@ extern "C" int dg_autotune(dg_ctx* c, const double* q, double dt, int* best_E, d
   if (e != cudaSuccess) return cuda_fail(e, "dg_autotune");
   if (best_E) *best_E = c->geom.E;
   if (best_ms) *best_ms = best;
+  return DG_OK;
+}
+
+extern "C" int dg_set_forcing_mode(dg_ctx* c, int mode) {
+  using namespace dgnn;
+  if (!c) return fail(DG_ERR_INVALID_ARG, "dg_set_forcing_mode: NULL context");
+  if (mode != DG_FORCING_STAGE && mode != DG_FORCING_POST)
+    return fail(DG_ERR_INVALID_ARG, "dg_set_forcing_mode: unknown mode");
+  c->forcing_mode = mode;
   return DG_OK;
 }
 

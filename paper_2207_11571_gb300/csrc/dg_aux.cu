@@ -207,6 +207,29 @@ cudaError_t launch_make_pairs(const dg_ctx* lo, const double* qb_n, const double
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- post-step forcing
+
+// Algorithm 1, third loop: q^{n+1} = (uncorrected step) + dt s(q^n), s stored per element
+// as [elem][slot][node] with slot = variable - first_var.
+__global__ void k_add_forcing(double* __restrict__ q, const float* __restrict__ s, int first_var, int n_vars,
+                              int stride, int np, long long N, double dt) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= N * n_vars) return;
+  const int slot = (int)(t / N);
+  const long long g = t - (long long)slot * N;
+  const long long e = g / np;
+  const int node = (int)(g - e * np);
+  q[(long long)(first_var + slot) * N + g] += dt * (double)s[e * stride + (long long)slot * np + node];
+}
+
+cudaError_t launch_add_forcing(const dg_ctx* c, double* q, const Forcing& f, double dt, cudaStream_t st) {
+  const long long total = c->N * f.n_vars;
+  const int threads = 256;
+  k_add_forcing<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(q, f.s, f.first_var, f.n_vars,
+                                                                               f.stride, c->np, c->N, dt);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- conversion self-check
 
 // Counts the inputs where the integer-pipe conversions differ from the hardware ones:

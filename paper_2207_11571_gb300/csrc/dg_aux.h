@@ -42,6 +42,8 @@ cudaError_t launch_diagnostics(const dg_ctx* c, const double* q, const double* R
                                double* partial, int nblocks, double* out, cudaStream_t st);
 cudaError_t launch_make_pairs(const dg_ctx* lo, const double* qb_n, const double* qnn_np1, const double* qb_np1,
                               double dt, int first_var, int n_vars, float* X, float* Y, cudaStream_t st);
+// q += dt s on the forced variables (Algorithm 1's correction after the step).
+cudaError_t launch_add_forcing(const dg_ctx* c, double* q, const Forcing& f, double dt, cudaStream_t st);
 
 // Operator kernels per precision (dg_kernels_f32.cu / dg_kernels_f64.cu).
 cudaError_t gradient_f32(const dg_ctx* c, const double* q, int src, cudaStream_t st);

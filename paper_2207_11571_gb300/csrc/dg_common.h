@@ -98,6 +98,7 @@ struct dg_ctx {
   double* red_host = nullptr;  // pinned host copy of the final reduction
   double* q_dev = nullptr;     // device state for dg_advance_host
   bool host_diag_pending = false;  // dg_advance_host_async enqueued diagnostics not yet collected
+  int forcing_mode = DG_FORCING_STAGE;  // where dg_rk3_step applies a network forcing
   float* s_buf = nullptr;      // forcing buffer [nel][5 n^3]
   double* filter_dev[dgnn::kMaxP + 1] = {};  // filter G to each lower order (dg_project)
   bool borrowed = false;       // member of a dg_batch: released by dg_batch_destroy only

@@ -78,6 +78,7 @@ _SIGS = {
     "dg_check_conversions": [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P],
     "dg_autotune": [_P, _P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P],
     "dg_blocking": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    "dg_set_forcing_mode": [_P, _I],
     "dg_rhs_noalloc": [_I, _I, _D, _D, _D, _I, _I, _P, _P, _P],
     "dg_create_batch": [ctypes.POINTER(dg_instance_desc), _I, ctypes.POINTER(dg_opts), ctypes.POINTER(_P)],
     "dg_batch_destroy": [_P],
@@ -304,6 +305,15 @@ def dg_autotune(ctx, q, dt, stream=None):
     check(lib().dg_autotune(ctypes.c_void_p(ctx), ptr(q), float(dt), ctypes.byref(E), ctypes.byref(ms),
                             stream_ptr(stream)))
     return E.value, ms.value
+
+
+DG_FORCING_STAGE, DG_FORCING_POST = 0, 1
+
+
+def dg_set_forcing_mode(ctx, mode):
+    """Where dg_rk3_step applies a network forcing: DG_FORCING_STAGE (s in every RK
+    stage, Eq. 4) or DG_FORCING_POST (Algorithm 1: uncorrected step, then q += dt s(q^n))."""
+    check(lib().dg_set_forcing_mode(ctypes.c_void_p(ctx), int(mode)))
 
 
 def dg_blocking(ctx):

@@ -9,7 +9,8 @@
    shuffled mini-batches.
 3. Evaluation window (from the end of the training window, or replayed from its start):
    the high-order run continues as the reference; from its filtered state, the corrected
-   low-order run (forcing in every RK stage) and plain runs at P = P_LO .. 6 advance in
+   low-order run (forcing in every RK stage, or after each step with --forcing post) and
+   plain runs at P = P_LO .. 6 advance in
    lockstep.  Every sample interval
    records -dKE/dt and KE (dg_diagnostics) and the L-inf momentum error against the
    filtered reference (Eq. 9).  Each run's advance is timed with CUDA events.
@@ -204,6 +205,9 @@ def parse(argv=None):
                     help="start of the corrected and plain runs: after the training window "
                          "(extrapolation) or at its start (as in the paper's Table 1 cases)")
     ap.add_argument("--io", choices=["all", "momentum"], default="all")
+    ap.add_argument("--forcing", choices=["stage", "post"], default="stage",
+                    help="corrected run: s in every RK stage (Eq. 4) or added after the "
+                         "uncorrected step (Algorithm 1, q += dt s(q^n))")
     ap.add_argument("--width", type=int, default=512)
     ap.add_argument("--hidden", type=int, default=4)
     ap.add_argument("--epochs", type=int, default=30)
@@ -280,6 +284,7 @@ def run(args):
     runs = []
     q_c = new_state(ctx_lo)
     dg.dg_project(ctx_hi, ctx_lo, q_hi, q_c)
+    dg.dg_set_forcing_mode(ctx_lo, dg.DG_FORCING_POST if args.forcing == "post" else dg.DG_FORCING_STAGE)
     runs.append(Run(f"P{args.P_lo}+NN", args.P_lo, ctx_lo, q_c, stable_dt(ctx_lo, q_c, args.cfl), net=net,
                     guard=not args.no_guard))
     plain_ctx = {}

@@ -86,6 +86,7 @@ def test_batch_rejects_cube_blocks_before_touching_cuda(L):
     assert L.dg_blocking(None, None, None) == dg.DG_ERR_INVALID_ARG
     assert L.dg_advance_host_async(None, None, 1e-3, 1, None, 0, None) == dg.DG_ERR_INVALID_ARG
     assert L.dg_advance_host_wait(None, None, None) == dg.DG_ERR_INVALID_ARG
+    assert L.dg_set_forcing_mode(None, 0) == dg.DG_ERR_INVALID_ARG
 
 
 def test_batch_calls_reject_null_handles(L):

@@ -246,6 +246,42 @@ def test_rhs_and_rk3_with_forcing_match_oracle(L, block_shape):
     dg.dg_destroy(ctx)
 
 
+def test_rk3_with_post_step_forcing_matches_oracle(L):
+    """Algorithm 1's placement (dg_set_forcing_mode POST), FP64 operator: the uncorrected
+    RK3 step, then q += dt s(q^n), against the oracle's corrected_step(mode='post')."""
+    from paper_2207_11571_gb300 import dg, nn
+    K, P = 2, 3
+    flow = physics.Flow(Re=200.0, Mach=0.1)
+    mesh = dgsem.Mesh(K, P)
+    q_or = dgsem.tgv_state(mesh, flow, inputs.perturbation((5, K ** 3 * 64)))
+    ctx = dg.dg_create(K, P, 200.0, 0.1, 0.71, 0)
+    dg.dg_set_forcing_mode(ctx, dg.DG_FORCING_POST)
+    h, params = make_net(nn, 192, 128, 2, seed=9, max_batch=8, first_var=1, n_vars=3)
+    feats = dgsem.element_features(q_or, (1, 2, 3))
+    sc32 = (feats.mean(0).astype(np.float32), (feats.std(0) + 1e-2).astype(np.float32),
+            np.zeros(192, np.float32), np.full(192, 0.05, np.float32))
+    nn.nn_set_scalers(h, *sc32)
+    sc = tuple(s.astype(np.float64) for s in sc32)
+    q = torch.from_numpy(q_or.reshape(5, -1).copy()).cuda()
+    dg.dg_rk3_step(ctx, q, 1e-3, 2, forcing=h)
+    ref, plain = q_or, q_or
+    for _ in range(2):
+        ref = algorithm1.corrected_step(ref, 1e-3, mesh, flow, params, sc, mode="post", io_vars=(1, 2, 3), bf16=True)
+        plain = dgsem.rk3_step(plain, 1e-3, lambda z: dgsem.rhs(z, mesh, flow))
+    got = q.cpu().numpy().reshape(q_or.shape)
+    # the forcing's effect over the two steps (the momenta directly, density and energy
+    # through the second step's fluxes) within the network tolerance
+    assert rel(got[1:4] - plain[1:4], ref[1:4] - plain[1:4]) < NN_RTOL
+    assert rel(got - plain, ref - plain) < NN_RTOL
+    # and it differs from the in-stage placement only at second order in dt
+    stage = algorithm1.corrected_step(algorithm1.corrected_step(q_or, 1e-3, mesh, flow, params, sc, mode="stage",
+                                                                io_vars=(1, 2, 3), bf16=True),
+                                      1e-3, mesh, flow, params, sc, mode="stage", io_vars=(1, 2, 3), bf16=True)
+    assert np.linalg.norm(got[1:4] - stage[1:4]) < 0.05 * np.linalg.norm(ref[1:4] - plain[1:4])
+    nn.nn_destroy(h)
+    dg.dg_destroy(ctx)
+
+
 def test_save_load_roundtrip_and_corruption_detection(L, tmp_path):
     from paper_2207_11571_gb300 import dg, nn
     h, _ = make_net(nn, 192, 64, 2, seed=5, first_var=1, n_vars=3)
