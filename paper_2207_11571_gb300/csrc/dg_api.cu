@@ -142,11 +142,19 @@ static int diag_enqueue(dg_ctx* c, const double* q, const double* qref, const nn
   double* dev_out = c->red + (size_t)c->red_blocks * kDiagLen;
   DG_CUDA(launch_diagnostics(c, q, R, qref, c->red, c->red_blocks, dev_out, st));
   DG_CUDA(cudaMemcpyAsync(c->red_host, dev_out, kDiagLen * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // the kernels' error flag rides along in the slot after the diagnostics
+  DG_CUDA(cudaMemcpyAsync(c->red_host + kDiagLen, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
   return DG_OK;
 }
 
 static int diag_collect(dg_ctx* c, bool with_rhs, bool with_ref, dg_diag* out, cudaStream_t st) {
   DG_CUDA(cudaStreamSynchronize(st));
+  int err = 0;
+  std::memcpy(&err, c->red_host + kDiagLen, sizeof(int));
+  if (err) {
+    DG_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
+    return fail(DG_ERR_TIMEOUT, "a bounded wait in the streamed flux kernel expired (its results are invalid)");
+  }
   const double* r = c->red_host;
   const double vol = 8.0 * M_PI * M_PI * M_PI;
   std::memset(out, 0, sizeof(*out));
@@ -271,7 +279,9 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
   if (f32 && e == cudaSuccess) e = cudaMalloc(&c->dlt, 5 * c->N * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&c->rhs_tmp, 5 * c->N * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->red, (size_t)(c->red_blocks + 1) * kDiagLen * sizeof(double));
-  if (e == cudaSuccess) e = cudaMallocHost(&c->red_host, kDiagLen * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->red_host, (kDiagLen + 1) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->err_dev, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->err_dev, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->s_buf, 5 * c->N * sizeof(float));
   if (e != cudaSuccess) {
     dg_destroy(c);
@@ -294,6 +304,7 @@ int dg_destroy(dg_ctx* c) {
   cudaFree(c->s_buf);
   cudaFree(c->q_dev);
   if (c->red_host) cudaFreeHost(c->red_host);
+  if (c->err_dev) cudaFree(c->err_dev);
   for (int i = 0; i <= kMaxP; ++i) cudaFree(c->filter_dev[i]);
   delete c;
   return DG_OK;

@@ -97,6 +97,7 @@ struct dg_ctx {
   int red_blocks = 0;
   double* red_host = nullptr;  // pinned host copy of the final reduction
   double* q_dev = nullptr;     // device state for dg_advance_host
+  int* err_dev = nullptr;      // device error flag: a bounded wait in a kernel expired
   bool host_diag_pending = false;  // dg_advance_host_async enqueued diagnostics not yet collected
   int forcing_mode = DG_FORCING_STAGE;  // where dg_rk3_step applies a network forcing
   float* s_buf = nullptr;      // forcing buffer [nel][5 n^3]

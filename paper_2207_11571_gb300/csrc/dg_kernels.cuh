@@ -859,6 +859,8 @@ struct BatchTable {
   T* g[kMaxBatch];                   // RK register
   RkArgs<T> rk[kMaxBatch];
   OpConst<T> C[kMaxBatch];
+  int bulk[kMaxBatch];               // streamed phase B: own tiles by TMA bulk copies (see StreamMesh)
+  int* err[kMaxBatch];               // device error flag of the instance (may be NULL)
 };
 
 __device__ __forceinline__ int batch_instance(const int* start, int n, int b) {
@@ -902,6 +904,39 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// TMA bulk copies (cp.async.bulk, global -> shared, completion counted in bytes on an
+// mbarrier).  Addresses 16-byte aligned, size a multiple of 16 bytes.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bulk_bar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_bar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void bulk_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// Bounded wait for the phase with the given parity (about a second); false on expiry.
+__device__ __forceinline__ bool bulk_wait(unsigned long long* bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > 2000000000LL) return false;
+  }
+}
+
 // load_face_data with cp.async (no registers held while the copies fly).
 template <int D>
 __device__ __forceinline__ void copy_face_data(const float* qf, const float* vis, long long N, long long g,
@@ -940,16 +975,29 @@ struct StreamItem {
   const OpConst<float>* C;
   const RkArgs<float>* rk;
   Forcing fc;
-  int e;  // element
+  int e;     // element
+  int bulk;  // own tile by TMA bulk copies (every component row 16-byte aligned modulo the element shift)
+  int* err;  // device error flag (may be NULL)
 };
 
-// Shared memory of the streamed kernel, in floats: D, lifted terms, the per-direction
-// volume fluxes and then their derivatives [3][5][np], and two buffers of (own tile
-// [14][np], halo [9][6 n2]).
+// Shared memory of the streamed kernel, in floats: two mbarriers (4 floats), D, lifted
+// terms, the per-direction volume fluxes and then their derivatives [3][5][np], and two
+// 16-byte aligned buffers of (own tile [14][kTS], halo [9][6 n2]).  An own-tile row has
+// room for the element's 0-3 float misalignment (node nd of component c at c kTS + sh + nd,
+// sh = (e np) mod 4), so that the bulk copies land on 16-byte boundaries.
+template <int P>
+__host__ __device__ constexpr int stream_tile_stride() { return ((P + 1) * (P + 1) * (P + 1) + 3 + 3) & ~3; }
+template <int P>
+__host__ __device__ constexpr int stream_buf_floats() {
+  return (14 * stream_tile_stride<P>() + kFaceComponents * 6 * (P + 1) * (P + 1) + 3) & ~3;
+}
+template <int P>
+__host__ __device__ constexpr int stream_buf_offset() {
+  return (4 + (P + 1) * (P + 1) + 5 * 6 * (P + 1) * (P + 1) + 15 * (P + 1) * (P + 1) * (P + 1) + 3) & ~3;
+}
 template <int P>
 __host__ __device__ constexpr int stream_smem_floats() {
-  return (P + 1) * (P + 1) + 5 * 6 * (P + 1) * (P + 1) + 15 * (P + 1) * (P + 1) * (P + 1) +
-         2 * (14 * (P + 1) * (P + 1) * (P + 1) + kFaceComponents * 6 * (P + 1) * (P + 1));
+  return stream_buf_offset<P>() + 2 * stream_buf_floats<P>();
 }
 
 
@@ -959,25 +1007,50 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
   using T = float;
   constexpr int n = P + 1, n2 = n * n, np = n2 * n, haloN = 6 * n2;
   constexpr int FC = kFaceComponents;
-  constexpr int kBuf = 14 * np + FC * haloN;
+  constexpr int kTS = stream_tile_stride<P>();
+  constexpr int kBuf = stream_buf_floats<P>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sD = reinterpret_cast<T*>(smem_raw);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);  // one per buffer
+  T* sD = reinterpret_cast<T*>(smem_raw) + 4;
   T* sS = sD + n2;                 // [5][haloN]: lifted interface terms
   T* sV = sS + 5 * haloN;          // [3][5][np]: volume fluxes, then their derivatives
-  T* buf0 = sV + 15 * np;          // two buffers: [14][np] own tile, then [9][haloN] halo
+  T* buf0 = reinterpret_cast<T*>(smem_raw) + stream_buf_offset<P>();  // two buffers: own tile, halo
 
-  auto prefetch = [&](int item, T* b) {
+  // element k + 1's own tile and halo into buffer bi; the own tile's rows by one bulk
+  // copy each (16-byte aligned interior, issued by thread 0, counted on bar[bi]) and their
+  // 0-3 float ragged ends by 4-byte cp.async, or (unaligned layouts) all by cp.async
+  auto prefetch = [&](int item, int bi) {
     const StreamItem m = src.at(item);
+    T* b = buf0 + bi * kBuf;
     const long long N = m.C->N;
     const long long e0 = (long long)m.e * np;
-    for (int nd = threadIdx.x; nd < np; nd += blockDim.x) {
+    const int sh = (int)(e0 & 3);
+    if (m.bulk) {
+      const int hd = (4 - sh) & 3, tl = (sh + np) & 3, L = np - hd - tl;
+      if (threadIdx.x == 0) {
+        bulk_expect_tx(&bar[bi], 14u * 4u * (unsigned)L);
+        for (int c = 0; c < 14; ++c) {
+          const float* g = (c < 5 ? m.qf + c * N : m.vis + (c - 5) * N) + e0;
+          bulk_copy(b + c * kTS + sh + hd, g + hd, 4u * (unsigned)L, &bar[bi]);
+        }
+      }
+      for (int i = threadIdx.x; i < 14 * 8; i += blockDim.x) {
+        const int c = i >> 3, j = i & 7;
+        if (j < 4 ? j >= hd : j - 4 >= tl) continue;
+        const int nd = j < 4 ? j : np - tl + (j - 4);
+        const float* g = (c < 5 ? m.qf + c * N : m.vis + (c - 5) * N) + e0;
+        cp_async4(b + c * kTS + sh + nd, g + nd);
+      }
+    } else {
+      for (int nd = threadIdx.x; nd < np; nd += blockDim.x) {
 #pragma unroll
-      for (int v = 0; v < 5; ++v) cp_async4(b + v * np + nd, m.qf + v * N + e0 + nd);
+        for (int v = 0; v < 5; ++v) cp_async4(b + v * kTS + sh + nd, m.qf + v * N + e0 + nd);
 #pragma unroll
-      for (int c = 0; c < 9; ++c) cp_async4(b + (5 + c) * np + nd, m.vis + c * N + e0 + nd);
+        for (int c = 0; c < 9; ++c) cp_async4(b + (5 + c) * kTS + sh + nd, m.vis + c * N + e0 + nd);
+      }
     }
     const BlockCoords bc = block_coords(m.e, m.C->K);
-    T* h = b + 14 * np;
+    T* h = b + 14 * kTS;
     for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
       const Item<P> it = item_of<P>(t);
       const int enb = neighbour_of(bc, 0, m.C->K, it.d, it.side ? 1 : -1);
@@ -993,7 +1066,13 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
 
   int item = blockIdx.x;
   if (item >= n_items) return;
-  prefetch(item, buf0);
+  if (threadIdx.x == 0) {
+    bulk_bar_init(&bar[0]);
+    bulk_bar_init(&bar[1]);
+    bulk_bar_fence_init();
+  }
+  __syncthreads();
+  prefetch(item, 0);
   {
     const OpConst<T>& C0 = *src.at(item).C;   // D depends on P only
     for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C0.D[t];
@@ -1002,20 +1081,29 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
   const bool active = node < np;
   const int idx[3] = {node % n, (node / n) % n, node / n2};
 
+  unsigned phases = 0u;   // bit i: parity of buffer i's next bulk phase (members may mix modes)
   for (int k = 0; item < n_items; item += gridDim.x, ++k) {
+    const StreamItem m = src.at(item);
     T* b = buf0 + (k & 1) * kBuf;
     cp_async_wait_all();
-    __syncthreads();                       // this item's data landed; the other buffer is free
+    bool landed = true;
+    if (m.bulk) {
+      landed = bulk_wait(&bar[k & 1], (phases >> (k & 1)) & 1u);
+      phases ^= 1u << (k & 1);
+    }
+    if (__syncthreads_or(!landed)) {       // this item's data landed; the other buffer is free
+      if (threadIdx.x == 0 && m.err) atomicExch(m.err, 1);
+      break;                               // a bounded wait expired: give up (host reports it)
+    }
     const int next = item + gridDim.x;
-    if (next < n_items) prefetch(next, buf0 + ((k + 1) & 1) * kBuf);
+    if (next < n_items) prefetch(next, (k + 1) & 1);
 
-    const StreamItem m = src.at(item);
     const OpConst<T>& C = *m.C;
     const RkArgs<T>& rk = *m.rk;
     const long long N = C.N;
     const long long gi = (long long)m.e * np + node;
-    T* sX = b;
-    T* sH = b + 14 * np;
+    T* sX = b + (int)(((long long)m.e * np) & 3);   // own tile: component c of node nd at sX[c kTS + nd]
+    T* sH = b + 14 * kTS;
 
     // RK operands of this thread's node, loaded now and used at the end
     T gold[5], dold[5];
@@ -1038,9 +1126,9 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
     if (active) {
       T s[5], vs[9];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) s[v] = sX[v * np + node];
+      for (int v = 0; v < 5; ++v) s[v] = sX[v * kTS + node];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) vs[c] = sX[(5 + c) * np + node];
+      for (int c = 0; c < 9; ++c) vs[c] = sX[(5 + c) * kTS + node];
       const Prim<T> w = prim_c(s, C);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -1058,7 +1146,7 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
       const int o = face_node<P>(it.d, it.side ? P : 0, it.ab);
       T so[5], to[4], sn[5], tn[4];
 #pragma unroll
-      for (int v = 0; v < 5; ++v) so[v] = sX[v * np + o];
+      for (int v = 0; v < 5; ++v) so[v] = sX[v * kTS + o];
 #pragma unroll
       for (int v = 0; v < 5; ++v) sn[v] = sH[v * haloN + t];
 #pragma unroll
@@ -1066,17 +1154,17 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
       switch (it.d) {
         case 0:
 #pragma unroll
-          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(0, i)) * np + o];
+          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(0, i)) * kTS + o];
           interface_item<0>(so, to, sn, tn, sS + t, haloN, it.side, C);
           break;
         case 1:
 #pragma unroll
-          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(1, i)) * np + o];
+          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(1, i)) * kTS + o];
           interface_item<1>(so, to, sn, tn, sS + t, haloN, it.side, C);
           break;
         default:
 #pragma unroll
-          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(2, i)) * np + o];
+          for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(2, i)) * kTS + o];
           interface_item<2>(so, to, sn, tn, sS + t, haloN, it.side, C);
       }
     }
@@ -1148,12 +1236,14 @@ struct StreamMesh {
   Forcing fc;
   OpConst<float> C;
   RkArgs<float> rk;
+  int bulk;  // qf and vis 16-byte aligned and N a multiple of 4: own tiles by TMA bulk copies
+  int* err;  // device error flag (may be NULL)
 };
 
 struct SingleSource {
   const StreamMesh& m;
   __device__ __forceinline__ StreamItem at(int item) const {
-    return StreamItem{m.q, m.qf, m.vis, m.dqdt, m.greg, m.dlt, &m.C, &m.rk, m.fc, item};
+    return StreamItem{m.q, m.qf, m.vis, m.dqdt, m.greg, m.dlt, &m.C, &m.rk, m.fc, item, m.bulk, m.err};
   }
 };
 
@@ -1162,7 +1252,7 @@ struct BatchSource {
   __device__ __forceinline__ StreamItem at(int item) const {
     const int i = batch_instance(tb.block_start, tb.n, item);
     return StreamItem{tb.q[i], tb.qf[i], tb.vis[i], nullptr, tb.g[i], tb.dlt[i], &tb.C[i], &tb.rk[i], Forcing{},
-                      item - tb.block_start[i]};
+                      item - tb.block_start[i], tb.bulk[i], tb.err[i]};
   }
 };
 

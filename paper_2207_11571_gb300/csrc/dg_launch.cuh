@@ -149,6 +149,13 @@ cudaError_t stream_grid(K kern, int threads, size_t smem, int items, int* grid) 
   return cudaSuccess;
 }
 
+// Own tiles of the streamed kernel by TMA bulk copies: every component row of qf and vis
+// must start on a 16-byte boundary up to the element's shift (e np) mod 4.
+inline int stream_bulk_ok(const dg_ctx* c) {
+  return (reinterpret_cast<uintptr_t>(c->qf) % 16 == 0) && (reinterpret_cast<uintptr_t>(c->vis) % 16 == 0) &&
+         (c->N % 4 == 0);
+}
+
 // Streamed phase B (FP32 operator, P >= 6, one element per block step).
 template <int P, int MODE>
 cudaError_t flux_stream_launch(const dg_ctx* c, double* q, double* dqdt, const Forcing& f,
@@ -169,6 +176,8 @@ cudaError_t flux_stream_launch(const dg_ctx* c, double* q, double* dqdt, const F
   m.fc = f;
   m.C = make_const<float>(c);
   m.rk = rk;
+  m.bulk = stream_bulk_ok(c);
+  m.err = c->err_dev;
   kern<<<grid, stream_threads(P), smem, st>>>(m);
   return cudaGetLastError();
 }
@@ -273,6 +282,8 @@ void fill_batch(BatchTable<T>* tb, dg_ctx* const* ctx, double* const* q, const d
     tb->g[i] = static_cast<T*>(c->g);
     tb->rk[i] = RkArgs<T>{T(A), T(B), T(dt[i]), T(invB1)};
     tb->C[i] = make_const<T>(c);
+    tb->bulk[i] = stream_bulk_ok(c);
+    tb->err[i] = c->err_dev;
   }
   tb->block_start[n] = blocks;
 }

@@ -124,8 +124,10 @@ def test_rhs_fp64_matches_oracle_on_rough_state(dg, K, P, les, E):
 
 
 @pytest.mark.parametrize("K,P,les", [(4, 3, False), (3, 3, True), (2, 6, True), (2, 8, False), (8, 3, False),
-                                     (3, 4, False), (2, 5, True)])
+                                     (3, 4, False), (2, 5, True), (3, 8, False), (3, 6, True)])
 def test_rhs_fp32_error_against_fp64_oracle(dg, K, P, les):
+    """At P >= 6 the streamed kernel copies the own tiles with TMA bulk copies when N is a
+    multiple of 4 (even K) and with 4-byte cp.async otherwise (odd K): both are covered."""
     c = Ctx(dg, K, P, les=les, precision=1)
     _, q_or = c.tgv()
     R = c.rhs(to_dev(q_or))
