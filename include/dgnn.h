@@ -271,6 +271,14 @@ int dg_blocking(const dg_ctx* ctx, int* elems_per_block, int* block_shape);
  * widening FP32 -> FP64 is not exact (mismatches[1]).  mismatches: HOST, 2 values. */
 int dg_check_conversions(const double* x, int64_t n, int64_t* mismatches, void* stream);
 
+/* Self-check of the bounded device-side waits (failure detection without a fault): one
+ * block waits on two mbarriers that nothing arrives on, with the operator's bulk-copy wait
+ * and the tensor-core kernels' wait.  Both must give up after their limit (about one
+ * second) and the kernel must return, leaving the context usable.  Returns DG_OK and the
+ * elapsed time in *seconds (HOST, may be NULL); DG_ERR_CUDA if a wait reported success
+ * without arrivals or on a CUDA error.  Synchronises the stream. */
+int dg_check_bounded_waits(double* seconds, void* stream);
+
 const char* dg_last_error(void);
 
 #ifdef __cplusplus

@@ -10,6 +10,7 @@
 #include "dg_aux.h"
 #include "dg_kernels.cuh"
 #include "nn_bridge.h"
+#include "tc_common.cuh"
 
 namespace dgnn {
 
@@ -544,6 +545,52 @@ extern "C" int dg_set_forcing_mode(dg_ctx* c, int mode) {
   if (mode != DG_FORCING_STAGE && mode != DG_FORCING_POST)
     return fail(DG_ERR_INVALID_ARG, "dg_set_forcing_mode: unknown mode");
   c->forcing_mode = mode;
+  return DG_OK;
+}
+
+namespace dgnn {
+// Two bounded waits on mbarriers that never complete (no arrivals): out[0] from the
+// operator's bulk-copy wait, out[1] from the tensor-core wait; 1 = reported completion.
+__global__ void k_wait_selfcheck(int* out) {
+  __shared__ unsigned long long bars[2];
+  if (threadIdx.x == 0) {
+    bulk_bar_init(&bars[0]);
+    bulk_bar_init(&bars[1]);
+    bulk_bar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) out[0] = bulk_wait(&bars[0], 0u) ? 1 : 0;
+  if (threadIdx.x == 32) out[1] = tc::mbar_wait(reinterpret_cast<uint64_t*>(&bars[1]), 0u) ? 1 : 0;
+}
+}  // namespace dgnn
+
+extern "C" int dg_check_bounded_waits(double* seconds, void* stream) {
+  using namespace dgnn;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d = nullptr;
+  DG_CUDA(cudaMalloc(&d, 2 * sizeof(int)));
+  int h[2] = {-1, -1};
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0xFF, 2 * sizeof(int), st);
+  if (e == cudaSuccess) e = cudaEventRecord(a, st);
+  if (e == cudaSuccess) {
+    k_wait_selfcheck<<<1, 64, 0, st>>>(d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "dg_check_bounded_waits");
+  if (h[0] != 0 || h[1] != 0)
+    return fail(DG_ERR_CUDA, "dg_check_bounded_waits: a wait reported completion without arrivals");
+  if (seconds) *seconds = ms / 1e3;
   return DG_OK;
 }
 

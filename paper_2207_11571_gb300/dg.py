@@ -79,6 +79,7 @@ _SIGS = {
     "dg_autotune": [_P, _P, _D, ctypes.POINTER(_I), ctypes.POINTER(_D), _P],
     "dg_blocking": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     "dg_set_forcing_mode": [_P, _I],
+    "dg_check_bounded_waits": [ctypes.POINTER(_D), _P],
     "dg_rhs_noalloc": [_I, _I, _D, _D, _D, _I, _I, _P, _P, _P],
     "dg_create_batch": [ctypes.POINTER(dg_instance_desc), _I, ctypes.POINTER(dg_opts), ctypes.POINTER(_P)],
     "dg_batch_destroy": [_P],
@@ -305,6 +306,13 @@ def dg_autotune(ctx, q, dt, stream=None):
     check(lib().dg_autotune(ctypes.c_void_p(ctx), ptr(q), float(dt), ctypes.byref(E), ctypes.byref(ms),
                             stream_ptr(stream)))
     return E.value, ms.value
+
+
+def dg_check_bounded_waits(stream=None):
+    """Runs the bounded-wait self-check; returns the seconds the two expiring waits took."""
+    sec = ctypes.c_double()
+    check(lib().dg_check_bounded_waits(ctypes.byref(sec), stream_ptr(stream)))
+    return sec.value
 
 
 DG_FORCING_STAGE, DG_FORCING_POST = 0, 1

@@ -331,6 +331,16 @@ def test_advance_host_async_on_two_streams_equals_device_path(dg):
         dg.dg_advance_host_async(ctxs[0].h, dev[0], 1e-3, 1)
 
 
+def test_bounded_waits_expire_and_leave_the_context_usable(dg):
+    """Failure detection without a fault: waits on mbarriers that nothing completes give up
+    after their limit (about a second), the kernel returns, and the next launches work."""
+    secs = dg.dg_check_bounded_waits()
+    assert 0.2 < secs < 10.0, secs
+    c = Ctx(dg, 2, 3)
+    q, q_or = c.tgv()
+    assert_fp64_parity(c.rhs(to_dev(q_or)), q_or, c.mesh, c.flow)
+
+
 def test_rhs_rejects_aliasing_and_size_mismatch(dg):
     c = Ctx(dg, 2, 3)
     q, _ = c.tgv()
