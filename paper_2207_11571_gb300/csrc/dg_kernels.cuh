@@ -980,9 +980,11 @@ struct StreamItem {
   int* err;  // device error flag (may be NULL)
 };
 
-// Shared memory of the streamed kernel, in floats: two mbarriers (4 floats), D, lifted
-// terms, the per-direction volume fluxes and then their derivatives [3][5][np], and two
-// 16-byte aligned buffers of (own tile [14][kTS], halo [9][6 n2]).  An own-tile row has
+// Shared memory of the streamed kernel, in floats: two mbarriers (4 floats), the
+// per-direction volume fluxes and then their derivatives [3][5][np], and two 16-byte
+// aligned buffers of (own tile [14][kTS], halo [9][6 n2]); the interface items write
+// their lifted terms over the halo slots they read (components 0-4), so that the
+// footprint leaves room for the L1 cache that the halo gathers and RK loads go through.  An own-tile row has
 // room for the element's 0-3 float misalignment (node nd of component c at c kTS + sh + nd,
 // sh = (e np) mod 4), so that the bulk copies land on 16-byte boundaries.
 template <int P>
@@ -993,7 +995,7 @@ __host__ __device__ constexpr int stream_buf_floats() {
 }
 template <int P>
 __host__ __device__ constexpr int stream_buf_offset() {
-  return (4 + (P + 1) * (P + 1) + 5 * 6 * (P + 1) * (P + 1) + 15 * (P + 1) * (P + 1) * (P + 1) + 3) & ~3;
+  return (4 + 15 * (P + 1) * (P + 1) * (P + 1) + 3) & ~3;
 }
 template <int P>
 __host__ __device__ constexpr int stream_smem_floats() {
@@ -1011,9 +1013,7 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
   constexpr int kBuf = stream_buf_floats<P>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw);  // one per buffer
-  T* sD = reinterpret_cast<T*>(smem_raw) + 4;
-  T* sS = sD + n2;                 // [5][haloN]: lifted interface terms
-  T* sV = sS + 5 * haloN;          // [3][5][np]: volume fluxes, then their derivatives
+  T* sV = reinterpret_cast<T*>(smem_raw) + 4;  // [3][5][np]: volume fluxes, then their derivatives
   T* buf0 = reinterpret_cast<T*>(smem_raw) + stream_buf_offset<P>();  // two buffers: own tile, halo
 
   // element k + 1's own tile and halo into buffer bi; the own tile's rows by one bulk
@@ -1073,10 +1073,6 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
   }
   __syncthreads();
   prefetch(item, 0);
-  {
-    const OpConst<T>& C0 = *src.at(item).C;   // D depends on P only
-    for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C0.D[t];
-  }
   const int node = threadIdx.x;
   const bool active = node < np;
   const int idx[3] = {node % n, (node / n) % n, node / n2};
@@ -1140,7 +1136,8 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
       }
     }
 
-    // interface terms, one work item per (face, face node)
+    // interface terms, one work item per (face, face node); each item reads its halo slot
+    // and then writes its lifted terms over components 0-4 of that slot
     for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
       const Item<P> it = item_of<P>(t);
       const int o = face_node<P>(it.d, it.side ? P : 0, it.ab);
@@ -1155,17 +1152,17 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
         case 0:
 #pragma unroll
           for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(0, i)) * kTS + o];
-          interface_item<0>(so, to, sn, tn, sS + t, haloN, it.side, C);
+          interface_item<0>(so, to, sn, tn, sH + t, haloN, it.side, C);
           break;
         case 1:
 #pragma unroll
           for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(1, i)) * kTS + o];
-          interface_item<1>(so, to, sn, tn, sS + t, haloN, it.side, C);
+          interface_item<1>(so, to, sn, tn, sH + t, haloN, it.side, C);
           break;
         default:
 #pragma unroll
           for (int i = 0; i < 4; ++i) to[i] = sX[(5 + face_vis_index(2, i)) * kTS + o];
-          interface_item<2>(so, to, sn, tn, sS + t, haloN, it.side, C);
+          interface_item<2>(so, to, sn, tn, sH + t, haloN, it.side, C);
       }
     }
     __syncthreads();
@@ -1194,7 +1191,7 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
       if (!(right || left)) continue;
       const int h = item_index<P>(face_ab<P>(d, idx), right ? 1 : 0, d, 0);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) R[c] += sS[c * haloN + h];
+      for (int c = 0; c < 5; ++c) R[c] += sH[c * haloN + h];   // lifted terms over the halo slots
     }
     if (m.fc.s != nullptr) {
       const long long fb = (long long)m.e * m.fc.stride + node;
