@@ -208,6 +208,13 @@ int dg_advance_host_wait(dg_ctx* ctx, dg_diag* diag, void* stream);
 int dg_project(const dg_ctx* hi, const dg_ctx* lo, const double* q_hi, double* q_lo,
                void* stream);
 
+/* q_hi = I q_lo: each element's order-P_lo nodal polynomial evaluated at the order-P_hi
+ * Gauss-Lobatto nodes (exact: Q_{P_lo} is contained in Q_{P_hi}), so dg_project(hi, lo)
+ * returns q_lo.  Used to restart a high-order burst from a low-order state (retraining
+ * the forcing of Algorithm 1 during a run).  Both contexts share K, P_lo <= P_hi; q_lo,
+ * q_hi: device. */
+int dg_prolong(const dg_ctx* lo, const dg_ctx* hi, const double* q_lo, double* q_hi, void* stream);
+
 /* Diagnostics of q (FP64 reductions, deterministic order).  q_ref (device, same
  * layout) may be NULL; when given, e_inf = ||q - q_ref||_inf on the momenta (Eq. 9).
  * forcing (may be NULL) enters dke_dt.  out: HOST.  Returns DG_ERR_NONFINITE (after

@@ -189,6 +189,19 @@ def project(q_hi, P_hi, P_lo):
     return out
 
 
+def prolong(q_lo, P_lo, P_hi):
+    """Each element's order-P_lo nodal polynomial evaluated at the order-P_hi GL nodes
+    (Lagrange interpolation in each direction): the exact embedding of Q_{P_lo} into
+    Q_{P_hi}, the inverse of the filter on Q_{P_lo}."""
+    xi_lo, _ = basis.gl_nodes_weights(P_lo)
+    xi_hi, _ = basis.gl_nodes_weights(P_hi)
+    I1 = basis.lagrange_interpolation_matrix(xi_lo, xi_hi)
+    out = np.einsum('im,...m->...i', I1, q_lo)
+    out = np.einsum('jm,...mi->...ji', I1, out)
+    out = np.einsum('km,...mji->...kji', I1, out)
+    return out
+
+
 # ----------------------------------------------------------------------------- diagnostics
 
 def diagnostics(q, mesh, flow, R=None, q_ref=None):

@@ -307,6 +307,7 @@ int dg_destroy(dg_ctx* c) {
   if (c->red_host) cudaFreeHost(c->red_host);
   if (c->err_dev) cudaFree(c->err_dev);
   for (int i = 0; i <= kMaxP; ++i) cudaFree(c->filter_dev[i]);
+  for (int i = 0; i <= kMaxP; ++i) cudaFree(c->prolong_dev[i]);
   delete c;
   return DG_OK;
 }
@@ -398,6 +399,22 @@ int dg_project(const dg_ctx* hi, const dg_ctx* lo, const double* q_hi, double* q
     DG_CUDA(cudaMemcpy(h->filter_dev[lo->P], G, sizeof(double) * lo->n * hi->n, cudaMemcpyHostToDevice));
   }
   DG_CUDA(launch_project(hi, lo, q_hi, q_lo, h->filter_dev[lo->P], (cudaStream_t)stream));
+  return DG_OK;
+}
+
+int dg_prolong(const dg_ctx* lo, const dg_ctx* hi, const double* q_lo, double* q_hi, void* stream) {
+  if (!hi || !lo || !q_hi || !q_lo) return fail(DG_ERR_INVALID_ARG, "dg_prolong: NULL argument");
+  if (hi->K != lo->K) return fail(DG_ERR_INVALID_ARG, "dg_prolong: contexts must share K");
+  if (lo->P > hi->P) return fail(DG_ERR_INVALID_ARG, "dg_prolong: needs P_lo <= P_hi");
+  dg_ctx* l = const_cast<dg_ctx*>(lo);
+  if (!l->prolong_dev[hi->P]) {
+    double I[kMaxN1 * kMaxN1];
+    int rc = build_prolongation(lo->P, hi->P, I);
+    if (rc) return rc;
+    DG_CUDA(cudaMalloc(&l->prolong_dev[hi->P], sizeof(I)));
+    DG_CUDA(cudaMemcpy(l->prolong_dev[hi->P], I, sizeof(double) * lo->n * hi->n, cudaMemcpyHostToDevice));
+  }
+  DG_CUDA(launch_prolong(lo, hi, q_lo, q_hi, l->prolong_dev[hi->P], (cudaStream_t)stream));
   return DG_OK;
 }
 

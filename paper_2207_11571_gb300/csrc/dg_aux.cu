@@ -93,6 +93,14 @@ cudaError_t launch_project(const dg_ctx* hi, const dg_ctx* lo, const double* qh,
   return cudaGetLastError();
 }
 
+// k_project is a transform from nh to nl nodes per direction for any nh, nl <= 9 (its
+// scratch holds every intermediate of either direction), so it also interpolates upwards.
+cudaError_t launch_prolong(const dg_ctx* lo, const dg_ctx* hi, const double* ql, double* qh, const double* Idev,
+                           cudaStream_t st) {
+  k_project<<<lo->nel, 256, 0, st>>>(ql, qh, lo->nel, lo->n, hi->n, lo->N, hi->N, Idev);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- diagnostics
 
 // Per-node contributions reduced in a fixed order: block tree, then one block over the

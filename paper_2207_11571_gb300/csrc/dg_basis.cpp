@@ -143,4 +143,23 @@ int build_filter(int P_hi, int P_lo, double* G) {
   return DG_OK;
 }
 
+int build_prolongation(int P_lo, int P_hi, double* I) {
+  if (P_lo < 1 || P_lo > P_hi || P_hi > kMaxP)
+    return fail(DG_ERR_INVALID_ARG, "prolongation needs 1 <= P_lo <= P_hi <= 8");
+  Basis1D hi, lo;
+  int st = build_basis(P_hi, &hi);
+  if (st) return st;
+  st = build_basis(P_lo, &lo);
+  if (st) return st;
+  const int nh = P_hi + 1, nl = P_lo + 1;
+  for (int a = 0; a < nh; ++a)
+    for (int j = 0; j < nl; ++j) {
+      long double l = 1.0L;
+      for (int k = 0; k < nl; ++k)
+        if (k != j) l *= ((long double)hi.xi[a] - lo.xi[k]) / ((long double)lo.xi[j] - lo.xi[k]);
+      I[a * nl + j] = (double)l;
+    }
+  return DG_OK;
+}
+
 }  // namespace dgnn

@@ -33,6 +33,9 @@ struct Basis1D {
 int build_basis(int P, Basis1D* out);
 // Filter G of Eq. 2 in 1D: (P_lo+1) x (P_hi+1), row-major.
 int build_filter(int P_hi, int P_lo, double* G);
+// Interpolation from the order-P_lo nodes to the order-P_hi nodes in 1D, (P_hi+1) x
+// (P_lo+1) row-major: I[a][j] = l_j(xi_hi_a), l_j the Lagrange basis on the P_lo nodes.
+int build_prolongation(int P_lo, int P_hi, double* I);
 
 // Mesh and basis constants passed by value to every kernel.
 struct Geom {
@@ -102,6 +105,7 @@ struct dg_ctx {
   int forcing_mode = DG_FORCING_STAGE;  // where dg_rk3_step applies a network forcing
   float* s_buf = nullptr;      // forcing buffer [nel][5 n^3]
   double* filter_dev[dgnn::kMaxP + 1] = {};  // filter G to each lower order (dg_project)
+  double* prolong_dev[dgnn::kMaxP + 1] = {};  // interpolation to each higher order (dg_prolong)
   bool borrowed = false;       // member of a dg_batch: released by dg_batch_destroy only
 };
 

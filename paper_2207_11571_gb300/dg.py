@@ -72,6 +72,7 @@ _SIGS = {
     "dg_advance_host_async": [_P, _P, _D, _I, _P, _I, _P],
     "dg_advance_host_wait": [_P, ctypes.POINTER(dg_diag), _P],
     "dg_project": [_P, _P, _P, _P, _P],
+    "dg_prolong": [_P, _P, _P, _P, _P],
     "dg_diagnostics": [_P, _P, _P, _P, ctypes.POINTER(dg_diag), _P],
     "dg_stable_dt": [_P, _P, _D, ctypes.POINTER(_D), _P],
     "dg_make_pairs": [_P, _P, _P, _P, _D, _I, _I, _P, _P, _P],
@@ -257,6 +258,13 @@ def dg_project(hi, lo, q_hi, q_lo, stream=None):
     _check_state(hi, q_hi, "q_hi")
     _check_state(lo, q_lo, "q_lo")
     check(lib().dg_project(ctypes.c_void_p(hi), ctypes.c_void_p(lo), ptr(q_hi), ptr(q_lo), stream_ptr(stream)))
+
+
+def dg_prolong(lo, hi, q_lo, q_hi, stream=None):
+    """q_hi = the order-P_lo solution of lo evaluated at hi's nodes (same K)."""
+    _check_state(lo, q_lo, "q_lo")
+    _check_state(hi, q_hi, "q_hi")
+    check(lib().dg_prolong(ctypes.c_void_p(lo), ctypes.c_void_p(hi), ptr(q_lo), ptr(q_hi), stream_ptr(stream)))
 
 
 def dg_diagnostics(ctx, q, q_ref=None, forcing=None, stream=None, raise_nonfinite=True):

@@ -136,18 +136,39 @@ def train(args, X, Y, first_var, n_vars):
         net = nn.nn_create(feat, feat, args.width, args.hidden, first_var, n_vars, args.batch,
                            inputs.uniform_draws(dims, args.seed))
         nn.nn_compute_scalers(net, X, Y)
+    t0 = time.perf_counter()
+    losses = run_epochs(args, net, X, Y, args.epochs, args.seed)
+    return net, losses, time.perf_counter() - t0
+
+
+def run_epochs(args, net, X, Y, epochs, seed):
+    """Shuffled mini-batch epochs of nn_train_step; returns the last batch's loss per epoch."""
     rows = X.shape[0]
     losses = []
-    t0 = time.perf_counter()
-    for epoch in range(args.epochs):
-        perm = torch.from_numpy(inputs.epoch_permutation(rows, args.seed, epoch)).cuda()
+    for epoch in range(epochs):
+        perm = torch.from_numpy(inputs.epoch_permutation(rows, seed, epoch)).cuda()
         ep = []
         for b0 in range(0, rows - args.batch + 1, args.batch):
             ep.append(nn.nn_train_step(net, X, Y, perm[b0:b0 + args.batch], lr=args.lr,
                                        want_loss=(b0 + args.batch > rows - args.batch)))
         losses.append(ep[-1])
     torch.cuda.synchronize()
-    return net, losses, time.perf_counter() - t0
+    return losses
+
+
+def retrain(args, run, net, ctx_hi, ctx_lo, dt_lo, ratio, first_var, n_vars, seed):
+    """Train-advance-retrain (the extension the paper proposes as future work): a short
+    high-order burst restarted from the corrected low-order state (prolonged to P_HO, the
+    exact embedding), Algorithm 1's pairs over it, and more epochs of the same network from
+    its current weights and scalers.  Returns (seconds, losses)."""
+    t0 = time.perf_counter()
+    q_burst = new_state(ctx_hi)
+    dg.dg_prolong(ctx_lo, ctx_hi, run.q, q_burst)
+    n = max(1, math.ceil(args.retrain_window / dt_lo - 1e-9))
+    X, Y = generate_pairs(args, ctx_hi, q_burst, ctx_lo, dt_lo, ratio, n, first_var, n_vars)
+    losses = run_epochs(args, net, X, Y, args.retrain_epochs, seed)
+    del X, Y, q_burst
+    return time.perf_counter() - t0, losses
 
 
 def rel_l2(a, b):
@@ -214,6 +235,11 @@ def parse(argv=None):
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=2207)
+    ap.add_argument("--retrain_every", type=float, default=0.0,
+                    help="corrected run: every this many time units, retrain on a high-order burst "
+                         "restarted from its own state (0: off)")
+    ap.add_argument("--retrain_window", type=float, default=0.15, help="length of each high-order burst")
+    ap.add_argument("--retrain_epochs", type=int, default=10, help="epochs of each retraining")
     ap.add_argument("--init_net", type=str, default="", help="start training from this saved network")
     ap.add_argument("--save_net", type=str, default="", help="save the trained network here")
     ap.add_argument("--out", type=str, default="experiment.json")
@@ -303,6 +329,8 @@ def run(args):
     for r in runs:
         r.sample(t0, qbar if r.P == args.P_lo else None)
     n_samples = round((args.t_end - t0) / args.sample)
+    retrains = []
+    every = round(args.retrain_every / args.sample) if args.retrain_every > 0 else 0
     for j in range(1, n_samples + 1):
         tj = t0 + j * args.sample
         ref.advance(args.sample)
@@ -312,11 +340,19 @@ def run(args):
         for r in runs:
             r.advance(args.sample)
             r.sample(tj, qbar if r.P == args.P_lo else None)
+        corr_run = runs[0]
+        if every and j % every == 0 and j < n_samples and corr_run.diverged_at is None:
+            secs, rl = retrain(args, corr_run, net, ctx_hi, ctx_lo, dt_lo, ratio, first_var, n_vars,
+                               args.seed + 1000 + j)
+            corr_run.ms += 1e3 * secs          # the burst and the training are part of its cost
+            corr_run.net = net                 # forcing back on after a fallback
+            retrains.append({"t": tj, "seconds": secs, "loss_first": rl[0], "loss_last": rl[-1]})
 
     out = {"config": vars(args), "dt_lo": dt_lo, "ratio_hi_per_lo": ratio, "n_pairs": n_pairs,
            "pairs_rows": n_pairs * K ** 3, "train_loss": losses, "train_seconds": t_train,
            "pairs_seconds": t_pairs, "ho_to_window_seconds": t_ho_initial,
-           "reference": {"name": ref.name, "ms": ref.ms, "steps": ref.steps}, "runs": []}
+           "reference": {"name": ref.name, "ms": ref.ms, "steps": ref.steps}, "runs": [],
+           "retrains": retrains}
     for r in runs:
         rec = {"name": r.name, "P": r.P, "ms": r.ms, "steps": r.steps,
                "errors": run_errors(r, ref.t, ref.dke, ref.ke, bar_ke),

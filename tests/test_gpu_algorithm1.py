@@ -55,3 +55,20 @@ def test_transfer_learning_starts_from_the_saved_network(experiment, saved_net):
     fresh = ex.run(ex.parse(COMMON + window))
     assert warm["train_loss"][0] < 0.5 * fresh["train_loss"][0], (warm["train_loss"], fresh["train_loss"])
     assert warm["train_loss"][-1] < fresh["train_loss"][-1], (warm["train_loss"], fresh["train_loss"])
+
+
+def test_retraining_during_the_run_restarts_high_order_bursts(experiment):
+    """Train-advance-retrain: every 0.1 time units the corrected run's state is prolonged to
+    P_HO, a short burst gives new pairs and the network trains on from its weights; the run
+    stays stable, every retraining is accounted in the corrected run's cost, and the
+    retraining loss starts near the trained network's level (warm start)."""
+    from paper_2207_11571_gb300 import experiment as ex
+    args = ex.parse(COMMON + ["--t_train", "0.5", "--t_train_end", "0.75", "--t_end", "0.95", "--epochs", "10",
+                              "--forcing", "post", "--retrain_every", "0.1", "--retrain_window", "0.05",
+                              "--retrain_epochs", "2"])
+    out = ex.run(args)
+    assert len(out["retrains"]) >= 2, out["retrains"]
+    corr = out["runs"][0]
+    assert corr["diverged_at"] is None
+    assert corr["ms"] >= 1e3 * sum(r["seconds"] for r in out["retrains"])
+    assert out["retrains"][0]["loss_first"] < 10 * out["train_loss"][-1]

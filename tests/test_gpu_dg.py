@@ -272,6 +272,18 @@ def test_project_matches_oracle(dg, P_hi, P_lo, K):
     np.testing.assert_allclose(to_np(q_lo, K, P_lo + 1), dgsem.project(q_or, P_hi, P_lo), rtol=1e-14, atol=1e-14)
 
 
+@pytest.mark.parametrize("P_lo,P_hi,K", [(3, 8, 2), (2, 6, 3), (5, 5, 2)])
+def test_prolong_matches_oracle_and_filter_inverts_it(dg, P_lo, P_hi, K):
+    lo, hi = Ctx(dg, K, P_lo), Ctx(dg, K, P_hi)
+    _, q_or = lo.tgv()
+    q_hi = torch.empty(5 * hi.N, dtype=torch.float64, device="cuda")
+    dg.dg_prolong(lo.h, hi.h, to_dev(q_or), q_hi)
+    np.testing.assert_allclose(to_np(q_hi, K, P_hi + 1), dgsem.prolong(q_or, P_lo, P_hi), rtol=1e-14, atol=1e-14)
+    back = torch.empty(5 * lo.N, dtype=torch.float64, device="cuda")
+    dg.dg_project(hi.h, lo.h, q_hi, back)
+    np.testing.assert_allclose(to_np(back, K, P_lo + 1), q_or, rtol=1e-14, atol=1e-13)   # rho e ~ 179: relative
+
+
 @pytest.mark.parametrize("first,nv", [(0, 5), (1, 3)])
 def test_make_pairs_match_oracle(dg, first, nv):
     """Algorithm 1's pair (q_bar^n, (q_bar^{n+1} - q_NN^{n+1}) / dt) on the GPU vs the oracle."""

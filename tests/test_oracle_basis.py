@@ -102,3 +102,26 @@ def test_project_3d_tensor_product_reproduces_q3_field():
     f8 = poly(*m8.coordinates())[None]
     f3 = poly(*m3.coordinates())[None]
     np.testing.assert_allclose(dgsem.project(f8, 8, 3), f3, atol=1e-12)
+
+
+@pytest.mark.parametrize("P_lo,P_hi", [(3, 8), (2, 8), (3, 6), (5, 5)])
+def test_prolong_is_exact_on_low_order_polynomials(P_lo, P_hi):
+    """Prolongation evaluates the order-P_lo interpolant at the P_hi nodes: a polynomial of
+    degree <= P_lo per direction sampled on the P_lo nodes comes out as its values on the
+    P_hi nodes."""
+    ml, mh = dgsem.Mesh(2, P_lo), dgsem.Mesh(2, P_hi)
+    def poly(X, Y, Z):
+        return 2 - X + 0.5 * Y * Z + X ** min(P_lo, 2) * Y - (Z ** P_lo) / 3
+    fl = poly(*ml.coordinates())[None]
+    fh = poly(*mh.coordinates())[None]
+    np.testing.assert_allclose(dgsem.prolong(fl, P_lo, P_hi), fh, atol=1e-11, rtol=1e-12)
+
+
+@pytest.mark.parametrize("P_lo,P_hi", [(3, 8), (2, 7), (4, 6)])
+def test_filter_inverts_prolongation(P_lo, P_hi):
+    """Any nodal P_lo field is a polynomial in Q_{P_lo}; the filter G (the L2 projection
+    onto Q_{P_lo}) returns it unchanged after prolongation."""
+    rng = np.random.default_rng(P_lo + 10 * P_hi)
+    q = rng.standard_normal((5, 2, 2, 2) + (P_lo + 1,) * 3)
+    back = dgsem.project(dgsem.prolong(q, P_lo, P_hi), P_hi, P_lo)
+    np.testing.assert_allclose(back, q, atol=1e-12)
