@@ -145,7 +145,14 @@ def rhs(q, mesh, flow, forcing=None):
     R = np.zeros_like(q)
     for d in range(3):
         F = physics.inviscid_flux(q, d, g) - physics.viscous_flux(q, G, mu, lam, d)
-        R -= (2.0 / h) * d_contract(F, mesh.D, d)
+        if flow.split:
+            # split form: the Euler part of the volume term is 2 sum_m D_im F#(q_i, q_m)
+            # along each line (kep_flux); the viscous part keeps the standard form.  The
+            # surface term below uses the nodal flux F as in the standard form.
+            Fv = physics.viscous_flux(q, G, mu, lam, d)
+            R -= (2.0 / h) * (split_volume(q, mesh.D, d, g) - d_contract(Fv, mesh.D, d))
+        else:
+            R -= (2.0 / h) * d_contract(F, mesh.D, d)
 
         qm = face(q, d, 1)
         qp = neighbour(face(q, d, 0), d, +1)
@@ -162,6 +169,15 @@ def rhs(q, mesh, flow, forcing=None):
     if forcing is not None:
         R += forcing
     return R
+
+
+def split_volume(q, D, d, gamma):
+    """2 sum_m D[i, m] F#(q_i, q_m) along the node lines of direction d (F# = kep_flux)."""
+    ax = NODE_AXIS[d]
+    qd = np.moveaxis(q, ax, -1)                          # (..., n): the line along d last
+    Fs = physics.kep_flux(qd[..., :, None], qd[..., None, :], d, gamma)   # (..., i, m)
+    V = 2.0 * np.einsum('im,...im->...i', D, Fs)
+    return np.moveaxis(V, -1, ax)
 
 
 def rk3_step(q, dt, rhs_fn):

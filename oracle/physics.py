@@ -24,6 +24,7 @@ class Flow:
     Prt: float = 0.9
     les_delta: float = 0.0  # filter width; 0 -> h/(P+1) (reading: not stated in the paper)
     inviscid: bool = False  # mu = 0 (used by the Euler convergence pin)
+    split: bool = False     # kinetic-energy-preserving split-form volume term (see dgsem.rhs)
 
     @property
     def mu(self):
@@ -57,6 +58,30 @@ def inviscid_flux(q, d, gamma):
         f[1 + i] = q[1 + i] * vd + (p if i == d else 0.0)
     f[4] = vd * (q[4] + p)  # rho v_d H
     return f
+
+
+def kep_flux(qa, qb, d, gamma):
+    """Two-point flux of the kinetic-energy-preserving split form (Pirozzoli's averages,
+    as used in split-form DGSEM; not part of the paper, a robustness variant of its
+    volume term): with {a} = (a_a + a_b)/2, mass flux m = {rho}{v_d},
+        (m, m {v_1} + {p} delta_1d, m {v_2} + {p} delta_2d, m {v_3} + {p} delta_3d, m {H}),
+    H = (rho e + p) / rho.  Symmetric in (qa, qb); equal to the Euler flux column d when
+    qa = qb."""
+    def prim(q):
+        rho = q[0]
+        v = q[1:4] / rho
+        p = pressure(q, gamma)
+        return rho, v, p, (q[4] + p) / rho
+    ra, va, pa, Ha = prim(qa)
+    rb, vb, pb, Hb = prim(qb)
+    m = 0.25 * (ra + rb) * (va[d] + vb[d])
+    pm = 0.5 * (pa + pb)
+    F = np.empty(np.broadcast_shapes(qa.shape, qb.shape))
+    F[0] = m
+    for j in range(3):
+        F[1 + j] = m * 0.5 * (va[j] + vb[j]) + (pm if j == d else 0.0)
+    F[4] = m * 0.5 * (Ha + Hb)
+    return F
 
 
 def transport_coefficients(q, G, flow, delta):

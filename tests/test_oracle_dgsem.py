@@ -390,3 +390,75 @@ def test_operator_at_an_element_depends_only_on_elements_two_face_steps_away():
         Rp = dgsem.rhs(qp, mp, flow)[:, 2, 2, 2]
         ez, ey, ex = centre
         np.testing.assert_allclose(Rp, R[:, ez, ey, ex], rtol=0, atol=1e-12 * np.abs(R).max())
+
+
+# ----------------------------------------------------------------------------- split-form volume term
+
+def test_kep_flux_is_symmetric_and_consistent():
+    """F#(a, b) = F#(b, a) and F#(q, q) = Euler flux column d (consistency)."""
+    qa = inputs.random_conserved((3, 5), 7, rhoE=(1 / (1.4 * 0.09) / 0.4, 1.0))
+    qb = inputs.random_conserved((3, 5), 8, rhoE=(1 / (1.4 * 0.09) / 0.4, 1.0))
+    for d in range(3):
+        np.testing.assert_allclose(physics.kep_flux(qa, qb, d, 1.4), physics.kep_flux(qb, qa, d, 1.4), rtol=1e-15)
+        np.testing.assert_allclose(physics.kep_flux(qa, qa, d, 1.4), physics.inviscid_flux(qa, d, 1.4),
+                                   rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("les", [False, True])
+def test_split_form_free_stream_and_conservation(les):
+    """The split-form operator keeps a uniform state and conserves all five variables on
+    rough states (2 sum_m D_im F#_im telescopes under the SBP property of GL nodes)."""
+    mesh = dgsem.Mesh(3, 3)
+    flow = physics.Flow(Re=50.0, Mach=0.3, les=les, split=True)
+    q = uniform_state(mesh, 1.2, (0.3, -0.2, 0.1), flow.p0)
+    assert np.abs(dgsem.rhs(q, mesh, flow)).max() < 1e-12 * flow.p0 * (2 / mesh.h) * 16
+    q = inputs.random_conserved((3,) * 3 + (4,) * 3, 11, rhoE=(1 / (1.4 * 0.09) / 0.4, 1.0))
+    R = dgsem.rhs(q, mesh, flow)
+    W = mesh.quadrature_weights()
+    for v in range(5):
+        assert abs((W * R[v]).sum()) < 1e-13 * (W * np.abs(R[v])).sum(), v
+
+
+def test_split_form_equals_standard_form_where_the_flux_is_linear():
+    """With v and p constant (an Euler density wave) the mass and momentum fluxes are
+    linear in the state, so the split average 2 sum_m D_im {.} reduces to D f exactly
+    and the two operators agree in those four components; the energy flux rho v H is not
+    linear in rho and the forms differ there."""
+    mesh = dgsem.Mesh(3, 3)
+    x, y, z = mesh.coordinates()
+    std = physics.Flow(Mach=0.5, inviscid=True)
+    spl = physics.Flow(Mach=0.5, inviscid=True, split=True)
+    q = uniform_state(mesh, 1.0, (1.0, -0.5, 0.25), std.p0)
+    rho = 1.0 + 0.2 * np.sin(x + 2 * y - z)
+    q[0] = rho
+    q[1], q[2], q[3] = rho, -0.5 * rho, 0.25 * rho
+    q[4] = std.p0 / 0.4 + 0.5 * rho * (1 + 0.25 + 0.0625)
+    Rs, Rp = dgsem.rhs(q, mesh, std), dgsem.rhs(q, mesh, spl)
+    np.testing.assert_allclose(Rp[:4], Rs[:4], rtol=0, atol=1e-12 * np.abs(Rs[:4]).max())
+    assert np.abs(Rp[4] - Rs[4]).max() > 1e-8 * np.abs(Rs[4]).max()
+
+
+def test_split_form_density_wave_converges():
+    """The split form is a consistent discretisation: the density wave error falls with h
+    at the rate of the standard form (bar P - 0.5 on K = 2, 4, 8)."""
+    flow = physics.Flow(Mach=0.5, inviscid=True, split=True)
+    P = 3
+    errs = []
+    for K in (2, 4, 8):
+        mesh = dgsem.Mesh(K, P)
+        x, y, z = mesh.coordinates()
+        def exact(t):
+            rho = 1.0 + 0.2 * np.sin(x + y + z - 3.0 * t)
+            q = uniform_state(mesh, 1.0, (1.0, 1.0, 1.0), flow.p0)
+            q[0] = rho
+            q[1:4] = rho
+            q[4] = flow.p0 / 0.4 + 1.5 * rho
+            return q
+        T, nsteps = 0.2, 5 * K
+        q = exact(0.0)
+        for _ in range(nsteps):
+            q = dgsem.rk3_step(q, T / nsteps, lambda s: dgsem.rhs(s, mesh, flow))
+        W = mesh.quadrature_weights()
+        errs.append(math.sqrt((W * (q[0] - exact(T)[0]) ** 2).sum() / (2 * math.pi) ** 3))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert errs[2] < 2e-3 and min(rates) > P - 0.5, (errs, rates)
