@@ -68,6 +68,11 @@ typedef struct {
                          1: 2 x 2 x 2 cubes of elements (P <= 3 and even K only, else
                          DG_ERR_INVALID_ARG): a cube's twelve internal faces need no halo
                          and their interface fluxes are formed once for both sides */
+  int volume_flux;    /* 0: standard strong-form volume term (default, the paper's);
+                         1: kinetic-energy-preserving split form, 2 sum_m D_im F#(q_i, q_m)
+                         with Pirozzoli's two-point flux for the Euler part (a robustness
+                         variant for under-resolved turbulence, not in the paper; rows of
+                         elements only: block_shape 1 returns DG_ERR_INVALID_ARG) */
 } dg_opts;
 
 /* Integral diagnostics (Sec. 2.4 Eq. 9 and kinetic-energy budget), FP64. */

@@ -51,6 +51,9 @@ cudaError_t launch_gradient(const dg_ctx* c, const double* q, int src, cudaStrea
 cudaError_t launch_flux(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
                         double dt, cudaStream_t st) {
   const double invB1 = 1.0 / kRkB[0];
+  if (c->geom.split)
+    return c->opts.precision == DG_PREC_FP32 ? flux_split_f32(c, q, dqdt, f, mode, A, B, dt, invB1, st)
+                                             : flux_split_f64(c, q, dqdt, f, mode, A, B, dt, invB1, st);
   return c->opts.precision == DG_PREC_FP32 ? flux_f32(c, q, dqdt, f, mode, A, B, dt, invB1, st)
                                            : flux_f64(c, q, dqdt, f, mode, A, B, dt, invB1, st);
 }
@@ -213,6 +216,9 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
   if (o.block_shape != 0 && o.block_shape != 1) return fail(DG_ERR_INVALID_ARG, "dg_create: block_shape must be 0 or 1");
   if (o.block_shape == 1 && (!cube_ok(P) || K % 2 != 0))
     return fail(DG_ERR_INVALID_ARG, "dg_create: cube blocks need P <= 3 and an even K");
+  if (o.volume_flux != 0 && o.volume_flux != 1) return fail(DG_ERR_INVALID_ARG, "dg_create: volume_flux must be 0 or 1");
+  if (o.volume_flux == 1 && o.block_shape != 0)
+    return fail(DG_ERR_INVALID_ARG, "dg_create: the split-form volume term runs on rows of elements (block_shape 0)");
 
   dg_ctx* c = new dg_ctx();
   c->K = K;
@@ -238,6 +244,7 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
   c->geom.E = o.elems_per_block > 0 ? o.elems_per_block : default_elems_per_block(P);
   c->geom.cube = o.block_shape;
   if (c->geom.cube) c->geom.E = kCubeElems;
+  c->geom.split = o.volume_flux;
   c->geom.two_over_h = 2.0 / h;
   c->geom.winv = 1.0 / c->basis.w[0];
   std::memset(c->geom.D, 0, sizeof(c->geom.D));
@@ -518,7 +525,7 @@ extern "C" int dg_autotune(dg_ctx* c, const double* q, double dt, int* best_E, d
   // candidates: rows of E = 1, 2, 4, ... elements, then (where allowed) cubes
   std::vector<std::pair<int, int>> cand;  // (E, cube)
   for (int E = 1; E <= max_elems_per_block(c->P); E *= 2) cand.push_back({E, 0});
-  if (cube_ok(c->P) && c->K % 2 == 0 && !c->borrowed) cand.push_back({kCubeElems, 1});
+  if (cube_ok(c->P) && c->K % 2 == 0 && !c->borrowed && !c->geom.split) cand.push_back({kCubeElems, 1});
   for (const auto& ce : cand) {
     if (e != cudaSuccess) break;
     c->geom.E = ce.first;

@@ -53,6 +53,10 @@ cudaError_t gradient_f32(const dg_ctx* c, const double* q, int src, cudaStream_t
 cudaError_t gradient_f64(const dg_ctx* c, const double* q, int src, cudaStream_t st);
 cudaError_t flux_f32(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
                      double dt, double invB1, cudaStream_t st);
+cudaError_t flux_split_f32(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                           double dt, double invB1, cudaStream_t st);
+cudaError_t flux_split_f64(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                           double dt, double invB1, cudaStream_t st);
 cudaError_t flux_f64(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
                      double dt, double invB1, cudaStream_t st);
 

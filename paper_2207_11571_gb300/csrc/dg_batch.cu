@@ -163,6 +163,7 @@ int dg_create_batch(const dg_instance_desc* desc, int n, const dg_opts* opts, dg
   dg_opts_default(&o);
   if (opts) o = *opts;
   if (o.block_shape != 0) return fail(DG_ERR_INVALID_ARG, "dg_create_batch: batch members use rows of elements (block_shape 0)");
+  if (o.volume_flux != 0) return fail(DG_ERR_INVALID_ARG, "dg_create_batch: batch members use the standard volume term");
   dg_batch* b = new dg_batch();
   b->precision = o.precision;
   for (int i = 0; i < n; ++i) {

@@ -44,6 +44,7 @@ struct Geom {
   long long N;      // nodes = nel * n^3
   int E;            // elements per block
   int cube;         // 1: blocks are 2 x 2 x 2 cubes of elements (E = 8; P <= 3, even K)
+  int split;        // 1: kinetic-energy-preserving split-form volume term (rows of elements)
   double two_over_h;
   double winv;      // 1 / w_0 = 1 / w_P
   double D[kMaxN1 * kMaxN1];

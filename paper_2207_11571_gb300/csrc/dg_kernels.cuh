@@ -557,6 +557,32 @@ __host__ __device__ constexpr int min_blocks_for(int P, int tsize) {
   return tsize == 8 ? 1 : P == 6 ? 4 : P == 7 ? 3 : 2;
 }
 
+// Split form: a node's primitives for the two-point flux, (rho, v1, v2, v3, p', H) with
+// H = (rho e + p) / rho (the reference pressure cancels in the split pressure term, so p'
+// enters it; H needs the full enthalpy).
+template <typename T>
+__device__ __forceinline__ void store_split_prims(const T s[5], const Prim<T>& w, const OpConst<T>& C, T* out,
+                                                  int stride) {
+  out[0] = w.rho;
+  out[stride] = w.v[0];
+  out[2 * stride] = w.v[1];
+  out[3 * stride] = w.v[2];
+  out[4 * stride] = w.pp;
+  out[5 * stride] = (s[4] + w.pp + C.Hc) * w.ir;
+}
+
+// Pirozzoli's kinetic-energy-preserving two-point flux in direction d from two nodes'
+// primitives: m = {rho}{v_d}; (m, m {v_j} + {p'} delta_jd, m {H}).
+template <typename T>
+__device__ __forceinline__ void kep_flux_prims(const T a[6], const T b[6], int d, T F[5]) {
+  const T m = T(0.25) * (a[0] + b[0]) * (a[1 + d] + b[1 + d]);
+  F[0] = m;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) F[1 + k] = m * (T(0.5) * (a[1 + k] + b[1 + k]));
+  F[1 + d] += T(0.5) * (a[4] + b[4]);
+  F[4] = m * (T(0.5) * (a[5] + b[5]));
+}
+
 // Phase B forms the volume fluxes before the interface phase, in a tile of their own
 // (FP32 at P = 4, 5, one node per thread): one barrier less for a larger shared
 // footprint.  Measured per RK3 step, 24^3/P4 408 vs 415 us, 20^3/P5 431 vs 439 us, but
@@ -573,7 +599,11 @@ __host__ __device__ constexpr bool flux_early(int P, int tsize) { return tsize =
 // tile and the RK operands are loaded after the interface phase (register budget).
 // CUBE: the block is a 2 x 2 x 2 cube of elements; the halo holds only the external
 // faces, and each internal face is one work item that writes both sides' lifted terms.
-template <int P, typename T, int MODE, bool CUBE = false>
+// SPLIT: the Euler part of the volume term in the kinetic-energy-preserving split form,
+// 2 sum_m D_im F#(q_i, q_m) along each line with Pirozzoli's two-point flux F# (mass flux
+// {rho}{v_d}; momentum m {v_j} + {p'} delta_jd; energy m {H}), from a tile of primitives;
+// the viscous part and the surface terms keep the standard form.
+template <int P, typename T, int MODE, bool CUBE = false, bool SPLIT = false>
 __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, const T* __restrict__ qf,
                                            const T* __restrict__ vis, double* __restrict__ dqdt,
                                            T* __restrict__ greg, float* __restrict__ dlt, const Forcing& fc,
@@ -597,6 +627,7 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   T* sF = kEarlyF ? sX + 14 * tileN : sX; // [15][E np]: volume fluxes
   T* sH = kEarlyF ? sF + kTileComponents * tileN : sX + kTileComponents * tileN;  // [9][E 6 n2]
   T* sS = sH + FC * haloN;                // [5][E 6 n2]: lifted interface terms
+  T* sW = sS + 5 * faceN;                 // SPLIT: primitives [6][E np] (rho, v, p', H)
   const int e0 = blk * E;
   const BlockCoords bc = CUBE ? cube_coords(blk, C.K) : block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
@@ -643,13 +674,14 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
     for (int c = 0; c < 9; ++c) sX[(5 + c) * tileN + tix[j]] = vs[j][c];
     if (kEarlyF) {
       const Prim<T> w = prim_c(s[j], C);
+      if (SPLIT) store_split_prims(s[j], w, C, sW + tix[j], tileN);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         T F[5], fv[5];
         euler_flux(s[j], w, C.Hc, d, F);
         viscous_flux(vs[j], w.v, d, fv);
 #pragma unroll
-        for (int c = 0; c < 5; ++c) sF[(5 * d + c) * tileN + tix[j]] = F[c] - fv[c];
+        for (int c = 0; c < 5; ++c) sF[(5 * d + c) * tileN + tix[j]] = SPLIT ? -fv[c] : F[c] - fv[c];
       }
     }
   }
@@ -749,13 +781,14 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
       for (int c = 0; c < 9; ++c) vs[j][c] = sX[(5 + c) * tileN + tix[j]];
     }
     const Prim<T> w = prim_c(s[j], C);
+    if (SPLIT) store_split_prims(s[j], w, C, sW + tix[j], tileN);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       T F[5], fv[5];
       euler_flux(s[j], w, C.Hc, d, F);
       viscous_flux(vs[j], w.v, d, fv);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) sX[(5 * d + c) * tileN + tix[j]] = F[c] - fv[c];
+      for (int c = 0; c < 5; ++c) sX[(5 * d + c) * tileN + tix[j]] = SPLIT ? -fv[c] : F[c] - fv[c];
     }
   }
   if (!kEarlyF) __syncthreads();
@@ -779,6 +812,31 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
 #pragma unroll
         for (int m = 0; m < n; ++m) acc += Drow[m] * sF[(5 * d + c) * tileN + base + m * stride[d]];
         R[c] -= C.s2h * acc;
+      }
+    }
+    if (SPLIT) {
+      const int ti = tix[j];
+      T wi[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) wi[k] = sW[k * tileN + ti];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T* Drow = sD + idx[d] * n;
+        const int base = lj * np + nd - idx[d] * stride[d];
+        T acc[5] = {T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          const int o = base + m * stride[d];
+          T wm[6];
+#pragma unroll
+          for (int k = 0; k < 6; ++k) wm[k] = sW[k * tileN + o];
+          T F[5];
+          kep_flux_prims(wi, wm, d, F);
+#pragma unroll
+          for (int c = 0; c < 5; ++c) acc[c] += Drow[m] * F[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) R[c] -= C.s2h * (T(2) * acc[c]);
       }
     }
 #pragma unroll
@@ -833,11 +891,11 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   }
 }
 
-template <int P, typename T, int MODE, bool CUBE = false>
+template <int P, typename T, int MODE, bool CUBE = false, bool SPLIT = false>
 __global__ void __launch_bounds__(flux_max_threads(P), min_blocks_for(P, sizeof(T)))
 k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ vis, double* __restrict__ dqdt,
        T* __restrict__ greg, float* __restrict__ dlt, Forcing fc, const OpConst<T> C, RkArgs<T> rk) {
-  flux_block<P, T, MODE, CUBE>(blockIdx.x, q, qf, vis, dqdt, greg, dlt, fc, C, rk);
+  flux_block<P, T, MODE, CUBE, SPLIT>(blockIdx.x, q, qf, vis, dqdt, greg, dlt, fc, C, rk);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -262,6 +262,52 @@ cudaError_t flux_t(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, i
 }
 
 // ---------------------------------------------------------------------------------------
+// Split-form phase B (rows of E elements, every order, both precisions): k_flux with the
+// two-point-flux volume term and a tile of primitives [6][E np] on top of flux_smem.
+template <int P, typename T, int MODE>
+cudaError_t flux_split_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, const RkArgs<T>& rk,
+                         cudaStream_t st) {
+  constexpr int np = (P + 1) * (P + 1) * (P + 1);
+  const int E = c->geom.E;
+  const size_t smem = flux_smem<P, T>(E) + sizeof(T) * 6 * E * np;
+  auto kern = k_flux<P, T, MODE, false, true>;
+  cudaError_t e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (c->nel + E - 1) / E;
+  kern<<<grid, flux_threads(P, E), smem, st>>>(q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt,
+                                                static_cast<T*>(c->g), c->dlt, f, make_const<T>(c), rk);
+  return cudaGetLastError();
+}
+
+template <int P, typename T>
+cudaError_t flux_split_dispatch_mode(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode,
+                                     const RkArgs<T>& rk, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    switch (mode) {
+      case 0: return flux_split_p<P, T, 0>(c, q, dqdt, f, rk, st);
+      case 2: return flux_split_p<P, T, 2>(c, q, dqdt, f, rk, st);
+      case 3: return flux_split_p<P, T, 3>(c, q, dqdt, f, rk, st);
+      case 4: return flux_split_p<P, T, 4>(c, q, dqdt, f, rk, st);
+    }
+  } else {
+    switch (mode) {
+      case 0: return flux_split_p<P, T, 0>(c, q, dqdt, f, rk, st);
+      case 1: return flux_split_p<P, T, 1>(c, q, dqdt, f, rk, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T>
+cudaError_t flux_split_t(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                         double dt, double invB1, cudaStream_t st) {
+  const RkArgs<T> rk{T(A), T(B), T(dt), T(invB1)};
+#define DG_S(PP) flux_split_dispatch_mode<PP, T>(c, q, dqdt, f, mode, rk, st)
+  DG_FOR_EACH_P(DG_S)
+#undef DG_S
+}
+
+// ---------------------------------------------------------------------------------------
 // Batched RK stage: one phase-A and one phase-B launch for all instances of order P.
 // Instances must share the operator precision T and the elements-per-block E.
 

@@ -32,7 +32,8 @@ class DGError(RuntimeError):
 class dg_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int),
                 ("gamma", ctypes.c_double), ("Cs", ctypes.c_double), ("Prt", ctypes.c_double),
-                ("les_delta", ctypes.c_double), ("elems_per_block", ctypes.c_int), ("block_shape", ctypes.c_int)]
+                ("les_delta", ctypes.c_double), ("elems_per_block", ctypes.c_int), ("block_shape", ctypes.c_int),
+                ("volume_flux", ctypes.c_int)]
 
 
 class dg_diag(ctypes.Structure):

@@ -32,9 +32,9 @@ import torch
 from . import dg, inputs, nn
 
 
-def make_ctx(K, P, args, les=False, precision=None):
+def make_ctx(K, P, args, les=False, precision=None, split=False):
     prec = dg.DG_PREC_FP32 if precision is None else precision
-    return dg.dg_create(K, P, args.Re, args.Mach, args.Pr, int(les), precision=prec)
+    return dg.dg_create(K, P, args.Re, args.Mach, args.Pr, int(les), precision=prec, volume_flux=int(split))
 
 
 def new_state(ctx):
@@ -214,6 +214,9 @@ def parse(argv=None):
     ap.add_argument("--Pr", type=float, default=0.71)
     ap.add_argument("--les_hi", action="store_true")
     ap.add_argument("--les_lo", action="store_true")
+    ap.add_argument("--split_lo", action="store_true",
+                    help="low-order runs with the kinetic-energy-preserving split-form volume term")
+    ap.add_argument("--split_hi", action="store_true", help="the same for the high-order run")
     ap.add_argument("--cfl", type=float, default=0.7)
     ap.add_argument("--t_train", type=float, default=4.0)
     ap.add_argument("--t_train_end", type=float, default=5.0)
@@ -254,7 +257,7 @@ def run(args):
     wall0 = time.perf_counter()
 
     # 1. high-order evolution to the training window
-    ctx_hi = make_ctx(K, args.P_hi, args, args.les_hi)
+    ctx_hi = make_ctx(K, args.P_hi, args, args.les_hi, split=args.split_hi)
     q_hi = new_state(ctx_hi)
     nodes_hi = dg.dg_sizes(ctx_hi)[0]
     dg.dg_init_tgv(ctx_hi, q_hi, torch.from_numpy(inputs.perturbation((5, nodes_hi)).ravel()).cuda())
@@ -273,7 +276,7 @@ def run(args):
     t_ho_initial = time.perf_counter() - wall0
 
     # 2. pairs over the training window (Algorithm 1, first loop)
-    ctx_lo = make_ctx(K, args.P_lo, args, args.les_lo)
+    ctx_lo = make_ctx(K, args.P_lo, args, args.les_lo, split=args.split_lo)
     qtmp = new_state(ctx_lo)
     dg.dg_project(ctx_hi, ctx_lo, q_hi, qtmp)
     dt_lo_cfl = stable_dt(ctx_lo, qtmp, args.cfl)
@@ -284,8 +287,8 @@ def run(args):
     q_hi_start = q_hi.clone() if args.eval_start == "window_start" else None
     t1 = time.perf_counter()
     if args.window_precision == "fp64":   # the training window in an FP64 operator
-        w_hi = make_ctx(K, args.P_hi, args, args.les_hi, dg.DG_PREC_FP64)
-        w_lo = make_ctx(K, args.P_lo, args, args.les_lo, dg.DG_PREC_FP64)
+        w_hi = make_ctx(K, args.P_hi, args, args.les_hi, dg.DG_PREC_FP64, split=args.split_hi)
+        w_lo = make_ctx(K, args.P_lo, args, args.les_lo, dg.DG_PREC_FP64, split=args.split_lo)
     else:
         w_hi, w_lo = ctx_hi, ctx_lo
     X, Y = generate_pairs(args, w_hi, q_hi, w_lo, dt_lo, ratio, n_pairs, first_var, n_vars)
@@ -315,7 +318,7 @@ def run(args):
                     guard=not args.no_guard))
     plain_ctx = {}
     for P in [int(p) for p in args.plain.split(",")]:
-        c = make_ctx(K, P, args, args.les_lo)
+        c = make_ctx(K, P, args, args.les_lo, split=args.split_lo)
         plain_ctx[P] = c
         qp = new_state(c)
         dg.dg_project(ctx_hi, c, q_hi, qp)

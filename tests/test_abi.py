@@ -50,7 +50,8 @@ def test_opts_defaults(L):
 
 @pytest.mark.parametrize("bad", [dict(K=0), dict(K=300), dict(P=0), dict(P=9), dict(Re=-1.0),
                                  dict(Mach=0.0), dict(closure=2), dict(block_shape=2),
-                                 dict(block_shape=1, K=5), dict(block_shape=1, P=4)])
+                                 dict(block_shape=1, K=5), dict(block_shape=1, P=4), dict(volume_flux=2),
+                                 dict(volume_flux=1, block_shape=1)])
 def test_create_rejects_bad_arguments_before_touching_cuda(L, bad):
     from paper_2207_11571_gb300 import dg
     args = dict(K=4, P=3, Re=1600.0, Mach=0.1, Pr=0.71, closure=0)
@@ -82,6 +83,9 @@ def test_batch_rejects_cube_blocks_before_touching_cuda(L):
     from paper_2207_11571_gb300 import dg
     with pytest.raises(dg.DGError) as e:
         dg.dg_create_batch([(4, 3, 1600.0, 0.1, 0.71, 0)], block_shape=1)
+    assert e.value.status == dg.DG_ERR_INVALID_ARG
+    with pytest.raises(dg.DGError) as e:
+        dg.dg_create_batch([(4, 3, 1600.0, 0.1, 0.71, 0)], volume_flux=1)
     assert e.value.status == dg.DG_ERR_INVALID_ARG
     assert L.dg_blocking(None, None, None) == dg.DG_ERR_INVALID_ARG
     assert L.dg_advance_host_async(None, None, 1e-3, 1, None, 0, None) == dg.DG_ERR_INVALID_ARG
