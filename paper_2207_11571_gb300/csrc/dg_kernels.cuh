@@ -655,6 +655,14 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
     if (MODE == 4 || MODE == 1) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) gold[j][v] = (MODE == 1 && rk.A == T(0)) ? T(0) : greg[v * N + gi[j]];
+      // the FP64 state is read only by the final update: start its lines towards L1 now, so
+      // that read does not wait on DRAM at the end of the block (no registers held)
+#pragma unroll
+      for (int v = 0; v < 5; ++v) asm volatile("prefetch.global.L1 [%0];" ::"l"(q + v * N + gi[j]));
+    }
+    if (fc.s != nullptr) {   // likewise the forcing, added to R at the end
+      const float* fs = fc.s + (gi[j] / np) * fc.stride + node[j];
+      for (int slot = 0; slot < fc.n_vars; ++slot) asm volatile("prefetch.global.L1 [%0];" ::"l"(fs + slot * np));
     }
   };
 
