@@ -668,14 +668,14 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
 
   // own loads first (all independent)
   T s[NPT][5], vs[NPT][9];
-#pragma unroll
-  for (int j = 0; j < NPT; ++j) {
-    if (!active[j]) continue;
+  auto own_loads = [&](int j) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) s[j][v] = qf[v * N + gi[j]];
 #pragma unroll
     for (int c = 0; c < 9; ++c) vs[j][c] = vis[c * N + gi[j]];
     if (kHold) load_rk(j);
+  };
+  auto own_stores = [&](int j) {
 #pragma unroll
     for (int v = 0; v < 5; ++v) sX[v * tileN + tix[j]] = s[j][v];
 #pragma unroll
@@ -692,19 +692,40 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
         for (int c = 0; c < 5; ++c) sF[(5 * d + c) * tileN + tix[j]] = SPLIT ? -fv[c] : F[c] - fv[c];
       }
     }
-  }
+  };
   // halo: neighbours' stage state and face-normal viscous quantities on every face
-  for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
-    const Item<P> it = CUBE ? cube_item_of<P>(t) : item_of<P>(t);
-    if (!CUBE && e0 + it.hl >= C.nel) continue;
-    const int enb = CUBE ? cube_neighbour(bc, it.hl, C.K, it.d, it.side ? 1 : -1)
-                         : neighbour_of(bc, it.hl, C.K, it.d, it.side ? 1 : -1);
-    const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
-    switch (it.d) {
-      case 0: load_face_data<0>(qf, vis, N, gnb, sH + t, haloN); break;
-      case 1: load_face_data<1>(qf, vis, N, gnb, sH + t, haloN); break;
-      default: load_face_data<2>(qf, vis, N, gnb, sH + t, haloN);
+  auto halo_gather = [&]() {
+    for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
+      const Item<P> it = CUBE ? cube_item_of<P>(t) : item_of<P>(t);
+      if (!CUBE && e0 + it.hl >= C.nel) continue;
+      const int enb = CUBE ? cube_neighbour(bc, it.hl, C.K, it.d, it.side ? 1 : -1)
+                           : neighbour_of(bc, it.hl, C.K, it.d, it.side ? 1 : -1);
+      const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
+      switch (it.d) {
+        case 0: load_face_data<0>(qf, vis, N, gnb, sH + t, haloN); break;
+        case 1: load_face_data<1>(qf, vis, N, gnb, sH + t, haloN); break;
+        default: load_face_data<2>(qf, vis, N, gnb, sH + t, haloN);
+      }
     }
+  };
+  if (kHold) {
+    // one node per thread: the own values stay in registers anyway, so their tile stores
+    // wait until the halo gathers are issued and the two latencies overlap
+#pragma unroll
+    for (int j = 0; j < NPT; ++j)
+      if (active[j]) own_loads(j);
+    halo_gather();
+#pragma unroll
+    for (int j = 0; j < NPT; ++j)
+      if (active[j]) own_stores(j);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NPT; ++j)
+      if (active[j]) {
+        own_loads(j);
+        own_stores(j);
+      }
+    halo_gather();
   }
   __syncthreads();
 
