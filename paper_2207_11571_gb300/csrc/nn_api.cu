@@ -64,12 +64,22 @@ constexpr int kLossThreads = 128;
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
+// Programmatic dependent launch for the chain of network kernels: each kernel first waits
+// until its predecessor has completed and its writes are visible, then lets its own
+// successor be launched, so that launch latency overlaps execution.  (A kernel launched
+// without the attribute passes the wait at once.)
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------------------------- kernels
 
 // act0[r][f] = bf16((X[row(r)][f] - mean[f]) / std[f]) for f < n_in, 0 for the padding.
 __global__ void k_prep_features(const float* __restrict__ X, const int64_t* __restrict__ idx, int rows, int n_in,
                                 int ld, const float* __restrict__ mean, const float* __restrict__ sd,
                                 bf16* __restrict__ out) {
+  pdl_enter();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)rows * ld) return;
   const int r = (int)(t / ld), f = (int)(t - (long long)r * ld);
@@ -85,6 +95,7 @@ __global__ void k_prep_features(const float* __restrict__ X, const int64_t* __re
 __global__ void k_prep_state(const double* __restrict__ q, long long N, int np, int first_var, int n_vars, int e0,
                              int rows, int ld, const double* __restrict__ mean, const float* __restrict__ sd,
                              bf16* __restrict__ out) {
+  pdl_enter();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)rows * ld) return;
   const int r = (int)(t / ld), f = (int)(t - (long long)r * ld);
@@ -102,6 +113,7 @@ __global__ void k_prep_state(const double* __restrict__ q, long long N, int np, 
 __global__ void k_prep_state_f32(const float* __restrict__ qf, long long N, int np, int first_var, int n_vars, int e0,
                                  int rows, int ld, const float* __restrict__ mshift, const float* __restrict__ sd,
                                  bf16* __restrict__ out) {
+  pdl_enter();
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)rows * ld) return;
   const int r = (int)(t / ld), f = (int)(t - (long long)r * ld);
@@ -118,6 +130,7 @@ __global__ void k_prep_state_f32(const float* __restrict__ qf, long long N, int 
 __global__ void k_loss(const float* __restrict__ y, const float* __restrict__ Y, const int64_t* __restrict__ idx,
                        int rows, int n, const float* __restrict__ mean, const float* __restrict__ sd,
                        float* __restrict__ dy, double* __restrict__ partial) {
+  pdl_enter();
   // rows over blocks, features over threads; FP32 sums of a few squares per thread, a
   // warp-shuffle reduction, then the warps' sums added in FP64 in a fixed order
   __shared__ float wsum[kLossThreads / 32];
@@ -145,6 +158,7 @@ __global__ void k_loss(const float* __restrict__ y, const float* __restrict__ Y,
   }
 }
 __global__ void k_sum_partials(const double* __restrict__ partial, int n, double scale, double* __restrict__ out) {
+  pdl_enter();
   __shared__ double sh[kLossThreads];
   double acc = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partial[i];
@@ -163,6 +177,7 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int n, double
 // columns and row tiles), so every SM takes part.
 __global__ void k_grad_prep(const float* __restrict__ g, int rows, int n, int ldb, int ldt, bf16* __restrict__ gb,
                             bf16* __restrict__ gT, float* __restrict__ part) {
+  pdl_enter();
   __shared__ float tile[32][33];
   __shared__ float colsum[8][32];
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
@@ -191,6 +206,7 @@ __global__ void k_grad_prep(const float* __restrict__ g, int rows, int n, int ld
 
 // out[i] = sum over splits z of part[z][i], in split order (deterministic split-K sum).
 __global__ void k_split_sum(const float* __restrict__ part, int splits, long long count, float* __restrict__ out) {
+  pdl_enter();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= count) return;
   float s = 0.f;
@@ -202,6 +218,7 @@ __global__ void k_split_sum(const float* __restrict__ part, int splits, long lon
 // rows sums every 32nd tile, then the 32 partial sums are added in row order
 // (deterministic).
 __global__ void k_col_sum(const float* __restrict__ part, int tiles, int n, float* __restrict__ db) {
+  pdl_enter();
   __shared__ float sh[32][33];
   const int c = blockIdx.x * 32 + threadIdx.x;
   float s = 0.f;
@@ -218,6 +235,7 @@ __global__ void k_col_sum(const float* __restrict__ part, int tiles, int n, floa
 
 // act[rows][ld] (bf16) -> actT[n][ldt] for the first n columns, rows padded with zeros.
 __global__ void k_transpose_bf16(const bf16* __restrict__ a, int rows, int n, int ld, int ldt, bf16* __restrict__ aT) {
+  pdl_enter();
   __shared__ bf16 tile[32][34];
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -253,6 +271,7 @@ struct AdamTable {
 };
 
 __global__ void k_adam(const __grid_constant__ AdamTable tb) {
+  pdl_enter();
   int j = 0;
   while (j + 1 < tb.n && (int)blockIdx.x >= tb.block_start[j + 1]) ++j;
   const AdamSeg& S = tb.seg[j];
@@ -314,6 +333,22 @@ int check_err(const nn_model* m, cudaStream_t st) {
 }
 
 inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// Launches a network kernel with programmatic stream serialization (see pdl_enter).
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // Forward through all layers for `rows` rows whose scaled inputs are in act[0].
 // last: if S != null, unscaled forcing into S (ld n_out); else scaled output into m->y.
@@ -490,12 +525,12 @@ int nn_forcing_on_state(const nn_model* m, const dg_ctx* c, const double* q, flo
       // the stage state of the FP32 operator is the reference-shifted copy written by phase A
       int rc = ensure_shift(const_cast<nn_model*>(m), c);
       if (rc) return rc;
-      k_prep_state_f32<<<blocks_for(tot, 256), 256, 0, st>>>(static_cast<const float*>(c->qf), c->N, c->np,
+      DG_CUDA(pdl_launch(k_prep_state_f32, dim3(blocks_for(tot, 256)), dim3(256), st, static_cast<const float*>(c->qf), c->N, c->np,
                                                              m->d.first_var, m->d.n_vars, e0, rows, m->pad[0],
-                                                             m->mean_shift, m->std_in, m->act[0]);
+                                                             m->mean_shift, m->std_in, m->act[0]));
     } else {
-      k_prep_state<<<blocks_for(tot, 256), 256, 0, st>>>(q, c->N, c->np, m->d.first_var, m->d.n_vars, e0, rows,
-                                                         m->pad[0], m->mean_in_d, m->std_in, m->act[0]);
+      DG_CUDA(pdl_launch(k_prep_state, dim3(blocks_for(tot, 256)), dim3(256), st, q, c->N, c->np, m->d.first_var, m->d.n_vars, e0, rows,
+                                                         m->pad[0], m->mean_in_d, m->std_in, m->act[0]));
     }
     DG_CUDA(cudaGetLastError());
     int rc = forward_layers(m, rows, s + (long long)e0 * feat, st);
@@ -624,8 +659,8 @@ int nn_forward(const nn_model* m, const float* X, float* S, int rows, void* stre
   if (rows < 1 || rows > m->d.max_batch) return fail(DG_ERR_INVALID_ARG, "nn_forward: rows outside [1, max_batch]");
   cudaStream_t st = (cudaStream_t)stream;
   const long long tot = (long long)rows * m->pad[0];
-  k_prep_features<<<blocks_for(tot, 256), 256, 0, st>>>(X, nullptr, rows, m->d.n_in, m->pad[0], m->mean_in,
-                                                        m->std_in, m->act[0]);
+  DG_CUDA(pdl_launch(k_prep_features, dim3(blocks_for(tot, 256)), dim3(256), st, X, nullptr, rows, m->d.n_in, m->pad[0], m->mean_in,
+                                                        m->std_in, m->act[0]));
   DG_CUDA(cudaGetLastError());
   return forward_layers(m, rows, S, st);
 }
@@ -648,16 +683,16 @@ int nn_train_step(nn_model* m, const float* X, const float* Y, const int64_t* id
   const int L = m->L, n_out = m->d.n_out;
   // forward, keeping every layer input (bf16) in act[]
   long long tot = (long long)batch * m->pad[0];
-  k_prep_features<<<blocks_for(tot, 256), 256, 0, st>>>(X, idx, batch, m->d.n_in, m->pad[0], m->mean_in, m->std_in,
-                                                        m->act[0]);
+  DG_CUDA(pdl_launch(k_prep_features, dim3(blocks_for(tot, 256)), dim3(256), st, X, idx, batch, m->d.n_in, m->pad[0], m->mean_in, m->std_in,
+                                                        m->act[0]));
   DG_CUDA(cudaGetLastError());
   int rc = forward_layers(m, batch, nullptr, st);
   if (rc) return rc;
   // loss and dL/dy
-  k_loss<<<kLossBlocks, kLossThreads, 0, st>>>(m->y, Y, idx, batch, n_out, m->mean_out, m->std_out, m->dy,
-                                               m->loss_part);
+  DG_CUDA(pdl_launch(k_loss, dim3(kLossBlocks), dim3(kLossThreads), st, m->y, Y, idx, batch, n_out, m->mean_out, m->std_out, m->dy,
+                                               m->loss_part));
   DG_CUDA(cudaGetLastError());
-  k_sum_partials<<<1, kLossThreads, 0, st>>>(m->loss_part, kLossBlocks, 1.0 / ((double)batch * n_out), m->loss_dev);
+  DG_CUDA(pdl_launch(k_sum_partials, dim3(1), dim3(kLossThreads), st, m->loss_part, kLossBlocks, 1.0 / ((double)batch * n_out), m->loss_dev));
   DG_CUDA(cudaGetLastError());
   // backward
   float* g = m->dy;   // gradient w.r.t. the output of layer l, [batch][dims[l+1]]
@@ -667,12 +702,12 @@ int nn_train_step(nn_model* m, const float* X, const float* Y, const int64_t* id
     const int ldb = round_up(o, 64);
     const int tiles = m->bpad / 32;
     dim3 gp(ldb / 32, tiles), bt(32, 8);
-    k_grad_prep<<<gp, bt, 0, st>>>(g, batch, o, ldb, m->bpad, m->dyb, m->dyT, m->gpart);
+    DG_CUDA(pdl_launch(k_grad_prep, dim3(gp), dim3(bt), st, g, batch, o, ldb, m->bpad, m->dyb, m->dyT, m->gpart));
     DG_CUDA(cudaGetLastError());
-    k_col_sum<<<(o + 31) / 32, dim3(32, 32), 0, st>>>(m->gpart, tiles, o, m->gb[l]);
+    DG_CUDA(pdl_launch(k_col_sum, dim3((o + 31) / 32), dim3(dim3(32, 32)), st, m->gpart, tiles, o, m->gb[l]));
     DG_CUDA(cudaGetLastError());
     dim3 gt((in + 31) / 32, (m->bpad + 31) / 32);
-    k_transpose_bf16<<<gt, bt, 0, st>>>(m->act[l], batch, in, m->pad[l], m->bpad, m->actT[l]);
+    DG_CUDA(pdl_launch(k_transpose_bf16, dim3(gt), dim3(bt), st, m->act[l], batch, in, m->pad[l], m->bpad, m->actT[l]));
     DG_CUDA(cudaGetLastError());
     // dW = g^T act : M = o, N = in, K = batch.  Few output tiles and a long K: split K
     // so that the CTAs cover the SMs, then sum the partial products in a fixed order.
@@ -693,7 +728,7 @@ int nn_train_step(nn_model* m, const float* X, const float* Y, const int64_t* id
     if (rc) return rc;
     if (splits > 1) {
       const long long cnt = (long long)o * in;
-      k_split_sum<<<blocks_for(cnt, 256), 256, 0, st>>>(m->gws, splits, cnt, m->gW[l]);
+      DG_CUDA(pdl_launch(k_split_sum, dim3(blocks_for(cnt, 256)), dim3(256), st, m->gws, splits, cnt, m->gW[l]));
       DG_CUDA(cudaGetLastError());
     }
     if (l > 0) {
@@ -733,7 +768,7 @@ int nn_train_step(nn_model* m, const float* X, const float* Y, const int64_t* id
     blocks += (int)blocks_for(cb, 256);
   }
   at.block_start[at.n] = blocks;
-  k_adam<<<blocks, 256, 0, st>>>(at);
+  DG_CUDA(pdl_launch(k_adam, dim3(blocks), dim3(256), st, at));
   DG_CUDA(cudaGetLastError());
   if (loss_out) {
     DG_CUDA(cudaMemcpyAsync(m->loss_host, m->loss_dev, 8, cudaMemcpyDeviceToHost, st));
