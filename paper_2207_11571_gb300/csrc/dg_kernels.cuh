@@ -36,6 +36,14 @@
 
 namespace dgnn {
 
+// Programmatic dependent launch between the operator's launches: a kernel waits until its
+// predecessor in the stream has completed and its writes are visible, then lets its
+// successor be launched (which happens once every block of this grid has got here, i.e.
+// in its last wave), so the next launch overlaps this one's tail.  Kernels launched
+// without the attribute pass the wait at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Maximum threads per block for order P (one node per thread, E elements per block).
 __host__ __device__ constexpr int max_threads_for(int P) {
   return P == 1 ? 256 : P <= 4 ? 512 : P == 5 ? 448 : P == 6 ? 352 : P == 7 ? 512 : 736;
@@ -414,6 +422,8 @@ template <int P, typename T, int SRC, bool CUBE = false>
 __global__ void __launch_bounds__(max_threads_for(P))
 k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, const float* __restrict__ dlt,
            T* __restrict__ qf, float* __restrict__ qn32_out, T* __restrict__ vis, const OpConst<T> C) {
+  pdl_wait();
+  pdl_release();
   gradient_block<P, T, SRC, CUBE>(blockIdx.x, q, qn32_in, dlt, qf, qn32_out, vis, C);
 }
 
@@ -924,6 +934,8 @@ template <int P, typename T, int MODE, bool CUBE = false, bool SPLIT = false>
 __global__ void __launch_bounds__(flux_max_threads(P), min_blocks_for(P, sizeof(T)))
 k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ vis, double* __restrict__ dqdt,
        T* __restrict__ greg, float* __restrict__ dlt, Forcing fc, const OpConst<T> C, RkArgs<T> rk) {
+  pdl_wait();
+  pdl_release();
   flux_block<P, T, MODE, CUBE, SPLIT>(blockIdx.x, q, qf, vis, dqdt, greg, dlt, fc, C, rk);
 }
 
@@ -1151,6 +1163,7 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
     cp_async_commit();
   };
 
+  pdl_wait();
   int item = blockIdx.x;
   if (item >= n_items) return;
   if (threadIdx.x == 0) {
@@ -1180,6 +1193,7 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
     }
     const int next = item + gridDim.x;
     if (next < n_items) prefetch(next, (k + 1) & 1);
+    else pdl_release();   // this block's last element: the successor may launch
 
     const OpConst<T>& C = *m.C;
     const RkArgs<T>& rk = *m.rk;

@@ -67,6 +67,23 @@ static cudaError_t upload_const_D() {
   return e;
 }
 
+// Launch with programmatic stream serialization (the kernels wait for their predecessor
+// themselves, see pdl_wait in dg_kernels.cuh).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 template <typename K>
 cudaError_t set_smem(K kern, size_t smem) {
   if (smem > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -113,10 +130,9 @@ cudaError_t gradient_p(const dg_ctx* c, const double* q, cudaStream_t st) {
       cudaError_t e = set_smem(kern, smem);
       if (e != cudaSuccess) return e;
       const int h = c->K / 2;
-      kern<<<h * h * h, block_threads(P, kCubeElems), smem, st>>>(
+      return launch_pdl(kern, dim3(h * h * h), dim3(block_threads(P, kCubeElems)), smem, st, 
           q, c->qn32, c->dlt, static_cast<T*>(c->qf), SRC == 0 ? c->qn32 : nullptr, static_cast<T*>(c->vis),
           make_const<T>(c));
-      return cudaGetLastError();
     }
   }
   const int E = c->geom.E;
@@ -125,10 +141,9 @@ cudaError_t gradient_p(const dg_ctx* c, const double* q, cudaStream_t st) {
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = (c->nel + E - 1) / E;
-  kern<<<grid, block_threads(P, E), smem, st>>>(q, c->qn32, c->dlt, static_cast<T*>(c->qf),
+  return launch_pdl(kern, dim3(grid), dim3(block_threads(P, E)), smem, st, q, c->qn32, c->dlt, static_cast<T*>(c->qf),
                                                 SRC == 0 ? c->qn32 : nullptr, static_cast<T*>(c->vis),
                                                 make_const<T>(c));
-  return cudaGetLastError();
 }
 
 // Grid of a persistent streamed launch: resident blocks on every SM, at most one per item.
@@ -178,8 +193,7 @@ cudaError_t flux_stream_launch(const dg_ctx* c, double* q, double* dqdt, const F
   m.rk = rk;
   m.bulk = stream_bulk_ok(c);
   m.err = c->err_dev;
-  kern<<<grid, stream_threads(P), smem, st>>>(m);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(grid), dim3(stream_threads(P)), smem, st, m);
 }
 
 template <int P, typename T, int MODE>
@@ -195,10 +209,9 @@ cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, c
       cudaError_t e = set_smem(kern, smem);
       if (e != cudaSuccess) return e;
       const int h = c->K / 2;
-      kern<<<h * h * h, flux_threads(P, kCubeElems), smem, st>>>(
+      return launch_pdl(kern, dim3(h * h * h), dim3(flux_threads(P, kCubeElems)), smem, st, 
           q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt, static_cast<T*>(c->g), c->dlt, f,
           make_const<T>(c), rk);
-      return cudaGetLastError();
     }
   }
   const int E = c->geom.E;
@@ -207,9 +220,8 @@ cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, c
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = (c->nel + E - 1) / E;
-  kern<<<grid, flux_threads(P, E), smem, st>>>(q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt,
+  return launch_pdl(kern, dim3(grid), dim3(flux_threads(P, E)), smem, st, q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt,
                                                 static_cast<T*>(c->g), c->dlt, f, make_const<T>(c), rk);
-  return cudaGetLastError();
 }
 
 // FP64 operator: modes 0 (dq/dt) and 1 (FP64 RK stage).  FP32 operator: modes 0, 2, 3, 4.
@@ -274,9 +286,8 @@ cudaError_t flux_split_p(const dg_ctx* c, double* q, double* dqdt, const Forcing
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = (c->nel + E - 1) / E;
-  kern<<<grid, flux_threads(P, E), smem, st>>>(q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt,
+  return launch_pdl(kern, dim3(grid), dim3(flux_threads(P, E)), smem, st, q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt,
                                                 static_cast<T*>(c->g), c->dlt, f, make_const<T>(c), rk);
-  return cudaGetLastError();
 }
 
 template <int P, typename T>

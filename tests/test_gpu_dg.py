@@ -189,7 +189,12 @@ def test_autotune_may_pick_cube_blocks_and_keeps_results(dg):
     after = q.clone()
     dg.dg_rk3_step(c.h, after, 1e-3, 2)
     d = (after - before).abs().max().item()
-    assert d < 1e-5 * (before - q).abs().max().item()
+    incr = (before - q).abs().max().item()
+    if dg.dg_blocking(c.h)[1] == 0:
+        assert d == 0.0   # rows of any length: the same arithmetic per node
+    else:
+        # cube blocks form each internal face flux once for both sides: FP32 rounding differs
+        assert d < 1e-4 * incr, (d, incr)
 
 
 # kinetic-energy-preserving split-form volume term (dg_opts.volume_flux = 1)
