@@ -971,6 +971,8 @@ __device__ __forceinline__ int batch_instance(const int* start, int n, int b) {
 template <int P, typename T, int SRC>
 __global__ void __launch_bounds__(max_threads_for(P))
 k_gradient_batch(const __grid_constant__ BatchTable<T> tb) {
+  pdl_wait();
+  pdl_release();
   const int i = batch_instance(tb.block_start, tb.n, blockIdx.x);
   gradient_block<P, T, SRC>(blockIdx.x - tb.block_start[i], tb.q[i], tb.qn32[i], tb.dlt[i], tb.qf[i],
                             SRC == 0 ? tb.qn32[i] : nullptr, tb.vis[i], tb.C[i]);
@@ -979,6 +981,8 @@ k_gradient_batch(const __grid_constant__ BatchTable<T> tb) {
 template <int P, typename T, int MODE>
 __global__ void __launch_bounds__(flux_max_threads(P), min_blocks_for(P, sizeof(T)))
 k_flux_batch(const __grid_constant__ BatchTable<T> tb) {
+  pdl_wait();
+  pdl_release();
   const int i = batch_instance(tb.block_start, tb.n, blockIdx.x);
   flux_block<P, T, MODE>(blockIdx.x - tb.block_start[i], tb.q[i], tb.qf[i], tb.vis[i], nullptr, tb.g[i],
                          tb.dlt[i], Forcing{}, tb.C[i], tb.rk[i]);

@@ -361,10 +361,8 @@ cudaError_t batch_stage_p(const BatchTable<T>& tb, int E, int k, cudaStream_t st
       const size_t ss = sizeof(float) * stream_smem_floats<P>();
       int sgrid = 0;
       if ((e = stream_grid(kf, stream_threads(P), ss, grid, &sgrid)) != cudaSuccess) return e;
-      kg<<<grid, threads, gs, st>>>(tb);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-      kf<<<sgrid, stream_threads(P), ss, st>>>(tb);
-      return cudaGetLastError();
+      if ((e = launch_pdl(kg, dim3(grid), dim3(threads), gs, st, tb)) != cudaSuccess) return e;
+      return launch_pdl(kf, dim3(sgrid), dim3(stream_threads(P)), ss, st, tb);
     }
   }
   void (*kg)(const BatchTable<T>);
@@ -376,10 +374,8 @@ cudaError_t batch_stage_p(const BatchTable<T>& tb, int E, int k, cudaStream_t st
     kg = k_gradient_batch<P, T, 0>;
     kf = k_flux_batch<P, T, 1>;
   }
-  kg<<<grid, threads, gs, st>>>(tb);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  kf<<<grid, flux_threads(P, E), fs, st>>>(tb);
-  return cudaGetLastError();
+  if ((e = launch_pdl(kg, dim3(grid), dim3(threads), gs, st, tb)) != cudaSuccess) return e;
+  return launch_pdl(kf, dim3(grid), dim3(flux_threads(P, E)), fs, st, tb);
 }
 
 // Dynamic shared-memory attributes of the batched kernels of order P at E elements per
