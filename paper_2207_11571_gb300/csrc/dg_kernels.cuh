@@ -995,9 +995,9 @@ k_flux_batch(const __grid_constant__ BatchTable<T> tb) {
 // alternate: the block waits for the own tile and the face halo, then computes with no
 // memory traffic in flight.  The streamed kernel is persistent: each block walks the
 // elements blockIdx.x, blockIdx.x + gridDim.x, ... and, while it computes element k,
-// copies element k + 1's tile and halo into the other half of a double buffer with
-// cp.async (4-byte copies straight to shared memory, no registers held).  The per-node
-// and per-item arithmetic is flux_block's.
+// copies element k + 1's tile (TMA bulk copies, one per component row) and face halo
+// (4-byte cp.async) into the other half of a double buffer, straight to shared memory
+// with no registers held.  The per-node and per-item arithmetic is flux_block's.
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
