@@ -94,7 +94,9 @@ int dg_opts_default(dg_opts* opts);
  * polynomial order P (1 <= P <= 8) on Gauss-Lobatto nodes, for the flow (Re, Mach,
  * Pr) and closure (0: none; 1: Smagorinsky, Sec. 3.1 "LES").  Builds the basis on
  * the host in FP64, uploads it, and allocates the workspace (operator scratch and
- * the RK register).  opts may be NULL (defaults).  1 <= K <= 256. */
+ * the RK register).  opts may be NULL (defaults).  1 <= K <= 256.  DG_ERR_INVALID_ARG
+ * (before any CUDA call) for arguments out of range: Re, Mach, Pr <= 0, gamma <= 1,
+ * Cs < 0, Prt <= 0, a non-finite option, or the block_shape / volume_flux limits above. */
 int dg_create(int K, int P, double Re, double Mach, double Pr, int closure,
               const dg_opts* opts, dg_ctx** out);
 int dg_destroy(dg_ctx* ctx);

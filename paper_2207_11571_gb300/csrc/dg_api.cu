@@ -210,7 +210,10 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
   if (opts) o = *opts;
   if (o.precision != DG_PREC_FP64 && o.precision != DG_PREC_FP32)
     return fail(DG_ERR_INVALID_ARG, "dg_create: unknown precision");
-  if (!(o.gamma > 1.0)) return fail(DG_ERR_INVALID_ARG, "dg_create: gamma must be > 1");
+  if (!(o.gamma > 1.0) || !std::isfinite(o.gamma)) return fail(DG_ERR_INVALID_ARG, "dg_create: gamma must be finite and > 1");
+  if (!(o.Cs >= 0.0) || !std::isfinite(o.Cs)) return fail(DG_ERR_INVALID_ARG, "dg_create: Cs must be finite and >= 0");
+  if (!(o.Prt > 0.0) || !std::isfinite(o.Prt)) return fail(DG_ERR_INVALID_ARG, "dg_create: Prt must be finite and > 0");
+  if (!std::isfinite(o.les_delta)) return fail(DG_ERR_INVALID_ARG, "dg_create: les_delta must be finite");
   if (o.elems_per_block > max_elems_per_block(P))
     return fail(DG_ERR_INVALID_ARG, "dg_create: elems_per_block exceeds the block size limit for this P");
   if (o.block_shape != 0 && o.block_shape != 1) return fail(DG_ERR_INVALID_ARG, "dg_create: block_shape must be 0 or 1");

@@ -51,7 +51,8 @@ def test_opts_defaults(L):
 @pytest.mark.parametrize("bad", [dict(K=0), dict(K=300), dict(P=0), dict(P=9), dict(Re=-1.0),
                                  dict(Mach=0.0), dict(closure=2), dict(block_shape=2),
                                  dict(block_shape=1, K=5), dict(block_shape=1, P=4), dict(volume_flux=2),
-                                 dict(volume_flux=1, block_shape=1)])
+                                 dict(volume_flux=1, block_shape=1), dict(gamma=1.0), dict(gamma=float("inf")),
+                                 dict(Cs=-0.1), dict(Cs=float("nan")), dict(Prt=0.0), dict(les_delta=float("nan"))])
 def test_create_rejects_bad_arguments_before_touching_cuda(L, bad):
     from paper_2207_11571_gb300 import dg
     args = dict(K=4, P=3, Re=1600.0, Mach=0.1, Pr=0.71, closure=0)
