@@ -82,7 +82,9 @@ int nn_forcing_infer(const nn_model* net, const dg_ctx* ctx, const double* q, fl
 /* One optimisation step (Sec. 2.1, "Train corrective forcing"): forward on rows idx[0..batch)
  * of X and Y (idx DEVICE int64, or NULL for rows 0..batch-1), MSE loss against the scaled
  * targets, backward, Adam update of the FP32 weights and refresh of the BF16 copies.
- * hp may be NULL (defaults).  loss_out (HOST, may be NULL) receives the batch loss; when
+ * hp may be NULL (defaults: lr 1e-3, beta1 0.9, beta2 0.999, eps 1e-7); DG_ERR_INVALID_ARG
+ * unless lr >= 0, beta1 and beta2 in [0, 1) and eps > 0, all finite, or batch is outside
+ * [1, max_batch].  loss_out (HOST, may be NULL) receives the batch loss; when
  * given the call synchronises the stream.  Returns DG_ERR_TIMEOUT if a bounded wait in a
  * tensor-core kernel expired. */
 int nn_train_step(nn_model* net, const float* X, const float* Y, const int64_t* idx, int batch,

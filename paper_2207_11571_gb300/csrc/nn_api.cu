@@ -679,6 +679,9 @@ int nn_train_step(nn_model* m, const float* X, const float* Y, const int64_t* id
   if (batch < 1 || batch > m->d.max_batch) return fail(DG_ERR_INVALID_ARG, "nn_train_step: batch outside [1, max_batch]");
   nn_adam a{1e-3f, 0.9f, 0.999f, 1e-7f};
   if (hp) a = *hp;
+  if (!(a.lr >= 0.f) || !std::isfinite(a.lr) || !(a.beta1 >= 0.f && a.beta1 < 1.f) ||
+      !(a.beta2 >= 0.f && a.beta2 < 1.f) || !(a.eps > 0.f) || !std::isfinite(a.eps))
+    return fail(DG_ERR_INVALID_ARG, "nn_train_step: Adam needs lr >= 0, beta1 and beta2 in [0, 1), eps > 0 (finite)");
   cudaStream_t st = (cudaStream_t)stream;
   const int L = m->L, n_out = m->d.n_out;
   // forward, keeping every layer input (bf16) in act[]

@@ -144,6 +144,23 @@ def test_train_step_gradients_loss_and_adam_match_oracle(L):
     nn.nn_destroy(h)
 
 
+@pytest.mark.parametrize("bad", [dict(lr=-1e-3), dict(lr=float("nan")), dict(beta1=1.0), dict(beta2=-0.1),
+                                 dict(eps=0.0), dict(eps=float("inf"))])
+def test_train_step_rejects_bad_adam_hyperparameters(L, bad):
+    """Adam's update divides by sqrt(v) + eps and by 1 - beta^t: out-of-range values are
+    refused before any launch and leave the weights as they were."""
+    from paper_2207_11571_gb300 import nn
+    h, _ = make_net(nn, 64, 64, 1, seed=3, max_batch=128)
+    X = torch.zeros((128, 64), device="cuda")
+    W0, b0 = nn.nn_get_params(h, 0)
+    with pytest.raises(L.DGError) as e:
+        nn.nn_train_step(h, X, X, **bad)
+    assert e.value.status == L.DG_ERR_INVALID_ARG
+    W1, b1 = nn.nn_get_params(h, 0)
+    assert np.array_equal(W0, W1) and np.array_equal(b0, b1)
+    nn.nn_destroy(h)
+
+
 def test_training_follows_oracle_loss_curve(L):
     """Mini-batch Adam training on the GPU (BF16 GEMMs) tracks the FP64 oracle's loss
     curve on the same data, shuffles and initial weights, and cuts the loss > 5x."""
