@@ -15,7 +15,10 @@ and the device time per RK3 step of each operator.
     python -m paper_2207_11571_gb300.precision_run --K 32 --P 3 --t_end 10 --out r.json
 
 --max_seconds bounds the wall time of the time loop; the run then stops at the last
-completed sample time (reported as t_reached).
+completed sample time (reported as t_reached).  A run whose state turns non-finite
+(the standard-form operator on an under-resolved mesh without a closure) stops there:
+diverged_at gives the first sample time at which each diverged run was non-finite, and
+the comparison covers the samples before it.
 """
 import argparse
 import json
@@ -47,17 +50,21 @@ def run(K, P, Re=1600.0, Mach=0.1, Pr=0.71, les=False, cfl=0.7, t_end=10.0, samp
         steps = 0
         hist = {"t": [], "fp32": {"ke": [], "eps": []}, "fp64": {"ke": [], "eps": []}}
 
+        diverged = {}
+
         def record(t):
             hist["t"].append(t)
             for k, c in ctx.items():
-                d = dg.dg_diagnostics(c, q[k])
+                d = dg.dg_diagnostics(c, q[k], raise_nonfinite=False)
+                if d["nonfinite"]:
+                    diverged.setdefault(k, t)
                 hist[k]["ke"].append(d["ke"])
                 hist[k]["eps"].append(-d["dke_dt"])
 
         t = 0.0
         record(t)
         wall0 = time.time()
-        while t < t_end - 1e-12:
+        while t < t_end - 1e-12 and not diverged:
             if max_seconds > 0 and time.time() - wall0 > max_seconds:
                 break
             dt = dg.dg_stable_dt(ctx["fp64"], q["fp64"], cfl)
@@ -82,17 +89,20 @@ def run(K, P, Re=1600.0, Mach=0.1, Pr=0.71, les=False, cfl=0.7, t_end=10.0, samp
         for c in ctx.values():
             dg.dg_destroy(c)
 
-    ke32, ke64 = np.array(hist["fp32"]["ke"]), np.array(hist["fp64"]["ke"])
-    e32, e64 = np.array(hist["fp32"]["eps"]), np.array(hist["fp64"]["eps"])
+    # compare the samples where both runs are finite
+    m = len(hist["t"]) - (1 if diverged else 0)
+    ke32, ke64 = np.array(hist["fp32"]["ke"][:m]), np.array(hist["fp64"]["ke"][:m])
+    e32, e64 = np.array(hist["fp32"]["eps"][:m]), np.array(hist["fp64"]["eps"][:m])
     i32, i64 = int(np.argmax(e32)), int(np.argmax(e64))
     return {
         "mesh": f"{K}^3/P{P}", "nodes": N, "Re": Re, "Mach": Mach, "les": les, "cfl": cfl,
-        "t_end": t_end, "t_reached": hist["t"][-1], "steps": steps, "elems_per_block": tuned,
+        "t_end": t_end, "t_reached": hist["t"][m - 1], "diverged_at": diverged or None, "steps": steps,
+        "elems_per_block": tuned,
         "ke_rel_max": float(np.max(np.abs(ke32 - ke64) / ke64)),
         "dissipation_rel_l2": float(np.linalg.norm(e32 - e64) / np.linalg.norm(e64)),
         "dissipation_rel_max": float(np.max(np.abs(e32 - e64)) / np.max(np.abs(e64))),
         "peak_dissipation": {"fp32": [float(e32[i32]), hist["t"][i32]], "fp64": [float(e64[i64]), hist["t"][i64]]},
-        "momentum_rel_l2_at_end": mom_diff,
+        "momentum_rel_l2_at_end": None if diverged else mom_diff,
         "ms_per_step": {k: (ms[k] / steps if steps else None) for k in ms},
         "history": hist,
     }

@@ -18,6 +18,7 @@ def test_fp32_and_fp64_runs_agree_on_kinetic_energy_and_dissipation():
     # one, while KE moves by ~1e-3 of itself over the run: KE agrees far below 1e-6
     assert r["ke_rel_max"] < 1e-6
     # -dKE/dt is a small residual of the operator (advective work cancels in the
-    # integral): an FP32 rounding of ~1e-5 of |R| is at most ~2e-2 of it
-    assert r["dissipation_rel_l2"] < 2e-2
-    assert r["momentum_rel_l2_at_end"] < 1e-4
+    # integral), so the FP32 rounding of R shows more in it: measured 4.5e-6 on GB300;
+    # the momentum fields after 36 steps: measured 3.2e-8
+    assert r["dissipation_rel_l2"] < 1e-4
+    assert r["momentum_rel_l2_at_end"] < 1e-6
