@@ -171,11 +171,47 @@ def test_rk3_order_on_nonlinear_ode():
 
 # ----------------------------------------------------------------------------- convergence
 
+@pytest.mark.parametrize("P", [1, 2, 3, 4])
+def test_euler_density_wave_converges_at_order_p_plus_one_on_a_slab(P):
+    """The nodal DGSEM of Sec. 2.6 converges at order P + 1 on smooth solutions.  Exact
+    Euler density wave rho = 1 + 0.2 sin(x - t), v = (1, 0, 0), p = const, on a slab of
+    K x 1 x 1 cubic elements of size h = 2 pi / K: the field depends on x only, and the
+    one-element periodic y and z directions give q- = q+ on their faces, so the operator
+    acts exactly as on the K^3 cube (every (ey, ez) column is the same) at 1/K^2 of the
+    cost, which reaches the asymptotic range (K = 32).  RK3 to t = 1 with
+    dt = h / (4 (P+1)); L2 error rates from K = 8 to 16 >= P + 0.5 and from K = 16 to
+    32 >= P + 0.75 (measured 1.80/1.92, 2.93/2.99, 3.87/4.03, 4.80/5.22 for P = 1..4)."""
+    flow = physics.Flow(Mach=0.5, inviscid=True)
+    errs = []
+    for K in (8, 16, 32):
+        mesh = dgsem.Mesh(K, P)
+        n = P + 1
+        x1 = -math.pi + (np.arange(K)[:, None] + 0.5 * (mesh.xi[None, :] + 1.0)) * mesh.h
+        x = np.broadcast_to(x1[None, None, :, None, None, :], (1, 1, K, n, n, n))
+
+        def exact(t):
+            rho = 1.0 + 0.2 * np.sin(x - t)
+            q = np.zeros((5,) + x.shape)
+            q[0] = rho
+            q[1] = rho
+            q[4] = flow.p0 / (flow.gamma - 1.0) + 0.5 * rho
+            return q
+
+        T, nsteps = 1.0, 4 * (P + 1) * K
+        q = exact(0.0)
+        for _ in range(nsteps):
+            q = dgsem.rk3_step(q, T / nsteps, lambda s: dgsem.rhs(s, mesh, flow))
+        err = (q[0] - exact(T)[0])[0, 0, :, 0, 0, :]          # one x-line per element
+        errs.append(math.sqrt((mesh.w[None, :] * (mesh.h / 2.0) * err ** 2).sum() / (2 * math.pi)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[0] > P + 0.5 and rates[1] > P + 0.75, (P, errs, rates)
+
+
 def test_euler_density_wave_converges():
     """Exact Euler solution rho = 1 + 0.2 sin(x + y + z - 3 t), v = (1, 1, 1), p = const
     (no source).  After RK3 to t = 0.2 the L2 error falls with h; on K = 2, 4, 8 the
-    rate is still pre-asymptotic (one-dimensional runs of the same scheme reach
-    P + 1 only from K = 16 on), so the bar is P - 0.5."""
+    rate is still pre-asymptotic (the slab test above reaches P + 1 from K = 16 on), so
+    the bar is P - 0.5."""
     flow = physics.Flow(Mach=0.5, inviscid=True)
     for P in (2, 3):
         errs = []
