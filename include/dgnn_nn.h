@@ -107,7 +107,9 @@ int nn_load(const char* path, int max_batch, nn_model** out);
  * A, B row-major bf16 (DEVICE, leading dimensions lda, ldb multiples of 8 elements,
  * 16-byte aligned), C row-major float (ldc >= N), optional bias[N] and ReLU.  The operands
  * are read in 16-byte chunks: when K is not a multiple of 8, columns K .. roundup(K, 8) - 1
- * of A and B must hold zeros; columns beyond are never read. */
+ * of A and B must hold zeros; columns beyond are never read.  Synchronises the stream and
+ * returns DG_ERR_TIMEOUT if a bounded wait of the kernel expired; the flag it reads is one
+ * per process, so concurrent calls on several streams may see each other's timeout. */
 int nn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int ldb,
                  const float* bias, int relu, float* C, int ldc, void* stream);
 

@@ -813,11 +813,17 @@ int nn_gemm_bf16(int M, int N, int K, const void* A, int lda, const void* B, int
                  float* C, int ldc, void* stream) {
   if (!A || !B || !C) return fail(DG_ERR_INVALID_ARG, "nn_gemm_bf16: NULL argument");
   if (lda < K || ldb < K) return fail(DG_ERR_INVALID_ARG, "nn_gemm_bf16: leading dimension below K");
-  static int* err = nullptr;
-  if (!err) {
-    DG_CUDA(cudaMalloc(&err, sizeof(int)));
-    DG_CUDA(cudaMemset(err, 0, sizeof(int)));
-  }
+  // one error flag for the primitive, allocated once (thread-safe static initialisation)
+  static int* const err = []() -> int* {
+    int* p = nullptr;
+    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) {
+      cudaFree(p);
+      return nullptr;
+    }
+    return p;
+  }();
+  if (!err) return fail(DG_ERR_CUDA, "nn_gemm_bf16: could not allocate the error flag");
   GemmEpilogue ep;
   ep.kind = kGemmF32;
   ep.bias = bias;
