@@ -180,6 +180,53 @@ static int diagnostics_into(dg_ctx* c, const double* q, const double* qref, cons
   return diag_collect(c, with_rhs, qref != nullptr, out, st);
 }
 
+int setup_ctx(dg_ctx* c, int K, int P, double Re, double Mach, double Pr, int closure, const dg_opts& o) {
+  c->K = K;
+  c->P = P;
+  c->n = P + 1;
+  c->np = c->n * c->n * c->n;
+  c->nel = K * K * K;
+  c->N = (long long)c->nel * c->np;
+  c->closure = closure;
+  c->Re = Re;
+  c->Mach = Mach;
+  c->Pr = Pr;
+  c->opts = o;
+  int rc = build_basis(P, &c->basis);
+  if (rc) return rc;
+  const double h = 2.0 * M_PI / K;
+  c->geom.K = K;
+  c->geom.nel = c->nel;
+  c->geom.N = c->N;
+  c->geom.E = o.elems_per_block > 0 ? o.elems_per_block : default_elems_per_block(P);
+  c->geom.cube = o.block_shape;
+  if (c->geom.cube) c->geom.E = kCubeElems;
+  c->geom.split = o.volume_flux;
+  c->geom.two_over_h = 2.0 / h;
+  c->geom.winv = 1.0 / c->basis.w[0];
+  std::memset(c->geom.D, 0, sizeof(c->geom.D));
+  std::memcpy(c->geom.D, c->basis.D, sizeof(double) * c->n * c->n);
+  const double g = o.gamma;
+  c->phys.gamma = g;
+  c->phys.mu = 1.0 / Re;
+  c->phys.lam = c->phys.mu * g / ((g - 1.0) * Pr);
+  c->phys.les = closure;
+  const double delta = o.les_delta > 0 ? o.les_delta : h / (P + 1);
+  c->phys.csd2 = (o.Cs * delta) * (o.Cs * delta);
+  c->phys.lam_t = g / ((g - 1.0) * o.Prt);
+  if (o.precision == DG_PREC_FP32) {
+    // reference state: rho0 = 1 and the background pressure p0 = 1/(gamma M^2)
+    c->phys.rho_ref = 1.0;
+    c->phys.p_ref = 1.0 / (g * Mach * Mach);
+    c->phys.E_ref = c->phys.p_ref / (g - 1.0);
+  } else {
+    c->phys.rho_ref = c->phys.p_ref = c->phys.E_ref = 0.0;
+  }
+  c->phys.Hc = c->phys.E_ref + c->phys.p_ref;
+  c->phys.theta_ref = c->phys.rho_ref > 0 ? c->phys.p_ref / c->phys.rho_ref : 0.0;
+  return DG_OK;
+}
+
 }  // namespace dgnn
 
 using namespace dgnn;
@@ -224,52 +271,11 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
     return fail(DG_ERR_INVALID_ARG, "dg_create: the split-form volume term runs on rows of elements (block_shape 0)");
 
   dg_ctx* c = new dg_ctx();
-  c->K = K;
-  c->P = P;
-  c->n = P + 1;
-  c->np = c->n * c->n * c->n;
-  c->nel = K * K * K;
-  c->N = (long long)c->nel * c->np;
-  c->closure = closure;
-  c->Re = Re;
-  c->Mach = Mach;
-  c->Pr = Pr;
-  c->opts = o;
-  int rc = build_basis(P, &c->basis);
+  int rc = setup_ctx(c, K, P, Re, Mach, Pr, closure, o);
   if (rc) {
     delete c;
     return rc;
   }
-  const double h = 2.0 * M_PI / K;
-  c->geom.K = K;
-  c->geom.nel = c->nel;
-  c->geom.N = c->N;
-  c->geom.E = o.elems_per_block > 0 ? o.elems_per_block : default_elems_per_block(P);
-  c->geom.cube = o.block_shape;
-  if (c->geom.cube) c->geom.E = kCubeElems;
-  c->geom.split = o.volume_flux;
-  c->geom.two_over_h = 2.0 / h;
-  c->geom.winv = 1.0 / c->basis.w[0];
-  std::memset(c->geom.D, 0, sizeof(c->geom.D));
-  std::memcpy(c->geom.D, c->basis.D, sizeof(double) * c->n * c->n);
-  const double g = o.gamma;
-  c->phys.gamma = g;
-  c->phys.mu = 1.0 / Re;
-  c->phys.lam = c->phys.mu * g / ((g - 1.0) * Pr);
-  c->phys.les = closure;
-  const double delta = o.les_delta > 0 ? o.les_delta : h / (P + 1);
-  c->phys.csd2 = (o.Cs * delta) * (o.Cs * delta);
-  c->phys.lam_t = g / ((g - 1.0) * o.Prt);
-  if (o.precision == DG_PREC_FP32) {
-    // reference state: rho0 = 1 and the background pressure p0 = 1/(gamma M^2)
-    c->phys.rho_ref = 1.0;
-    c->phys.p_ref = 1.0 / (g * Mach * Mach);
-    c->phys.E_ref = c->phys.p_ref / (g - 1.0);
-  } else {
-    c->phys.rho_ref = c->phys.p_ref = c->phys.E_ref = 0.0;
-  }
-  c->phys.Hc = c->phys.E_ref + c->phys.p_ref;
-  c->phys.theta_ref = c->phys.rho_ref > 0 ? c->phys.p_ref / c->phys.rho_ref : 0.0;
 
   const bool f32 = o.precision == DG_PREC_FP32;
   if (f32) {

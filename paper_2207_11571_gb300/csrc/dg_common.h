@@ -122,4 +122,9 @@ cudaError_t launch_gradient(const dg_ctx* c, const double* q, int src, cudaStrea
 cudaError_t launch_flux(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode,
                         double rkA, double rkB, double dt, cudaStream_t st);
 
+// Fills the sizes, basis, geometry and physics constants of a context from validated
+// arguments (host only; no device memory is touched).  Shared by dg_create and the
+// no-allocation operator so that both run the kernels with the same constants.
+int setup_ctx(dg_ctx* c, int K, int P, double Re, double Mach, double Pr, int closure, const dg_opts& o);
+
 }  // namespace dgnn

@@ -80,47 +80,12 @@ extern "C" int dg_rhs_noalloc(int K, int P, double Re, double Mach, double Pr, i
   if (precision == DG_PREC_FP32) DG_CUDA(prepare_f32_constants());
 
   // A solver description on the host stack, with its workspace in the scratch array.
+  dg_opts o;
+  dg_opts_default(&o);
+  o.precision = precision;
   dg_ctx c;
-  c.K = K;
-  c.P = P;
-  c.n = P + 1;
-  c.np = c.n * c.n * c.n;
-  c.nel = K * K * K;
-  c.N = nodes;
-  c.closure = closure;
-  c.Re = Re;
-  c.Mach = Mach;
-  c.Pr = Pr;
-  dg_opts_default(&c.opts);
-  c.opts.precision = precision;
-  rc = build_basis(P, &c.basis);
+  rc = setup_ctx(&c, K, P, Re, Mach, Pr, closure, o);
   if (rc) return rc;
-  static const int kDefaultE[9] = {0, 32, 16, 4, 2, 2, 1, 1, 1};
-  const double h = 2.0 * M_PI / K;
-  c.geom.K = K;
-  c.geom.nel = c.nel;
-  c.geom.N = c.N;
-  c.geom.E = kDefaultE[P];
-  c.geom.two_over_h = 2.0 / h;
-  c.geom.winv = 1.0 / c.basis.w[0];
-  for (int i = 0; i < kMaxN1 * kMaxN1; ++i) c.geom.D[i] = i < c.n * c.n ? c.basis.D[i] : 0.0;
-  const double g = c.opts.gamma;
-  c.phys.gamma = g;
-  c.phys.mu = 1.0 / Re;
-  c.phys.lam = c.phys.mu * g / ((g - 1.0) * Pr);
-  c.phys.les = closure;
-  const double delta = h / (P + 1);
-  c.phys.csd2 = (c.opts.Cs * delta) * (c.opts.Cs * delta);
-  c.phys.lam_t = g / ((g - 1.0) * c.opts.Prt);
-  if (precision == DG_PREC_FP32) {
-    c.phys.rho_ref = 1.0;
-    c.phys.p_ref = 1.0 / (g * Mach * Mach);
-    c.phys.E_ref = c.phys.p_ref / (g - 1.0);
-  } else {
-    c.phys.rho_ref = c.phys.p_ref = c.phys.E_ref = 0.0;
-  }
-  c.phys.Hc = c.phys.E_ref + c.phys.p_ref;
-  c.phys.theta_ref = c.phys.rho_ref > 0 ? c.phys.p_ref / c.phys.rho_ref : 0.0;
   // stage state then viscous quantities, in the operator precision
   if (precision == DG_PREC_FP32) {
     float* s = reinterpret_cast<float*>(scratch);
