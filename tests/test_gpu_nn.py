@@ -263,6 +263,31 @@ def test_rhs_and_rk3_with_forcing_match_oracle(L, block_shape):
     dg.dg_destroy(ctx)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_momentum_only_forcing_conserves_mass_and_energy(L, prec):
+    """Sec. 2.2's momentum-only network (s_rho = s_rhoe = 0) inside every RK stage: total
+    mass and energy stay conserved to the operator's own bound (FP64 1e-13, FP32 1e-10,
+    as for the plain operator) while the forcing moves total momentum."""
+    from paper_2207_11571_gb300 import dg, nn
+    K, P = 4, 3
+    ctx = dg.dg_create(K, P, 200.0, 0.1, 0.71, 0, precision=prec)
+    N = K ** 3 * 64
+    q = torch.empty(5 * N, dtype=torch.float64, device="cuda")
+    dg.dg_init_tgv(ctx, q, torch.from_numpy(inputs.perturbation((5, N)).ravel()).cuda())
+    h, _ = make_net(nn, 192, 128, 2, seed=21, max_batch=64, first_var=1, n_vars=3)
+    nn.nn_set_scalers(h, np.zeros(192, np.float32), np.ones(192, np.float32), np.zeros(192, np.float32),
+                      np.full(192, 0.05, np.float32))
+    d0 = dg.dg_diagnostics(ctx, q)
+    dg.dg_rk3_step(ctx, q, 2e-3, 10, h)
+    d1 = dg.dg_diagnostics(ctx, q)
+    tol = 1e-13 if prec == 0 else 1e-10
+    assert abs(d1["mass"] - d0["mass"]) < tol * d0["mass"]
+    assert abs(d1["energy"] - d0["energy"]) < tol * d0["energy"]
+    assert max(abs(a - b) for a, b in zip(d1["momentum"], d0["momentum"])) > 1e-6
+    nn.nn_destroy(h)
+    dg.dg_destroy(ctx)
+
+
 def test_rk3_with_post_step_forcing_matches_oracle(L):
     """Algorithm 1's placement (dg_set_forcing_mode POST), FP64 operator: the uncorrected
     RK3 step, then q += dt s(q^n), against the oracle's corrected_step(mode='post')."""

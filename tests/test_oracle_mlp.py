@@ -129,6 +129,29 @@ def test_exact_forcing_reproduces_filtered_high_order_trajectory():
     np.testing.assert_array_equal(Xm, X[8:16][:, 64:256])
 
 
+@pytest.mark.parametrize("mode", ["stage", "post"])
+def test_momentum_only_forcing_conserves_mass_and_energy(mode):
+    """Sec. 2.2's network acts on the momenta only (s_rho = s_rhoe = 0): the corrected
+    steps keep total mass and energy to round-off, as the operator does, while the
+    forcing moves total momentum."""
+    mesh = dgsem.Mesh(2, 3)
+    flow = physics.Flow(Re=200.0)
+    q = dgsem.tgv_state(mesh, flow, inputs.perturbation((5, 512)))
+    dims = [192, 32, 192]
+    params = mlp.he_uniform_init(dims, inputs.uniform_draws(dims, 9))
+    feats = dgsem.element_features(q, (1, 2, 3))
+    scalers = (feats.mean(0), feats.std(0) + 1.0, np.zeros(192), np.full(192, 0.5))
+    W = mesh.quadrature_weights()
+    total = lambda z: (W * z).sum(axis=(-1, -2, -3, -4, -5, -6))
+    t0 = total(q)
+    z = q
+    for _ in range(3):
+        z = algorithm1.corrected_step(z, 1e-3, mesh, flow, params, scalers, mode=mode, io_vars=(1, 2, 3))
+    t1 = total(z)
+    assert abs(t1[0] - t0[0]) < 1e-13 * t0[0] and abs(t1[4] - t0[4]) < 1e-13 * t0[4]
+    assert np.abs(t1[1:4] - t0[1:4]).max() > 1e-6
+
+
 def test_stage_and_post_forcing_modes_agree_to_second_order():
     """Forcing inside every RK stage vs Algorithm 1's post-step correction: the two
     differ by O(dt^2) per step."""
