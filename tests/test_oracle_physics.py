@@ -100,3 +100,31 @@ def test_viscous_flux_couette_values():
     fy = physics.viscous_flux(q, G, mu, lam, 1)[:, 0]
     np.testing.assert_allclose(fx[1], 4.0 / 3.0 * mu * 1.5, rtol=1e-15)
     np.testing.assert_allclose(fy[2], -2.0 / 3.0 * mu * 1.5, rtol=1e-15)
+
+
+def test_smagorinsky_viscosity_closed_forms():
+    """Sec. 3.1's eddy viscosity mu_t = rho (Cs delta)^2 |S|, |S| = sqrt(2 S_ij S_ij):
+    plain shear du/dy = a gives |S| = |a|; pure rotation (antisymmetric gradient) gives
+    |S| = 0; uniform dilatation du/dx = dv/dy = dw/dz = b gives |S| = sqrt(6) |b|.  The
+    heat coefficient gains mu_t gamma / ((gamma - 1) Pr_t)."""
+    flow = physics.Flow(Re=100.0, les=True, Cs=0.2, Prt=0.9)
+    rho, delta = 1.3, 0.25
+    q = conserved(rho, [0.1, -0.2, 0.3], 1.0)[:, None]
+    c = rho * (flow.Cs * delta) ** 2
+    base_mu = 1.0 / flow.Re
+    base_lam = base_mu * GAMMA / ((GAMMA - 1) * flow.Pr)
+    cases = []
+    G = np.zeros((3, 4, 1))
+    G[1, 0] = -2.5                       # du/dy
+    cases.append((G, 2.5))
+    G = np.zeros((3, 4, 1))
+    G[1, 0], G[0, 1] = 1.7, -1.7         # du/dy = -dv/dx: rigid rotation
+    cases.append((G, 0.0))
+    G = np.zeros((3, 4, 1))
+    G[0, 0] = G[1, 1] = G[2, 2] = 0.4    # uniform dilatation
+    cases.append((G, np.sqrt(6.0) * 0.4))
+    for G, s_norm in cases:
+        mu, lam = physics.transport_coefficients(q, G, flow, delta)
+        mu_t = c * s_norm
+        np.testing.assert_allclose(mu[0], base_mu + mu_t, rtol=1e-14)
+        np.testing.assert_allclose(lam[0], base_lam + mu_t * GAMMA / ((GAMMA - 1) * flow.Prt), rtol=1e-14)
