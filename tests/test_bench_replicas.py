@@ -46,3 +46,24 @@ def test_replicas_barrier_and_max_over_ranks():
     res = sorted(q.get(timeout=10) for _ in range(2))
     assert [r[1] for r in res] == [2.5, 2.5]      # both ranks see the slowest rank's time
     assert [r[2] for r in res] == [0, 0]
+
+
+def test_reference_arm_prints_one_contract_line(capsys):
+    """Rank 0 of `bench.py --impl reference` times the FP64 oracle on the host and prints
+    one JSON line with the keys of the bench contract, the reference tag, a cpu_baseline
+    describing itself and an e2e entry with no host-device traffic."""
+    import argparse
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.run_reference(argparse.Namespace(gpus=1, steps=1, warmup=0), 0, 1) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
