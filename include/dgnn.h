@@ -140,7 +140,9 @@ int dg_rhs_noalloc(int K, int P, double Re, double Mach, double Pr, int closure,
 /* Advances q in place by nsteps low-storage RK3 steps of size dt (Sec. 2, Eq. 6 with
  * the third-order Runge-Kutta scheme of Sec. 3.1; Williamson 2N coefficients).  When
  * forcing != NULL the network forcing s(q_k) is evaluated on every stage state and
- * added to the operator (Eq. 4 integrated by RK3).  q: device, 5 N doubles. */
+ * added to the operator (Eq. 4 integrated by RK3), or, after
+ * dg_set_forcing_mode(ctx, DG_FORCING_POST), added once per step as in Algorithm 1.
+ * q: device, 5 N doubles. */
 int dg_rk3_step(dg_ctx* ctx, double* q, double dt, int nsteps, const nn_model* forcing,
                 void* stream);
 
@@ -248,8 +250,9 @@ int dg_make_pairs(const dg_ctx* lo, const double* q_bar_n, const double* q_nn_np
  * recording CUDA events on `stream` around every kernel launch.  Returns the summed
  * device time in milliseconds of the phase-A (BR1 gradient) and phase-B (flux, lift,
  * RK update) kernels, the number of launches of each, and the algorithmic bytes one
- * phase-B launch moves on average (state, stresses and RK register: each value read
- * or written once).  All outputs are HOST pointers; any may be NULL.  Synchronises. */
+ * launch of each phase moves, averaged over the three RK stages (state, stage state,
+ * stresses and RK increment: each value read or written once; neighbour reads not
+ * counted).  All outputs are HOST pointers; any may be NULL.  Synchronises. */
 int dg_profile_rk3(dg_ctx* ctx, double* q, double dt, int nsteps, double* ms_gradient,
                    double* ms_flux, int* launches_gradient, int* launches_flux,
                    double* flux_bytes_per_launch, double* gradient_bytes_per_launch,
