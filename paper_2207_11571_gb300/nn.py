@@ -90,6 +90,20 @@ def nn_get_desc(net):
     return d
 
 
+def _check_rows(t, width, name, rows=None, dtype="float32"):
+    """A CUDA tensor of ``rows`` rows (its first dimension if None) of ``width`` values
+    of ``dtype``; returns the row count.  The kernels index the rows without bounds of
+    their own, so a wrong size is refused here."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if str(t.dtype).split(".")[-1] != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    r = int(t.shape[0]) if rows is None else int(rows)
+    if t.numel() != r * width:
+        raise ValueError(f"{name} must hold {r} rows of {width} values, got {t.numel()} values")
+    return r
+
+
 def nn_set_scalers(net, mean_in, std_in, mean_out, std_out):
     dg = _dg()
     arrs = [np.ascontiguousarray(a, dtype=np.float32) for a in (mean_in, std_in, mean_out, std_out)]
@@ -106,12 +120,18 @@ def nn_get_scalers(net):
 
 def nn_compute_scalers(net, X, Y, stream=None):
     dg = _dg()
-    dg.check(dg.lib().nn_compute_scalers(_h(net), dg.ptr(X), dg.ptr(Y), int(X.shape[0]), dg.stream_ptr(stream)))
+    d = nn_get_desc(net)
+    rows = _check_rows(X, d.n_in, "X")
+    _check_rows(Y, d.n_out, "Y", rows)
+    dg.check(dg.lib().nn_compute_scalers(_h(net), dg.ptr(X), dg.ptr(Y), rows, dg.stream_ptr(stream)))
 
 
 def nn_forward(net, X, S, stream=None):
     dg = _dg()
-    dg.check(dg.lib().nn_forward(_h(net), dg.ptr(X), dg.ptr(S), int(X.shape[0]), dg.stream_ptr(stream)))
+    d = nn_get_desc(net)
+    rows = _check_rows(X, d.n_in, "X")
+    _check_rows(S, d.n_out, "S", rows)
+    dg.check(dg.lib().nn_forward(_h(net), dg.ptr(X), dg.ptr(S), rows, dg.stream_ptr(stream)))
 
 
 def nn_set_fused(net, enable=True):
@@ -122,14 +142,26 @@ def nn_set_fused(net, enable=True):
 
 def nn_forcing_infer(net, ctx, q, s, stream=None):
     dg = _dg()
+    dg._check_state(ctx, q, "q")
+    _check_rows(s, nn_get_desc(net).n_vars * dg.dg_sizes(ctx)[0], "s", rows=1)
     dg.check(dg.lib().nn_forcing_infer(_h(net), ctypes.c_void_p(ctx), dg.ptr(q), dg.ptr(s), dg.stream_ptr(stream)))
 
 
 def nn_train_step(net, X, Y, idx=None, batch=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-7, want_loss=True,
                   stream=None):
+    """One Adam step on rows idx of (X, Y) (all rows if idx is None).  The values of idx
+    must lie in [0, rows of X): they are not read back to the host to check."""
     dg = _dg()
+    d = nn_get_desc(net)
+    rows = _check_rows(X, d.n_in, "X")
+    _check_rows(Y, d.n_out, "Y", rows)
+    if idx is not None:
+        _check_rows(idx, idx.numel(), "idx", rows=1, dtype="int64")
     if batch is None:
-        batch = int(idx.shape[0]) if idx is not None else int(X.shape[0])
+        batch = int(idx.numel()) if idx is not None else rows
+    if batch > (idx.numel() if idx is not None else rows):
+        raise ValueError(f"batch {batch} exceeds the rows available ({rows} rows of X, idx of "
+                         f"{None if idx is None else idx.numel()})")
     hp = nn_adam(lr, beta1, beta2, eps)
     loss = ctypes.c_float()
     dg.check(dg.lib().nn_train_step(_h(net), dg.ptr(X), dg.ptr(Y), dg.ptr(idx), int(batch), ctypes.byref(hp),

@@ -113,3 +113,28 @@ def test_host_basis_matches_closed_forms_and_oracle(L):
         np.testing.assert_allclose(xi, xo, atol=2e-15)
         np.testing.assert_allclose(w, wo, rtol=1e-13)
         np.testing.assert_allclose(D, basis.lagrange_derivative_matrix(xo), atol=1e-12 * P * P)
+
+
+def test_network_bindings_check_rows_dtype_and_device():
+    """The nn bindings refuse a tensor of the wrong size, dtype or device before the
+    library sees its pointer (the kernels index rows without bounds of their own)."""
+    torch = pytest.importorskip("torch")
+    from paper_2207_11571_gb300 import nn
+
+    class OnDevice:   # a host tensor standing in for a CUDA one (no GPU here)
+        def __init__(self, t):
+            self.t, self.is_cuda, self.dtype, self.shape = t, True, t.dtype, t.shape
+
+        def numel(self):
+            return self.t.numel()
+
+    assert nn._check_rows(OnDevice(torch.zeros(10, 320)), 320, "X") == 10
+    assert nn._check_rows(OnDevice(torch.zeros(7, dtype=torch.int64)), 7, "idx", rows=1, dtype="int64") == 1
+    with pytest.raises(ValueError):
+        nn._check_rows(OnDevice(torch.zeros(10, 321)), 320, "X")
+    with pytest.raises(ValueError):
+        nn._check_rows(OnDevice(torch.zeros(9, 320)), 320, "S", rows=10)
+    with pytest.raises(TypeError):
+        nn._check_rows(OnDevice(torch.zeros(10, 320, dtype=torch.float64)), 320, "X")
+    with pytest.raises(ValueError):
+        nn._check_rows(torch.zeros(10, 320), 320, "X")          # host tensor
