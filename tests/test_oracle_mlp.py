@@ -169,3 +169,28 @@ def test_stage_and_post_forcing_modes_agree_to_second_order():
         b = algorithm1.corrected_step(q, dt, mesh, flow, params, scalers, mode='post')
         diffs.append(np.abs(a - b).max())
     assert diffs[1] < diffs[0] / 3.0 and diffs[1] > 0
+
+
+def test_he_uniform_initialisation_has_variance_two_over_fan_in():
+    """He et al.'s initialisation keeps Var(W) = 2 / fan_in (a uniform law on [-a, a]
+    has variance a^2 / 3); biases start at zero."""
+    dims = [320, 512, 256]
+    params = mlp.he_uniform_init(dims, inputs.uniform_draws(dims, 17))
+    for (W, b), fan_in, fan_out in zip(params, dims[:-1], dims[1:]):
+        assert W.shape == (fan_out, fan_in) and not b.any()
+        # sample variance of fan_in * fan_out >= 131072 draws: within 2 % of 2 / fan_in
+        assert abs(W.var() * fan_in / 2.0 - 1.0) < 0.02
+        assert np.abs(W).max() <= np.sqrt(6.0 / fan_in)
+
+
+def test_scalers_are_population_mean_and_std_with_unit_std_for_constant_features():
+    X = inputs.normal((500, 6), 3) * np.arange(1, 7) + np.arange(6)
+    X[:, 2] = 4.0
+    T = inputs.normal((500, 4), 4)
+    mi, si, mo, so = algorithm1.scalers_from_data(X, T)
+    np.testing.assert_allclose(mi, X.mean(axis=0), rtol=1e-14, atol=1e-14)
+    ref = X.std(axis=0, ddof=0)
+    ref[2] = 1.0
+    np.testing.assert_allclose(si, ref, rtol=1e-13)
+    np.testing.assert_allclose(so, T.std(axis=0, ddof=0), rtol=1e-13)
+    np.testing.assert_allclose(mo, T.mean(axis=0), atol=1e-15)
