@@ -236,10 +236,16 @@ def test_split_form_fp32_error_and_conservation(dg, K, P, les):
 
 
 def record_fp32_error(K, P, les, whole, per_var):
+    """Appends the measured FP32 errors to the JSON-lines file named by DGNN_ERROR_LOG
+    (nothing is written when it is unset)."""
     import json
     import os
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open("gpurun_out/fp32_operator_errors.jsonl", "a") as f:
+    path = os.environ.get("DGNN_ERROR_LOG")
+    if not path:
+        return
+    if os.path.dirname(path):
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+    with open(path, "a") as f:
         f.write(json.dumps({"K": K, "P": P, "les": les, "whole": whole, "per_var": per_var}) + "\n")
 
 
