@@ -24,5 +24,9 @@ Modules
              Eq. 4-6).
 
 Parity pins live in ``tests/test_oracle_*.py``.  Functions without an
-independent pin say "parity unpinned" in their docstring.
+independent pin say "parity unpinned" in their docstring.  Parity unpinned, because
+the paper does not fix them: the closure constants of
+``physics.transport_coefficients`` (filter width h/(P+1) and Pr_t = 0.9; the
+eddy-viscosity formula itself is pinned) and the constant of ``dgsem.stable_dt``
+(its form is pinned by the order ratios printed in Sec. 2.3).
 """
