@@ -8,29 +8,37 @@ import numpy as np
 from . import dgsem, mlp
 
 
-def generate_pairs(q_ho, mesh_ho, mesh_lo, flow_ho, flow_lo, dt_lo, ratio, n_steps, io_vars=(0, 1, 2, 3, 4)):
-    """High-order evolution with pair generation (first loop of Algorithm 1).
+def forcing_target(q_ho_start, q_ho_end, mesh_lo, flow_lo, dt_lo, P_hi):
+    """The corrective forcing the network is trained to produce (Sec. 2.1, Algorithm 1;
+    Eq. 4): the source that, added over one low-order step of length dt_lo, carries the
+    uncorrected low-order solution started from the filtered high-order state onto the
+    filtered high-order state at the end of the step,
 
-    For n = 0 .. n_steps-1:
-      q_NN^n   = G q_HO^n                      (match low order with filtered high order)
-      q_NN^n+1 = RK3_LO(q_NN^n, dt_lo)          (advance without correction)
-      q_HO     advanced ``ratio`` steps of dt_lo/ratio
-      s_n      = (G q_HO^{n+1} - q_NN^{n+1}) / dt_lo
-    Returns (X, T, q_ho_final): per-element inputs G q_HO^n and targets s_n,
-    shapes (n_steps * K^3, len(io_vars) * n_lo^3).
-    """
-    P_hi, P_lo = mesh_ho.P, mesh_lo.P
+        s = (G q_HO(t + dt_lo) - RK3_LO(G q_HO(t), dt_lo)) / dt_lo,
+
+    G the filter of Eq. 2.  Returns (G q_HO(t), s): the network's input and target."""
+    q_in = dgsem.project(q_ho_start, P_hi, mesh_lo.P)
+    q_lo_end = dgsem.rk3_step(q_in, dt_lo, lambda z: dgsem.rhs(z, mesh_lo, flow_lo))
+    return q_in, (dgsem.project(q_ho_end, P_hi, mesh_lo.P) - q_lo_end) / dt_lo
+
+
+def generate_pairs(q_ho, mesh_ho, mesh_lo, flow_ho, flow_lo, dt_lo, ratio, n_steps, io_vars=(0, 1, 2, 3, 4)):
+    """Training pairs over a window of the high-order run (Sec. 2.1, Algorithm 1): the
+    high-order solution advances in ``ratio`` RK3 steps of dt_lo / ratio per low-order
+    step, and every low-order step of the window gives one pair per element, the
+    forcing_target of that step.  Returns (X, T, q_ho_final): per-element inputs and
+    targets, shapes (n_steps * K^3, len(io_vars) * n_lo^3)."""
     dt_ho = dt_lo / ratio
     X, T = [], []
     q = q_ho
     for _ in range(n_steps):
-        q_nn = dgsem.project(q, P_hi, P_lo)
-        q_nn1 = dgsem.rk3_step(q_nn, dt_lo, lambda z: dgsem.rhs(z, mesh_lo, flow_lo))
+        q_next = q
         for _m in range(ratio):
-            q = dgsem.rk3_step(q, dt_ho, lambda z: dgsem.rhs(z, mesh_ho, flow_ho))
-        s = (dgsem.project(q, P_hi, P_lo) - q_nn1) / dt_lo
-        X.append(dgsem.element_features(q_nn, io_vars))
+            q_next = dgsem.rk3_step(q_next, dt_ho, lambda z: dgsem.rhs(z, mesh_ho, flow_ho))
+        q_in, s = forcing_target(q, q_next, mesh_lo, flow_lo, dt_lo, mesh_ho.P)
+        X.append(dgsem.element_features(q_in, io_vars))
         T.append(dgsem.element_features(s, io_vars))
+        q = q_next
     return np.concatenate(X), np.concatenate(T), q
 
 

@@ -100,7 +100,11 @@ def stable_dt(ctx, q, cfl):
 
 
 def generate_pairs(args, ctx_hi, q_hi, ctx_lo, dt_lo, ratio, n_steps, first_var, n_vars):
-    """Algorithm 1, first loop: returns device tensors X, Y (n_steps K^3 rows)."""
+    """Training pairs of Algorithm 1 (Sec. 2.1): per low-order step of the window, the
+    input is the filtered high-order state at the step start and the target the forcing
+    that carries the uncorrected low-order step from there onto the filtered high-order
+    state at the step end, divided by the step.  Returns device tensors X, Y (n_steps K^3
+    rows)."""
     nodes_lo, elems = dg.dg_sizes(ctx_lo)
     feat = n_vars * (args.P_lo + 1) ** 3
     X = torch.empty((n_steps * elems, feat), dtype=torch.float32, device="cuda")
@@ -110,11 +114,11 @@ def generate_pairs(args, ctx_hi, q_hi, ctx_lo, dt_lo, ratio, n_steps, first_var,
     qbar1 = new_state(ctx_lo)
     dt_hi = dt_lo / ratio
     for n in range(n_steps):
-        dg.dg_project(ctx_hi, ctx_lo, q_hi, qbar)                 # q_NN^n = G q_HO^n
+        dg.dg_project(ctx_hi, ctx_lo, q_hi, qbar)                 # filtered state, step start
         qnn.copy_(qbar)
-        dg.dg_rk3_step(ctx_lo, qnn, dt_lo, 1)                     # uncorrected LO step
-        dg.dg_rk3_step(ctx_hi, q_hi, dt_hi, ratio)               # HO steps over dt_lo
-        dg.dg_project(ctx_hi, ctx_lo, q_hi, qbar1)                # G q_HO^{n+1}
+        dg.dg_rk3_step(ctx_lo, qnn, dt_lo, 1)                     # low order, no forcing
+        dg.dg_rk3_step(ctx_hi, q_hi, dt_hi, ratio)               # high order over the same dt
+        dg.dg_project(ctx_hi, ctx_lo, q_hi, qbar1)                # filtered state, step end
         dg.dg_make_pairs(ctx_lo, qbar, qnn, qbar1, dt_lo, first_var, n_vars,
                          X[n * elems:(n + 1) * elems], Y[n * elems:(n + 1) * elems])
     return X, Y

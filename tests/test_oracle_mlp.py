@@ -58,6 +58,31 @@ def test_backward_matches_central_finite_differences():
                 assert abs(fd - an) <= 1e-7 * max(1e-3, abs(fd)), (l, which, idx, fd, an)
 
 
+def test_mse_loss_closed_form_on_a_two_by_three_example():
+    """Sec. 2.2 trains on the mean squared error: the mean over the batch and the outputs.
+    On y - t = [[1, -2, 0], [3, 0, -1]] the sum of squares is 15 over 6 entries, so
+    L = 2.5 and dL/dy = 2 (y - t) / 6."""
+    y = np.array([[1.0, -1.0, 2.0], [3.5, 0.25, 0.0]])
+    t = np.array([[0.0, 1.0, 2.0], [0.5, 0.25, 1.0]])
+    L, dy = mlp.mse_loss(y, t)
+    assert L == 2.5
+    np.testing.assert_array_equal(dy, np.array([[1.0, -2.0, 0.0], [3.0, 0.0, -1.0]]) / 3.0)
+
+
+def test_mse_loss_and_gradient_match_torch():
+    """The normalisation (batch x outputs) equals torch's mean-reduced MSE, and the
+    gradient equals autograd's."""
+    torch = pytest.importorskip("torch")
+    y = inputs.normal((17, 5), 11)
+    t = inputs.normal((17, 5), 12)
+    L, dy = mlp.mse_loss(y, t)
+    yt = torch.tensor(y, requires_grad=True)
+    Lt = torch.nn.functional.mse_loss(yt, torch.tensor(t), reduction="mean")
+    Lt.backward()
+    assert L == pytest.approx(Lt.item(), rel=1e-15)
+    np.testing.assert_allclose(dy, yt.grad.numpy(), rtol=1e-14, atol=0)
+
+
 def test_adam_constant_gradient_closed_form():
     """With a constant gradient g, bias correction makes m_hat = g and v_hat = g^2 exactly,
     so every step moves each weight by -lr g / (|g| + eps) (Kingma & Ba)."""
