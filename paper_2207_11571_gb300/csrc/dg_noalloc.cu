@@ -2,11 +2,11 @@
 //
 // Who needs it: code that calls the operator from a place where cudaMalloc is not
 // allowed or not wanted -- an in-situ analysis hook inside another solver's time loop
-// whose device memory was budgeted and locked at start-up, a host thread that must not
-// take the allocator's locks, or work recorded into a CUDA stream capture, where
-// allocation calls are illegal.  dg_create allocates its workspace (stage state and
-// viscous stresses, ~112 bytes per node in FP64); this entry point instead uses one
-// fixed scratch array that lives in the library's own device image.
+// whose device memory was budgeted and locked at start-up, or a host thread that must
+// not take the allocator's locks or synchronise the device (cudaMalloc and cudaFree may
+// do both).  dg_create allocates its workspace (stage state and viscous stresses, ~112
+// bytes per node in FP64); this entry point instead uses one fixed scratch array that
+// lives in the library's own device image.
 //
 // The scratch array holds the two intermediate fields of one operator evaluation: the
 // stage state (5 values per node) and the viscous stresses and heat flux (9 values per
@@ -18,8 +18,11 @@
 //
 // In host code the array's name is only a host-side stand-in; its device address comes
 // from cudaGetSymbolAddress, taken once per device (with that device current) on the
-// first call made while it is current.  That first call should therefore happen before
-// any stream capture that records later calls.
+// first call made while it is current.  The same first call uploads the FP32 kernels'
+// constant tables for that device (synchronous copies), whatever precision it asks for,
+// so later calls of either precision enqueue kernels only.  Make that first call before
+// any stream capture.  The cached address belongs to the device's context: after
+// cudaDeviceReset the library must not be called again in the process.
 #include <mutex>
 
 #include "dg_aux.h"
@@ -37,7 +40,8 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
 std::mutex g_noalloc_mu;
 double* g_noalloc_addr[kNoallocMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once per device).
+// Device address of the scratch array on the current device (looked up once per device,
+// together with the upload of the FP32 constant tables).
 int noalloc_scratch(double** out) {
   int dev = 0;
   DG_CUDA(cudaGetDevice(&dev));
@@ -47,6 +51,10 @@ int noalloc_scratch(double** out) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "dg_rhs_noalloc: cudaGetSymbolAddress of the scratch array");
+    // FP32 derivative tables in constant memory: uploaded here, at set-up, for both
+    // precisions, so that no later call issues a synchronous copy
+    e = prepare_f32_constants();
+    if (e != cudaSuccess) return cuda_fail(e, "dg_rhs_noalloc: constant tables");
     g_noalloc_addr[dev] = static_cast<double*>(p);
   }
   *out = g_noalloc_addr[dev];
@@ -77,7 +85,6 @@ extern "C" int dg_rhs_noalloc(int K, int P, double Re, double Mach, double Pr, i
   double* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
   if (rc) return rc;
-  if (precision == DG_PREC_FP32) DG_CUDA(prepare_f32_constants());
 
   // A solver description on the host stack, with its workspace in the scratch array.
   dg_opts o;
