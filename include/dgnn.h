@@ -28,6 +28,7 @@
 #ifndef DGNN_H
 #define DGNN_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -41,7 +42,8 @@ typedef enum {
   DG_ERR_NONFINITE = -3,   /* a diagnostic found NaN/Inf in the state */
   DG_ERR_TIMEOUT = -4,     /* a bounded device-side wait ran out (error flag set, kernel returned) */
   DG_ERR_IO = -5,          /* file missing, truncated or with a bad checksum */
-  DG_ERR_UNSUPPORTED = -6  /* a parameter combination this build does not implement */
+  DG_ERR_UNSUPPORTED = -6, /* a parameter combination this build does not implement */
+  DG_ERR_EXCHANGE = -7     /* a slab's exchange function reported a failure */
 } dg_status;
 
 typedef struct dg_ctx dg_ctx;
@@ -125,15 +127,20 @@ int dg_rhs(dg_ctx* ctx, const double* q, double* dqdt, const nn_model* forcing, 
 /* dqdt = p(q) like dg_rhs, without any device allocation and without a context (the
  * paper has no counterpart: this is a service for callers that may not allocate device
  * memory, e.g. an in-situ hook inside another code's time loop whose device memory is
- * fixed at start-up, or work recorded into a CUDA stream capture, where allocation calls
- * are not allowed).  The mesh and flow are given as in dg_create (default dg_opts apart
- * from precision, no forcing).  q, dqdt: DEVICE, 5 N doubles, N = K^3 (P+1)^3.
+ * fixed at start-up, or a host thread that must not take the allocator's locks or
+ * synchronise the device, as cudaMalloc and cudaFree may).  The mesh and flow are given
+ * as in dg_create (default dg_opts apart from precision, no forcing).  q, dqdt: DEVICE,
+ * 5 N doubles, N = K^3 (P+1)^3.
  * The two intermediate fields of the operator live in one scratch array inside the
  * library's device image (3.7 MB, kept by every GPU that loads the library until exit):
  * N may be at most 32768 nodes, larger meshes return DG_ERR_INVALID_ARG.  The first call
- * on a device (with that device current) looks up the array's device address; make it
- * before any stream capture.  All calls share the array: calls that overlap on the GPU
- * (other streams or host threads) race and must be serialised by the caller. */
+ * on a device (with that device current) does the set-up: it looks up the array's device
+ * address and uploads the FP32 kernels' constant tables (synchronous copies, whatever the
+ * precision asked for); make it before any stream capture.  Later calls only enqueue
+ * kernels on stream.  The looked-up address belongs to the device's context: after
+ * cudaDeviceReset no further call may be made.  All calls share the array and it keeps
+ * the last call's contents: calls that overlap on the GPU (other streams or host
+ * threads) race and must be serialised by the caller. */
 int dg_rhs_noalloc(int K, int P, double Re, double Mach, double Pr, int closure, int precision,
                    const double* q, double* dqdt, void* stream);
 
@@ -295,6 +302,71 @@ int dg_check_conversions(const double* x, int64_t n, int64_t* mismatches, void* 
  * elapsed time in *seconds (HOST, may be NULL); DG_ERR_CUDA if a wait reported success
  * without arrivals or on a CUDA error.  Synchronises the stream. */
 int dg_check_bounded_waits(double* seconds, void* stream);
+
+/* ---- Element-layer domain decomposition.  The paper runs its solver in parallel over
+ * MPI ranks (Sec. 2.6, implementation details); here the periodic K^3 mesh is split into
+ * slabs of whole element layers along z, one per GPU or rank, and each RK stage exchanges
+ * the face traces of the slabs' boundary layers twice: the stage state before the BR1
+ * gradient phase, the stage state and z-normal viscous fluxes before the flux phase (the
+ * interface fluxes of Sec. 3.1 read both sides of a face).  Diagnostics reduce per slab
+ * and are combined by dg_diag_combine (a fixed-order FP64 sum; the caller gathers the
+ * slabs' dg_diag structs across ranks). ---- */
+
+/* Exchange of one slab's traces, called by the library during dg_rhs, dg_rk3_step,
+ * dg_diagnostics and dg_advance_host(_async) on a slab context, once per exchange point,
+ * after the pack kernels are enqueued on stream.  send_lo holds the first owned layer's
+ * lower-face traces (for the slab below), send_hi the last owned layer's upper-face traces
+ * (for the slab above); the function must arrange, in the order of `stream`, that recv_lo
+ * receives the lower neighbour's send_hi and recv_hi the upper neighbour's send_lo (the
+ * mesh is periodic: slab 0's lower neighbour is the last slab), before the library's unpack
+ * kernels that it enqueues on stream after the function returns.  bytes: the size of each
+ * of the four DEVICE buffers' contents for this exchange (what: 0 FP64 state, 1 FP32 stage
+ * state, 2 stage state and viscous fluxes).  Returns 0, or nonzero for a failure (the
+ * library call then returns DG_ERR_EXCHANGE). */
+typedef int (*dg_exchange_fn)(void* user, int what, const void* send_lo, const void* send_hi, void* recv_lo,
+                              void* recv_hi, size_t bytes, void* stream);
+
+/* Creates the slab of element layers [z_begin, z_begin + z_count) (0 <= z_begin,
+ * 1 <= z_count, z_begin + z_count <= K) of the periodic K^3 mesh, with the arguments of
+ * dg_create (rows of elements only: block_shape 1 returns DG_ERR_INVALID_ARG).  Its local
+ * arrays hold z_count + 2 element layers: local layer 0 is global layer z_begin - 1 (mod K)
+ * and local layer z_count + 1 is global layer z_begin + z_count (mod K), the ghost layers
+ * whose face traces the exchange fills; local layers 1 .. z_count are the slab's own.
+ * Layout of the local state as for q (dg_sizes returns the local counts), element
+ * ex + K (ey + K lz).  dg_init_tgv fills every local layer from the global coordinates.
+ * The network forcing is not offered on a slab (DG_ERR_UNSUPPORTED). */
+int dg_create_part(int K, int P, double Re, double Mach, double Pr, int closure, const dg_opts* opts,
+                   int z_begin, int z_count, dg_ctx** out);
+
+/* The slab's global layers and its owned nodes in the local arrays: the owned nodes are
+ * [first_owned_node, first_owned_node + owned_nodes) of each variable's row (a whole-mesh
+ * context reports 0, K, 0, N).  HOST pointers, any may be NULL. */
+int dg_part_layout(const dg_ctx* ctx, int* z_begin, int* z_count, int64_t* first_owned_node,
+                   int64_t* owned_nodes);
+
+/* Sets the exchange function of a slab (fn NULL: none; a slab without one can evaluate
+ * the operator only if it spans the whole mesh, z_count = K, when it is its own
+ * neighbour).  user is passed through. */
+int dg_part_set_exchange(dg_ctx* ctx, dg_exchange_fn fn, void* user);
+
+/* Bytes of one side's traces for exchange `what` (0, 1, 2; see dg_exchange_fn).  HOST. */
+int dg_part_trace_bytes(const dg_ctx* ctx, int what, size_t* bytes);
+
+/* The slabs of one mesh on the current device, advanced together: parts[0..n) are the
+ * slabs in layer order covering 0 .. K-1 (same mesh, order, flow and precision), q[i]
+ * (HOST array of DEVICE pointers) slab i's local state.  The traces move between the
+ * slabs' buffers by device copies on stream.  dg_group_rk3_step: nsteps RK3 steps as
+ * dg_rk3_step; dg_group_rhs: dqdt[i] = p(q)[i] (owned layers written); dg_group_diagnostics:
+ * the diagnostics of the whole mesh (HOST out) from the slabs' owned nodes. */
+int dg_group_rk3_step(dg_ctx* const* parts, int n, double* const* q, double dt, int nsteps, void* stream);
+int dg_group_rhs(dg_ctx* const* parts, int n, double* const* q, double* const* dqdt, void* stream);
+int dg_group_diagnostics(dg_ctx* const* parts, int n, double* const* q, dg_diag* out, void* stream);
+
+/* Combines the diagnostics of the n slabs of one mesh (HOST arrays): sums in slab order,
+ * maxima of e_inf and max_wave.  On a slab, dg_diagnostics and dg_stable_dt see only its
+ * own nodes: the mesh's diagnostics are the combination of all slabs', and its stable
+ * step the minimum of the slabs' (dt from the combined max_wave). */
+int dg_diag_combine(const dg_diag* parts, int n, dg_diag* out);
 
 const char* dg_last_error(void);
 

@@ -97,40 +97,96 @@ static int forcing_for(dg_ctx* c, const double* q, const nn_model* net, Forcing*
   return DG_OK;
 }
 
-static int rhs_into(dg_ctx* c, const double* q, double* out, const nn_model* net, cudaStream_t st) {
-  DG_CUDA(launch_gradient(c, q, 0, st));
-  Forcing f;
-  int rc = forcing_for(c, q, net, &f, st);
-  if (rc) return rc;
-  DG_CUDA(launch_flux(c, const_cast<double*>(q), out, f, 0, 0.0, 0.0, 0.0, st));
+// Trace exchange of slabs before a phase (what: see launch_trace_pack): every part packs
+// its owned boundary faces; a group of slabs of one mesh on this device moves them by
+// device copies between neighbours (a single slab that spans the mesh: onto itself); a
+// single slab with an exchange function hands its buffers to that function; every part
+// then unpacks into its ghost layers.  Whole-mesh contexts exchange nothing.
+static int exchange_traces(dg_ctx* const* cs, int n, double* const* qs, int what, cudaStream_t st) {
+  if (!cs[0]->part) return DG_OK;
+  for (int i = 0; i < n; ++i) DG_CUDA(launch_trace_pack(cs[i], qs[i], what, cs[i]->trace[0], cs[i]->trace[1], st));
+  const size_t bytes = trace_bytes_for(cs[0], what);
+  if (n == 1 && cs[0]->xfn) {
+    const int rc = cs[0]->xfn(cs[0]->xuser, what, cs[0]->trace[0], cs[0]->trace[1], cs[0]->trace[2],
+                              cs[0]->trace[3], bytes, (void*)st);
+    if (rc != 0) return fail(DG_ERR_EXCHANGE, "the slab's exchange function returned " + std::to_string(rc));
+  } else {
+    for (int i = 0; i < n; ++i) {
+      const dg_ctx* lower = cs[(i + n - 1) % n];
+      const dg_ctx* upper = cs[(i + 1) % n];
+      DG_CUDA(cudaMemcpyAsync(cs[i]->trace[2], lower->trace[1], bytes, cudaMemcpyDeviceToDevice, st));
+      DG_CUDA(cudaMemcpyAsync(cs[i]->trace[3], upper->trace[0], bytes, cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    DG_CUDA(launch_trace_unpack(cs[i], qs[i], what, cs[i]->trace[2], cs[i]->trace[3], st));
   return DG_OK;
+}
+
+// Phase-A trace of stage state source src (0: the FP64 state; 1: the FP32 increment scheme).
+static int phase_a_what(const dg_ctx* c, int src) { return (c->opts.precision == DG_PREC_FP32 && src == 1) ? 1 : 0; }
+constexpr int kWhatPhaseB = 2;
+
+// dq/dt of n contexts: one whole mesh, or the slabs of one mesh exchanging traces.
+static int rhs_into_n(dg_ctx* const* cs, int n, double* const* qs, double* const* outs, const nn_model* net,
+                      cudaStream_t st) {
+  int rc = exchange_traces(cs, n, qs, phase_a_what(cs[0], 0), st);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) DG_CUDA(launch_gradient(cs[i], qs[i], 0, st));
+  Forcing f;
+  if (n == 1) {
+    rc = forcing_for(cs[0], qs[0], net, &f, st);
+    if (rc) return rc;
+  }
+  rc = exchange_traces(cs, n, qs, kWhatPhaseB, st);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) DG_CUDA(launch_flux(cs[i], qs[i], outs[i], f, 0, 0.0, 0.0, 0.0, st));
+  return DG_OK;
+}
+
+static int rhs_into(dg_ctx* c, const double* q, double* out, const nn_model* net, cudaStream_t st) {
+  double* qq = const_cast<double*>(q);
+  return rhs_into_n(&c, 1, &qq, &out, net, st);
 }
 
 // With a network forcing: DG_FORCING_STAGE adds s(q_k) to the operator in every stage
 // (Eq. 4 integrated by RK3); DG_FORCING_POST evaluates s once on q^n (the stage-1 state),
-// takes the uncorrected step and adds dt s(q^n) (Algorithm 1, third loop).
-static int rk3_steps(dg_ctx* c, double* q, double dt, int nsteps, const nn_model* net, cudaStream_t st) {
+// takes the uncorrected step and adds dt s(q^n) (Algorithm 1, third loop).  n > 1: the
+// slabs of one mesh advanced in lockstep (no forcing).  exchange = false (the autotuner's
+// timing on a scratch state) skips the slabs' trace exchange.
+static int rk3_steps_n(dg_ctx* const* cs, int n, double* const* qs, double dt, int nsteps, const nn_model* net,
+                       cudaStream_t st, bool exchange = true) {
+  dg_ctx* c = cs[0];
   const bool post = net && c->forcing_mode == DG_FORCING_POST;
   for (int s = 0; s < nsteps; ++s) {
     Forcing fpost;
     for (int k = 0; k < 3; ++k) {
       int src, mode;
       stage_plan(c, k, &src, &mode);
-      DG_CUDA(launch_gradient(c, q, src, st));
+      int rc = exchange ? exchange_traces(cs, n, qs, phase_a_what(c, src), st) : DG_OK;
+      if (rc) return rc;
+      for (int i = 0; i < n; ++i) DG_CUDA(launch_gradient(cs[i], qs[i], src, st));
       Forcing f;
       if (!post || k == 0) {
-        int rc = forcing_for(c, q, net, &f, st);
+        rc = forcing_for(c, qs[0], net, &f, st);
         if (rc) return rc;
       }
       if (post) {
         if (k == 0) fpost = f;
         f = Forcing{};
       }
-      DG_CUDA(launch_flux(c, q, nullptr, f, mode, kRkA[k], kRkB[k], dt, st));
+      rc = exchange ? exchange_traces(cs, n, qs, kWhatPhaseB, st) : DG_OK;
+      if (rc) return rc;
+      for (int i = 0; i < n; ++i) DG_CUDA(launch_flux(cs[i], qs[i], nullptr, f, mode, kRkA[k], kRkB[k], dt, st));
     }
-    if (post) DG_CUDA(launch_add_forcing(c, q, fpost, dt, st));
+    if (post) DG_CUDA(launch_add_forcing(c, qs[0], fpost, dt, st));
   }
   return DG_OK;
+}
+
+static int rk3_steps(dg_ctx* c, double* q, double dt, int nsteps, const nn_model* net, cudaStream_t st,
+                     bool exchange = true) {
+  return rk3_steps_n(&c, 1, &q, dt, nsteps, net, st, exchange);
 }
 
 // Diagnostics in two parts: the reductions and the copy of their result into the
@@ -187,6 +243,9 @@ int setup_ctx(dg_ctx* c, int K, int P, double Re, double Mach, double Pr, int cl
   c->np = c->n * c->n * c->n;
   c->nel = K * K * K;
   c->N = (long long)c->nel * c->np;
+  c->Kz = K;
+  c->e_begin = 0;
+  c->e_end = c->nel;
   c->closure = closure;
   c->Re = Re;
   c->Mach = Mach;
@@ -227,11 +286,164 @@ int setup_ctx(dg_ctx* c, int K, int P, double Re, double Mach, double Pr, int cl
   return DG_OK;
 }
 
+// A slab evaluates the operator only with its neighbours' traces: it needs an exchange
+// function unless it spans the whole mesh (its own lower and upper faces are then its
+// neighbours').  The network forcing is not offered on slabs.
+static int part_usable(const dg_ctx* c, const nn_model* net, const char* who) {
+  if (!c->part) return DG_OK;
+  if (net) return fail(DG_ERR_UNSUPPORTED, std::string(who) + ": no network forcing on a slab (dg_create_part)");
+  if (!c->xfn && c->z_count < c->K)
+    return fail(DG_ERR_INVALID_ARG, std::string(who) + ": a slab needs an exchange function (dg_part_set_exchange) "
+                                                       "or a group call (dg_group_*)");
+  return DG_OK;
+}
+
+// The parts of a group call must be the slabs of one mesh in order: same mesh, order,
+// flow and precision, consecutive layers covering 0 .. K-1, states given for each.
+static int check_group(dg_ctx* const* parts, int n, double* const* q, const char* who) {
+  if (!parts || !q || n < 1) return fail(DG_ERR_INVALID_ARG, std::string(who) + ": NULL argument or n < 1");
+  int z = 0;
+  for (int i = 0; i < n; ++i) {
+    const dg_ctx* c = parts[i];
+    if (!c || !q[i]) return fail(DG_ERR_INVALID_ARG, std::string(who) + ": NULL part or state");
+    if (!c->part) return fail(DG_ERR_INVALID_ARG, std::string(who) + ": part " + std::to_string(i) + " is not a slab");
+    const dg_ctx* a = parts[0];
+    if (c->K != a->K || c->P != a->P || c->Re != a->Re || c->Mach != a->Mach || c->Pr != a->Pr ||
+        c->closure != a->closure || c->opts.precision != a->opts.precision || c->geom.split != a->geom.split)
+      return fail(DG_ERR_INVALID_ARG, std::string(who) + ": parts of different meshes, orders, flows or precisions");
+    if (c->z_begin != z)
+      return fail(DG_ERR_INVALID_ARG, std::string(who) + ": part " + std::to_string(i) + " does not start at layer " +
+                                          std::to_string(z));
+    z += c->z_count;
+  }
+  if (z != parts[0]->K) return fail(DG_ERR_INVALID_ARG, std::string(who) + ": the parts do not cover the K layers");
+  return DG_OK;
+}
+
 }  // namespace dgnn
 
 using namespace dgnn;
 
 extern "C" {
+
+int dg_create_part(int K, int P, double Re, double Mach, double Pr, int closure, const dg_opts* opts, int z_begin,
+                   int z_count, dg_ctx** out) {
+  if (!out) return fail(DG_ERR_INVALID_ARG, "dg_create_part: out is NULL");
+  *out = nullptr;
+  if (K < 1 || K > 256) return fail(DG_ERR_INVALID_ARG, "dg_create_part: K must be in [1, 256]");
+  if (z_begin < 0 || z_count < 1 || z_begin + z_count > K)
+    return fail(DG_ERR_INVALID_ARG, "dg_create_part: layers [z_begin, z_begin + z_count) must lie in [0, K)");
+  dg_opts o;
+  dg_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.block_shape != 0) return fail(DG_ERR_INVALID_ARG, "dg_create_part: slabs run rows of elements (block_shape 0)");
+  // a whole-mesh context for the slab's local array of z_count + 2 layers: same checks,
+  // basis and constants; its element and node counts are then the local ones
+  dg_ctx* c = nullptr;
+  int rc = dg_create_local(K, P, Re, Mach, Pr, closure, &o, z_count + 2, &c);
+  if (rc) return rc;
+  c->part = 1;
+  c->z_begin = z_begin;
+  c->z_count = z_count;
+  c->e_begin = K * K;
+  c->e_end = K * K * (z_count + 1);
+  size_t tb = 0;
+  for (int w = 0; w < 3; ++w) tb = std::max(tb, trace_bytes_for(c, w));
+  c->trace_bytes = tb;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMalloc(&c->trace[i], tb);
+  // the ghost layers' FP32 increment stays zero: their stage state arrives whole in qn32
+  if (e == cudaSuccess && c->dlt) e = cudaMemset(c->dlt, 0, 5 * c->N * sizeof(float));
+  if (e != cudaSuccess) {
+    dg_destroy(c);
+    return cuda_fail(e, "dg_create_part: trace buffers");
+  }
+  *out = c;
+  return DG_OK;
+}
+
+int dg_part_layout(const dg_ctx* c, int* z_begin, int* z_count, int64_t* first_owned_node, int64_t* owned_nodes) {
+  if (!c) return fail(DG_ERR_INVALID_ARG, "dg_part_layout: NULL context");
+  if (z_begin) *z_begin = c->part ? c->z_begin : 0;
+  if (z_count) *z_count = c->part ? c->z_count : c->K;
+  if (first_owned_node) *first_owned_node = (int64_t)c->e_begin * c->np;
+  if (owned_nodes) *owned_nodes = (int64_t)(c->e_end - c->e_begin) * c->np;
+  return DG_OK;
+}
+
+int dg_part_set_exchange(dg_ctx* c, dg_exchange_fn fn, void* user) {
+  if (!c) return fail(DG_ERR_INVALID_ARG, "dg_part_set_exchange: NULL context");
+  if (!c->part) return fail(DG_ERR_INVALID_ARG, "dg_part_set_exchange: not a slab (dg_create_part)");
+  c->xfn = fn;
+  c->xuser = user;
+  return DG_OK;
+}
+
+int dg_part_trace_bytes(const dg_ctx* c, int what, size_t* bytes) {
+  if (!c || !bytes) return fail(DG_ERR_INVALID_ARG, "dg_part_trace_bytes: NULL argument");
+  if (!c->part) return fail(DG_ERR_INVALID_ARG, "dg_part_trace_bytes: not a slab (dg_create_part)");
+  if (what < 0 || what > 2) return fail(DG_ERR_INVALID_ARG, "dg_part_trace_bytes: what must be 0, 1 or 2");
+  *bytes = trace_bytes_for(c, what);
+  return DG_OK;
+}
+
+int dg_group_rk3_step(dg_ctx* const* parts, int n, double* const* q, double dt, int nsteps, void* stream) {
+  int rc = check_group(parts, n, q, "dg_group_rk3_step");
+  if (rc) return rc;
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_group_rk3_step: bad nsteps or dt");
+  return rk3_steps_n(parts, n, q, dt, nsteps, nullptr, (cudaStream_t)stream);
+}
+
+int dg_group_rhs(dg_ctx* const* parts, int n, double* const* q, double* const* dqdt, void* stream) {
+  int rc = check_group(parts, n, q, "dg_group_rhs");
+  if (rc) return rc;
+  if (!dqdt) return fail(DG_ERR_INVALID_ARG, "dg_group_rhs: NULL dqdt");
+  for (int i = 0; i < n; ++i)
+    if (!dqdt[i] || dqdt[i] == q[i]) return fail(DG_ERR_INVALID_ARG, "dg_group_rhs: NULL or aliasing dqdt");
+  return rhs_into_n(parts, n, q, dqdt, nullptr, (cudaStream_t)stream);
+}
+
+int dg_diag_combine(const dg_diag* parts, int n, dg_diag* out) {
+  if (!parts || !out || n < 1) return fail(DG_ERR_INVALID_ARG, "dg_diag_combine: NULL argument or n < 1");
+  dg_diag r = parts[0];
+  for (int i = 1; i < n; ++i) {   // in part order: the same sums on every rank
+    const dg_diag& p = parts[i];
+    r.mass += p.mass;
+    for (int k = 0; k < 3; ++k) r.momentum[k] += p.momentum[k];
+    r.energy += p.energy;
+    r.ke += p.ke;
+    r.dke_dt += p.dke_dt;
+    for (int k = 0; k < 3; ++k) r.e_inf[k] = std::max(r.e_inf[k], p.e_inf[k]);
+    r.max_wave = std::max(r.max_wave, p.max_wave);
+    r.nonfinite += p.nonfinite;
+  }
+  *out = r;
+  return r.nonfinite ? fail(DG_ERR_NONFINITE, "state holds non-finite values") : DG_OK;
+}
+
+int dg_group_diagnostics(dg_ctx* const* parts, int n, double* const* q, dg_diag* out, void* stream) {
+  int rc = check_group(parts, n, q, "dg_group_diagnostics");
+  if (rc) return rc;
+  if (!out) return fail(DG_ERR_INVALID_ARG, "dg_group_diagnostics: NULL out");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<double*> R(n);
+  for (int i = 0; i < n; ++i) R[i] = parts[i]->rhs_tmp;
+  rc = rhs_into_n(parts, n, q, R.data(), nullptr, st);
+  if (rc) return rc;
+  std::vector<dg_diag> d(n);
+  for (int i = 0; i < n; ++i) {
+    dg_ctx* c = parts[i];
+    double* dev_out = c->red + (size_t)c->red_blocks * kDiagLen;
+    DG_CUDA(launch_diagnostics(c, q[i], c->rhs_tmp, nullptr, c->red, c->red_blocks, dev_out, st));
+    DG_CUDA(cudaMemcpyAsync(c->red_host, dev_out, kDiagLen * sizeof(double), cudaMemcpyDeviceToHost, st));
+    DG_CUDA(cudaMemcpyAsync(c->red_host + kDiagLen, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  }
+  for (int i = 0; i < n; ++i) {
+    rc = diag_collect(parts[i], true, false, &d[i], st);
+    if (rc && rc != DG_ERR_NONFINITE) return rc;
+  }
+  return dg_diag_combine(d.data(), n, out);
+}
 
 int dg_opts_default(dg_opts* o) {
   if (!o) return fail(DG_ERR_INVALID_ARG, "dg_opts_default: NULL");
@@ -246,6 +458,15 @@ int dg_opts_default(dg_opts* o) {
 }
 
 int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, const dg_opts* opts, dg_ctx** out) {
+  return dg_create_local(K, P, Re, Mach, Pr, closure, opts, K, out);
+}
+
+}  // extern "C"
+
+namespace dgnn {
+// dg_create for a local array of K x K x Kz elements (Kz = K: the whole periodic mesh).
+int dg_create_local(int K, int P, double Re, double Mach, double Pr, int closure, const dg_opts* opts, int Kz,
+                    dg_ctx** out) {
   if (!out) return fail(DG_ERR_INVALID_ARG, "dg_create: out is NULL");
   *out = nullptr;
   if (K < 1 || K > 256) return fail(DG_ERR_INVALID_ARG, "dg_create: K must be in [1, 256]");
@@ -275,6 +496,14 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
   if (rc) {
     delete c;
     return rc;
+  }
+  if (Kz != K) {   // a slab's local array: element and node counts of its Kz layers
+    c->Kz = Kz;
+    c->nel = K * K * Kz;
+    c->N = (long long)c->nel * c->np;
+    c->e_end = c->nel;
+    c->geom.nel = c->nel;
+    c->geom.N = c->N;
   }
 
   const bool f32 = o.precision == DG_PREC_FP32;
@@ -307,6 +536,9 @@ int dg_create(int K, int P, double Re, double Mach, double Pr, int closure, cons
   *out = c;
   return DG_OK;
 }
+}  // namespace dgnn
+
+extern "C" {
 
 int dg_destroy(dg_ctx* c) {
   if (!c) return fail(DG_ERR_INVALID_ARG, "dg_destroy: NULL");
@@ -324,6 +556,7 @@ int dg_destroy(dg_ctx* c) {
   if (c->err_dev) cudaFree(c->err_dev);
   for (int i = 0; i <= kMaxP; ++i) cudaFree(c->filter_dev[i]);
   for (int i = 0; i <= kMaxP; ++i) cudaFree(c->prolong_dev[i]);
+  for (int i = 0; i < 4; ++i) cudaFree(c->trace[i]);
   delete c;
   return DG_OK;
 }
@@ -357,12 +590,16 @@ int dg_init_tgv(dg_ctx* c, double* q, const double* pert, void* stream) {
 int dg_rhs(dg_ctx* c, const double* q, double* dqdt, const nn_model* forcing, void* stream) {
   if (!c || !q || !dqdt) return fail(DG_ERR_INVALID_ARG, "dg_rhs: NULL argument");
   if (q == dqdt) return fail(DG_ERR_INVALID_ARG, "dg_rhs: q and dqdt must not alias");
+  int rc = part_usable(c, forcing, "dg_rhs");
+  if (rc) return rc;
   return rhs_into(c, q, dqdt, forcing, (cudaStream_t)stream);
 }
 
 int dg_rk3_step(dg_ctx* c, double* q, double dt, int nsteps, const nn_model* forcing, void* stream) {
   if (!c || !q) return fail(DG_ERR_INVALID_ARG, "dg_rk3_step: NULL argument");
   if (nsteps < 0 || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_rk3_step: bad nsteps or dt");
+  int rc = part_usable(c, forcing, "dg_rk3_step");
+  if (rc) return rc;
   return rk3_steps(c, q, dt, nsteps, forcing, (cudaStream_t)stream);
 }
 
@@ -370,6 +607,8 @@ int dg_advance_host_async(dg_ctx* c, double* q_host, double dt, int nsteps, cons
                           void* stream) {
   if (!c || !q_host) return fail(DG_ERR_INVALID_ARG, "dg_advance_host_async: NULL argument");
   if (nsteps < 0 || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_advance_host_async: bad nsteps or dt");
+  int prc = part_usable(c, forcing, "dg_advance_host_async");
+  if (prc) return prc;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = 5 * c->N * sizeof(double);
   if (!c->q_dev) DG_CUDA(cudaMalloc(&c->q_dev, bytes));
@@ -437,6 +676,8 @@ int dg_prolong(const dg_ctx* lo, const dg_ctx* hi, const double* q_lo, double* q
 int dg_diagnostics(dg_ctx* c, const double* q, const double* q_ref, const nn_model* forcing, dg_diag* out,
                    void* stream) {
   if (!c || !q || !out) return fail(DG_ERR_INVALID_ARG, "dg_diagnostics: NULL argument");
+  int rc = part_usable(c, forcing, "dg_diagnostics");
+  if (rc) return rc;
   return diagnostics_into(c, q, q_ref, forcing, true, out, (cudaStream_t)stream);
 }
 
@@ -534,20 +775,20 @@ extern "C" int dg_autotune(dg_ctx* c, const double* q, double dt, int* best_E, d
   // candidates: rows of E = 1, 2, 4, ... elements, then (where allowed) cubes
   std::vector<std::pair<int, int>> cand;  // (E, cube)
   for (int E = 1; E <= max_elems_per_block(c->P); E *= 2) cand.push_back({E, 0});
-  if (cube_ok(c->P) && c->K % 2 == 0 && !c->borrowed && !c->geom.split) cand.push_back({kCubeElems, 1});
+  if (cube_ok(c->P) && c->K % 2 == 0 && !c->borrowed && !c->geom.split && !c->part) cand.push_back({kCubeElems, 1});
   for (const auto& ce : cand) {
     if (e != cudaSuccess) break;
     c->geom.E = ce.first;
     c->geom.cube = ce.second;
     e = cudaMemcpyAsync(work, q, bytes, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) break;
-    if (rk3_steps(c, work, dt, 1, nullptr, st) != DG_OK) {  // shared memory too large for this E: skip
+    if (rk3_steps(c, work, dt, 1, nullptr, st, false) != DG_OK) {  // shared memory too large for this E: skip
       cudaGetLastError();
       continue;
     }
     cudaEventRecord(a, st);
     const int reps = 3;
-    if (rk3_steps(c, work, dt, reps, nullptr, st) != DG_OK) {
+    if (rk3_steps(c, work, dt, reps, nullptr, st, false) != DG_OK) {
       cudaGetLastError();
       continue;
     }

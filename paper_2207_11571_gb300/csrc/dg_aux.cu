@@ -18,7 +18,7 @@ __global__ void k_init_tgv(double* __restrict__ q, const double* __restrict__ pe
   const int e = (int)(t / np), node = (int)(t - (long long)e * np);
   const int i = node % n, j = (node / n) % n, k = node / (n * n);
   const int K = ng.K;
-  const int ex = e % K, ey = (e / K) % K, ez = e / (K * K);
+  const int ex = e % K, ey = (e / K) % K, ez = (e / (K * K) + ng.z_off) % K;
   const double x = -M_PI + (ex + 0.5 * (ng.xi[i] + 1.0)) * ng.h;
   const double y = -M_PI + (ey + 0.5 * (ng.xi[j] + 1.0)) * ng.h;
   const double z = -M_PI + (ez + 0.5 * (ng.xi[k] + 1.0)) * ng.h;
@@ -120,7 +120,7 @@ __global__ void k_diag_partial(const double* __restrict__ q, const double* __res
   for (int i = 0; i < kDiagLen; ++i) acc[i] = 0.0;
   const int n = ng.n, np = n * n * n;
   const double jac = 0.125 * ng.h * ng.h * ng.h;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ng.N;
+  for (long long t = ng.t_begin + blockIdx.x * (long long)blockDim.x + threadIdx.x; t < ng.t_end;
        t += (long long)gridDim.x * blockDim.x) {
     const int node = (int)(t % np);
     const int i = node % n, j = (node / n) % n, k = node / (n * n);
@@ -186,6 +186,127 @@ cudaError_t launch_diagnostics(const dg_ctx* c, const double* q, const double* R
   if (e != cudaSuccess) return e;
   k_diag_final<<<1, kDiagThreads, 0, st>>>(partial, nblocks, out);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- slab face traces
+
+// Components and element size of the traces of `what` (see launch_trace_pack).
+static void trace_shape(const dg_ctx* c, int what, int* comps, int* esize) {
+  const bool f32 = c->opts.precision == DG_PREC_FP32;
+  *comps = what == 2 ? 9 : 5;
+  *esize = what == 0 ? 8 : (what == 1 ? 4 : (f32 ? 4 : 8));
+}
+
+size_t trace_bytes_for(const dg_ctx* c, int what) {
+  int comps, esize;
+  trace_shape(c, what, &comps, &esize);
+  return (size_t)comps * esize * c->K * c->K * c->n * c->n;
+}
+
+// Source (component v) of a trace value: pointer to node 0 of component v's array.
+template <typename T>
+__device__ __forceinline__ const T* trace_src(int what, int v, const double* q, const float* qn32, const T* qf,
+                                              const T* vis, long long N) {
+  if (what == 0) return reinterpret_cast<const T*>(q + v * N);
+  if (what == 1) return reinterpret_cast<const T*>(qn32 + v * N);
+  // stage state, then tau_xz, tau_yz, tau_zz, k theta_z (indices 4, 5, 2, 8 of the 9-vector:
+  // symmetric tensor (xx, yy, zz, xy, xz, yz), then the heat flux)
+  if (v < 5) return qf + v * N;
+  const int vi[4] = {4, 5, 2, 8};
+  return vis + vi[v - 5] * N;
+}
+
+// One thread per (component, element of the layer, face node); side 0 = lo, 1 = hi.
+template <typename T>
+__global__ void k_trace_pack(const double* __restrict__ q, const float* __restrict__ qn32,
+                             const float* __restrict__ dlt, const T* __restrict__ qf, const T* __restrict__ vis,
+                             int what, int comps, int K, int n, int z_lo, int z_hi, long long N, T* __restrict__ lo,
+                             T* __restrict__ hi) {
+  const int n2 = n * n, K2 = K * K, np = n2 * n;
+  const long long per_side = (long long)comps * K2 * n2;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= 2 * per_side) return;
+  const int side = t >= per_side;
+  const long long u = t - side * per_side;
+  const int v = (int)(u / ((long long)K2 * n2));
+  const int r = (int)(u - (long long)v * K2 * n2);
+  const int el = r / n2, ab = r - el * n2;
+  const long long e = (long long)(side ? z_hi : z_lo) * K2 + el;
+  const long long node = e * np + ab + (side ? n2 * (n - 1) : 0);   // upper face k = P, lower face k = 0
+  T val;
+  if (what == 1) {
+    val = T(qn32[v * N + node] + dlt[v * N + node]);     // the stage state the neighbour's phase A forms
+  } else {
+    val = trace_src<T>(what, v, q, qn32, qf, vis, N)[node];
+  }
+  (side ? hi : lo)[u] = val;
+}
+
+template <typename T>
+__global__ void k_trace_unpack(double* __restrict__ q, float* __restrict__ qn32, float* __restrict__ dlt,
+                               T* __restrict__ qf, T* __restrict__ vis, int what, int comps, int K, int n,
+                               int z_glo, int z_ghi, long long N, const T* __restrict__ lo,
+                               const T* __restrict__ hi) {
+  const int n2 = n * n, K2 = K * K, np = n2 * n;
+  const long long per_side = (long long)comps * K2 * n2;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= 2 * per_side) return;
+  const int side = t >= per_side;
+  const long long u = t - side * per_side;
+  const int v = (int)(u / ((long long)K2 * n2));
+  const int r = (int)(u - (long long)v * K2 * n2);
+  const int el = r / n2, ab = r - el * n2;
+  // lower ghost layer: its upper face (k = P) faces the first owned layer; upper ghost
+  // layer: its lower face (k = 0)
+  const long long e = (long long)(side ? z_ghi : z_glo) * K2 + el;
+  const long long node = e * np + ab + (side ? 0 : n2 * (n - 1));
+  const T val = (side ? hi : lo)[u];
+  T* dst;
+  if (what == 0) dst = reinterpret_cast<T*>(q + v * N);
+  else if (what == 1) dst = reinterpret_cast<T*>(qn32 + v * N);
+  else if (v < 5) dst = qf + v * N;
+  else {
+    const int vi[4] = {4, 5, 2, 8};
+    dst = vis + vi[v - 5] * N;
+  }
+  dst[node] = val;
+}
+
+template <typename T>
+static cudaError_t trace_pack_t(const dg_ctx* c, const double* q, int what, void* lo, void* hi, cudaStream_t st) {
+  int comps, esize;
+  trace_shape(c, what, &comps, &esize);
+  const long long total = 2LL * comps * c->K * c->K * c->n * c->n;
+  k_trace_pack<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+      q, c->qn32, c->dlt, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), what, comps, c->K, c->n, 1,
+      c->z_count, c->N, static_cast<T*>(lo), static_cast<T*>(hi));
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t trace_unpack_t(const dg_ctx* c, double* q, int what, const void* lo, const void* hi,
+                                  cudaStream_t st) {
+  int comps, esize;
+  trace_shape(c, what, &comps, &esize);
+  const long long total = 2LL * comps * c->K * c->K * c->n * c->n;
+  k_trace_unpack<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+      q, c->qn32, c->dlt, static_cast<T*>(c->qf), static_cast<T*>(c->vis), what, comps, c->K, c->n, 0,
+      c->z_count + 1, c->N, static_cast<const T*>(lo), static_cast<const T*>(hi));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_pack(const dg_ctx* c, const double* q, int what, void* lo, void* hi, cudaStream_t st) {
+  int comps, esize;
+  trace_shape(c, what, &comps, &esize);
+  return esize == 8 ? trace_pack_t<double>(c, q, what, lo, hi, st) : trace_pack_t<float>(c, q, what, lo, hi, st);
+}
+
+cudaError_t launch_trace_unpack(const dg_ctx* c, double* q, int what, const void* lo, const void* hi,
+                                cudaStream_t st) {
+  int comps, esize;
+  trace_shape(c, what, &comps, &esize);
+  return esize == 8 ? trace_unpack_t<double>(c, q, what, lo, hi, st)
+                    : trace_unpack_t<float>(c, q, what, lo, hi, st);
 }
 
 // ---------------------------------------------------------------- Algorithm 1 pairs

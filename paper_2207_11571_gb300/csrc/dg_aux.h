@@ -6,9 +6,13 @@
 namespace dgnn {
 
 // Node coordinates and quadrature weights of a context, by value for kernels.
+// t_begin, t_end: the owned nodes (a whole mesh: 0, N; a slab: its own layers);
+// z_off: global element layer of local layer 0 (a slab's lower ghost layer).
 struct NodeGeom {
   int K, n;
   long long N;
+  long long t_begin, t_end;
+  int z_off;
   double h;
   double xi[kMaxN1];
   double w[kMaxN1];
@@ -19,6 +23,9 @@ inline NodeGeom node_geom(const dg_ctx* c) {
   g.K = c->K;
   g.n = c->n;
   g.N = c->N;
+  g.t_begin = (long long)c->e_begin * c->np;
+  g.t_end = (long long)c->e_end * c->np;
+  g.z_off = c->part ? (c->z_begin - 1 + c->K) % c->K : 0;
   g.h = 2.0 * M_PI / c->K;
   for (int i = 0; i < kMaxN1; ++i) {
     g.xi[i] = i < c->n ? c->basis.xi[i] : 0.0;
@@ -45,6 +52,23 @@ cudaError_t launch_diagnostics(const dg_ctx* c, const double* q, const double* R
                                double* partial, int nblocks, double* out, cudaStream_t st);
 cudaError_t launch_make_pairs(const dg_ctx* lo, const double* qb_n, const double* qnn_np1, const double* qb_np1,
                               double dt, int first_var, int n_vars, float* X, float* Y, cudaStream_t st);
+// Face traces of a slab (element-layer partition).  pack: the owned boundary layers'
+// faces normal to z, from the first owned layer's lower faces into send_lo and the last
+// owned layer's upper faces into send_hi; unpack: recv_lo into the lower ghost layer's
+// upper faces, recv_hi into the upper ghost layer's lower faces.  Buffer layout
+// [component][element of the layer][face node].
+//   what 0: the FP64 state q (5 doubles per face node);
+//   what 1: the FP32 stage state qn32 + dlt (5 floats; unpacked into qn32, the ghost dlt
+//           stays zero);
+//   what 2: the operator-precision stage state qf and the z-normal viscous quantities
+//           (tau_xz, tau_yz, tau_zz, k theta_z): 9 values.
+cudaError_t launch_trace_pack(const dg_ctx* c, const double* q, int what, void* send_lo, void* send_hi,
+                              cudaStream_t st);
+cudaError_t launch_trace_unpack(const dg_ctx* c, double* q, int what, const void* recv_lo, const void* recv_hi,
+                                cudaStream_t st);
+// Bytes of one side's traces for `what`.
+size_t trace_bytes_for(const dg_ctx* c, int what);
+
 // q += dt s on the forced variables (Algorithm 1's correction after the step).
 cudaError_t launch_add_forcing(const dg_ctx* c, double* q, const Forcing& f, double dt, cudaStream_t st);
 

@@ -88,8 +88,20 @@ struct dg_ctx {
   dgnn::Basis1D basis;
   dgnn::Geom geom{};
   dgnn::Phys phys{};
-  long long N = 0;
-  int nel = 0;
+  long long N = 0;   // nodes of the local arrays (a slab: its own layers and two ghost layers)
+  int nel = 0;       // elements of the local arrays
+  // Owned elements [e_begin, e_end) of the local K x K x Kz element array.  A whole mesh:
+  // 0, K^3, Kz = K.  A slab of the periodic mesh (dg_create_part): global element layers
+  // [z_begin, z_begin + z_count) at local layers 1 .. z_count, with one ghost layer on
+  // each side (local layers 0 and z_count + 1) that holds the neighbouring layers' face
+  // data, filled by the trace exchange before each phase.
+  int part = 0;
+  int z_begin = 0, z_count = 0, Kz = 0;
+  int e_begin = 0, e_end = 0;
+  void* trace[4] = {};           // device face-trace buffers: send_lo, send_hi, recv_lo, recv_hi
+  size_t trace_bytes = 0;        // bytes of each buffer
+  dg_exchange_fn xfn = nullptr;  // exchange of a slab's traces with its neighbours (dg_part_set_exchange)
+  void* xuser = nullptr;
   // workspace (device)
   void* qf = nullptr;     // operator-precision stage state (reference-shifted), [5][N]
   float* qn32 = nullptr;  // FP32 operator: reference-shifted FP32 image of q at the step start, [5][N]
@@ -126,5 +138,8 @@ cudaError_t launch_flux(const dg_ctx* c, double* q, double* dqdt, const Forcing&
 // arguments (host only; no device memory is touched).  Shared by dg_create and the
 // no-allocation operator so that both run the kernels with the same constants.
 int setup_ctx(dg_ctx* c, int K, int P, double Re, double Mach, double Pr, int closure, const dg_opts& o);
+// dg_create for a local array of K x K x Kz elements (Kz = K: the whole periodic mesh).
+int dg_create_local(int K, int P, double Re, double Mach, double Pr, int closure, const dg_opts* opts, int Kz,
+                    dg_ctx** out);
 
 }  // namespace dgnn

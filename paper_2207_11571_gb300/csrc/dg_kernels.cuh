@@ -50,9 +50,14 @@ __host__ __device__ constexpr int max_threads_for(int P) {
 }
 
 // Mesh, basis and physics constants in the operator precision T.
+// Elements processed: [e_begin, nel) of a local mesh of K x K x Kz elements (a whole
+// periodic mesh: e_begin = 0, nel = K^3, Kz = K; a slab of element layers with one ghost
+// layer on each side: e_begin = K^2, nel = K^2 (Kz - 1), and the ghost layers hold the
+// neighbouring slabs' face data).
 template <typename T>
 struct OpConst {
   int K, E, nel;
+  int Kz, e_begin;
   long long N;
   T gm1, rho_ref, theta_ref, Hc;  // reference-shifted state (zero references in FP64)
   T s2h;                          // 2 / h
@@ -83,8 +88,9 @@ __device__ __forceinline__ int wrap_step(int x, int shift, int K) {
   return x < 0 ? x + K : (x >= K ? x - K : x);
 }
 
-// Element index of block element hl shifted by +/-1 along d (periodic), without division.
-__device__ __forceinline__ int neighbour_of(const BlockCoords& b, int hl, int K, int d, int shift) {
+// Element index of block element hl shifted by +/-1 along d (periodic; Kz layers along z),
+// without division.
+__device__ __forceinline__ int neighbour_of(const BlockCoords& b, int hl, int K, int Kz, int d, int shift) {
   int x = b.x + hl, y = b.y, z = b.z;
   while (x >= K) {
     x -= K;
@@ -95,7 +101,7 @@ __device__ __forceinline__ int neighbour_of(const BlockCoords& b, int hl, int K,
   }
   if (d == 0) x = wrap_step(x, shift, K);
   else if (d == 1) y = wrap_step(y, shift, K);
-  else z = wrap_step(z, shift, K);
+  else z = wrap_step(z, shift, Kz);
   return x + K * (y + K * z);
 }
 
@@ -299,7 +305,7 @@ __device__ __forceinline__ void gradient_block(int blk, const double* __restrict
   T* sD = reinterpret_cast<T*>(smem_raw);
   T* sU = sD + n2;            // [4][E np]
   T* sH = sU + 4 * tileN;     // [4][haloN]: neighbours' gradient variables on the (external) faces
-  const int e0 = blk * E;
+  const int e0 = C.e_begin + blk * E;
   const BlockCoords bc = CUBE ? cube_coords(blk, C.K) : block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
 
@@ -330,7 +336,7 @@ __device__ __forceinline__ void gradient_block(int blk, const double* __restrict
     const Item<P> it = CUBE ? cube_item_of<P>(t) : item_of<P>(t);
     if (!CUBE && e0 + it.hl >= C.nel) continue;
     const int enb = CUBE ? cube_neighbour(bc, it.hl, C.K, it.d, it.side ? 1 : -1)
-                         : neighbour_of(bc, it.hl, C.K, it.d, it.side ? 1 : -1);
+                         : neighbour_of(bc, it.hl, C.K, C.Kz, it.d, it.side ? 1 : -1);
     const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
     T sn[5], Un[4];
     stage_state<T, SRC>(q, qn32_in, dlt, N, gnb, C, sn);
@@ -638,7 +644,7 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   T* sH = kEarlyF ? sF + kTileComponents * tileN : sX + kTileComponents * tileN;  // [9][E 6 n2]
   T* sS = sH + FC * haloN;                // [5][E 6 n2]: lifted interface terms
   T* sW = sS + 5 * faceN;                 // SPLIT: primitives [6][E np] (rho, v, p', H)
-  const int e0 = blk * E;
+  const int e0 = C.e_begin + blk * E;
   const BlockCoords bc = CUBE ? cube_coords(blk, C.K) : block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
   const long long N = C.N;
@@ -709,7 +715,7 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
       const Item<P> it = CUBE ? cube_item_of<P>(t) : item_of<P>(t);
       if (!CUBE && e0 + it.hl >= C.nel) continue;
       const int enb = CUBE ? cube_neighbour(bc, it.hl, C.K, it.d, it.side ? 1 : -1)
-                           : neighbour_of(bc, it.hl, C.K, it.d, it.side ? 1 : -1);
+                           : neighbour_of(bc, it.hl, C.K, C.Kz, it.d, it.side ? 1 : -1);
       const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
       switch (it.d) {
         case 0: load_face_data<0>(qf, vis, N, gnb, sH + t, haloN); break;
@@ -1156,7 +1162,7 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
     T* h = b + 14 * kTS;
     for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
       const Item<P> it = item_of<P>(t);
-      const int enb = neighbour_of(bc, 0, m.C->K, it.d, it.side ? 1 : -1);
+      const int enb = neighbour_of(bc, 0, m.C->K, m.C->Kz, it.d, it.side ? 1 : -1);
       const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
       switch (it.d) {
         case 0: copy_face_data<0>(m.qf, m.vis, N, gnb, h + t, haloN); break;
@@ -1345,7 +1351,7 @@ struct StreamMesh {
 struct SingleSource {
   const StreamMesh& m;
   __device__ __forceinline__ StreamItem at(int item) const {
-    return StreamItem{m.q, m.qf, m.vis, m.dqdt, m.greg, m.dlt, &m.C, &m.rk, m.fc, item, m.bulk, m.err};
+    return StreamItem{m.q, m.qf, m.vis, m.dqdt, m.greg, m.dlt, &m.C, &m.rk, m.fc, m.C.e_begin + item, m.bulk, m.err};
   }
 };
 
@@ -1354,14 +1360,14 @@ struct BatchSource {
   __device__ __forceinline__ StreamItem at(int item) const {
     const int i = batch_instance(tb.block_start, tb.n, item);
     return StreamItem{tb.q[i], tb.qf[i], tb.vis[i], nullptr, tb.g[i], tb.dlt[i], &tb.C[i], &tb.rk[i], Forcing{},
-                      item - tb.block_start[i], tb.bulk[i], tb.err[i]};
+                      tb.C[i].e_begin + item - tb.block_start[i], tb.bulk[i], tb.err[i]};
   }
 };
 
 template <int P, int MODE>
 __global__ void __launch_bounds__(stream_threads(P), stream_min_blocks(P))
 k_flux_stream(const __grid_constant__ StreamMesh mesh) {
-  flux_stream<P, MODE>(SingleSource{mesh}, mesh.C.nel);
+  flux_stream<P, MODE>(SingleSource{mesh}, mesh.C.nel - mesh.C.e_begin);
 }
 
 // Batched streamed phase B: members of order P, one element per work item

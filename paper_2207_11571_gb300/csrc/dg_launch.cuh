@@ -10,6 +10,9 @@
 
 namespace dgnn {
 
+// Elements a launch processes: the whole mesh, or a slab's own layers.
+inline int owned_elems(const dg_ctx* c) { return c->e_end - c->e_begin; }
+
 inline int block_threads(int P, int E) {
   const int np = (P + 1) * (P + 1) * (P + 1);
   return ((E * np + 31) / 32) * 32;
@@ -27,7 +30,9 @@ OpConst<T> make_const(const dg_ctx* c) {
   OpConst<T> k;
   k.K = c->K;
   k.E = c->geom.E;
-  k.nel = c->nel;
+  k.nel = c->e_end;
+  k.Kz = c->Kz;
+  k.e_begin = c->e_begin;
   k.N = c->N;
   const Phys& ph = c->phys;
   k.gm1 = T(ph.gamma - 1.0);
@@ -140,7 +145,7 @@ cudaError_t gradient_p(const dg_ctx* c, const double* q, cudaStream_t st) {
   auto kern = k_gradient<P, T, SRC>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  const int grid = (c->nel + E - 1) / E;
+  const int grid = (owned_elems(c) + E - 1) / E;
   return launch_pdl(kern, dim3(grid), dim3(block_threads(P, E)), smem, st, q, c->qn32, c->dlt, static_cast<T*>(c->qf),
                                                 SRC == 0 ? c->qn32 : nullptr, static_cast<T*>(c->vis),
                                                 make_const<T>(c));
@@ -180,7 +185,7 @@ cudaError_t flux_stream_launch(const dg_ctx* c, double* q, double* dqdt, const F
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int grid = 0;
-  if ((e = stream_grid(kern, stream_threads(P), smem, c->nel, &grid)) != cudaSuccess) return e;
+  if ((e = stream_grid(kern, stream_threads(P), smem, owned_elems(c), &grid)) != cudaSuccess) return e;
   StreamMesh m;
   m.q = q;
   m.qf = static_cast<const float*>(c->qf);
@@ -219,7 +224,7 @@ cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, c
   auto kern = k_flux<P, T, MODE>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  const int grid = (c->nel + E - 1) / E;
+  const int grid = (owned_elems(c) + E - 1) / E;
   return launch_pdl(kern, dim3(grid), dim3(flux_threads(P, E)), smem, st, q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt,
                                                 static_cast<T*>(c->g), c->dlt, f, make_const<T>(c), rk);
 }
@@ -285,7 +290,7 @@ cudaError_t flux_split_p(const dg_ctx* c, double* q, double* dqdt, const Forcing
   auto kern = k_flux<P, T, MODE, false, true>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  const int grid = (c->nel + E - 1) / E;
+  const int grid = (owned_elems(c) + E - 1) / E;
   return launch_pdl(kern, dim3(grid), dim3(flux_threads(P, E)), smem, st, q, static_cast<const T*>(c->qf), static_cast<const T*>(c->vis), dqdt,
                                                 static_cast<T*>(c->g), c->dlt, f, make_const<T>(c), rk);
 }
@@ -330,7 +335,7 @@ void fill_batch(BatchTable<T>* tb, dg_ctx* const* ctx, double* const* q, const d
   for (int i = 0; i < n; ++i) {
     const dg_ctx* c = ctx[i];
     tb->block_start[i] = blocks;
-    blocks += (c->nel + c->geom.E - 1) / c->geom.E;
+    blocks += (owned_elems(c) + c->geom.E - 1) / c->geom.E;
     tb->q[i] = q[i];
     tb->qn32[i] = c->qn32;
     tb->dlt[i] = c->dlt;

@@ -18,6 +18,7 @@ DG_ERR_NONFINITE = -3
 DG_ERR_TIMEOUT = -4
 DG_ERR_IO = -5
 DG_ERR_UNSUPPORTED = -6
+DG_ERR_EXCHANGE = -7
 
 DG_PREC_FP64 = 0
 DG_PREC_FP32 = 1
@@ -59,6 +60,10 @@ _P = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
 
+# int (*)(void* user, int what, const void* send_lo, const void* send_hi, void* recv_lo,
+#         void* recv_hi, size_t bytes, void* stream)
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, _P, _I, _P, _P, _P, _P, ctypes.c_size_t, _P)
+
 # name -> argument types (all return int)
 _SIGS = {
     "dg_opts_default": [ctypes.POINTER(dg_opts)],
@@ -89,6 +94,15 @@ _SIGS = {
     "dg_batch_member": [_P, _I, ctypes.POINTER(_P)],
     "dg_batch_rk3_step": [_P, ctypes.POINTER(_P), ctypes.POINTER(_D), _I, _I, _P],
     "dg_batch_autotune": [_P, ctypes.POINTER(_P), ctypes.POINTER(_D), _P],
+    "dg_create_part": [_I, _I, _D, _D, _D, _I, ctypes.POINTER(dg_opts), _I, _I, ctypes.POINTER(_P)],
+    "dg_part_layout": [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_int64),
+                       ctypes.POINTER(ctypes.c_int64)],
+    "dg_part_set_exchange": [_P, EXCHANGE_FN, _P],
+    "dg_part_trace_bytes": [_P, _I, ctypes.POINTER(ctypes.c_size_t)],
+    "dg_group_rk3_step": [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), _D, _I, _P],
+    "dg_group_rhs": [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _P],
+    "dg_group_diagnostics": [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), ctypes.POINTER(dg_diag), _P],
+    "dg_diag_combine": [ctypes.POINTER(dg_diag), _I, ctypes.POINTER(dg_diag)],
     "dg_profile_rk3": [_P, _P, _D, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I),
                        ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D), _P],
 }
@@ -343,8 +357,8 @@ def dg_blocking(ctx):
 
 def dg_rhs_noalloc(K, P, Re, Mach, Pr, closure, precision, q, dqdt, stream=None):
     """dqdt = p(q) without device allocation (for callers that may not allocate, such as
-    an in-situ hook with a fixed memory budget or work inside a stream capture); at most
-    32768 nodes; calls share one scratch array, so overlapping calls must be serialised."""
+    an in-situ hook with a fixed memory budget); at most 32768 nodes; calls share one
+    scratch array, so overlapping calls must be serialised."""
     nodes = K ** 3 * (P + 1) ** 3
     for t, nm in ((q, "q"), (dqdt, "dqdt")):
         if t.numel() != 5 * nodes or str(t.dtype) != "torch.float64" or not t.is_cuda:
@@ -407,3 +421,82 @@ def dg_check_conversions(x, stream=None):
     mm = (ctypes.c_int64 * 2)()
     check(lib().dg_check_conversions(ptr(x), int(x.numel()), mm, stream_ptr(stream)))
     return int(mm[0]), int(mm[1])
+
+
+# ----------------------------------------------------------------------------- slabs
+
+def dg_create_part(K, P, Re, Mach, Pr=0.71, closure=0, z_begin=0, z_count=None, opts=None, **kw):
+    """Context of the slab of element layers [z_begin, z_begin + z_count) with one ghost
+    layer on each side (local arrays of z_count + 2 layers)."""
+    o = opts if opts is not None else dg_opts_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    h = ctypes.c_void_p()
+    check(lib().dg_create_part(int(K), int(P), float(Re), float(Mach), float(Pr), int(closure), ctypes.byref(o),
+                               int(z_begin), int(K if z_count is None else z_count), ctypes.byref(h)))
+    return h.value
+
+
+def dg_part_layout(ctx):
+    """(z_begin, z_count, first owned node, owned nodes) of a slab's local arrays."""
+    zb, zc, f, n = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+    check(lib().dg_part_layout(ctypes.c_void_p(ctx), ctypes.byref(zb), ctypes.byref(zc), ctypes.byref(f),
+                               ctypes.byref(n)))
+    return zb.value, zc.value, f.value, n.value
+
+
+def dg_part_set_exchange(ctx, fn):
+    """fn: an EXCHANGE_FN instance (the caller keeps it alive) or None."""
+    check(lib().dg_part_set_exchange(ctypes.c_void_p(ctx), fn if fn is not None else EXCHANGE_FN(), None))
+
+
+def dg_part_trace_bytes(ctx, what):
+    b = ctypes.c_size_t()
+    check(lib().dg_part_trace_bytes(ctypes.c_void_p(ctx), int(what), ctypes.byref(b)))
+    return b.value
+
+
+def _group_arrays(parts, qs, name="q"):
+    n = len(parts)
+    if len(qs) != n:
+        raise ValueError(f"need {n} states")
+    for i, (c, q) in enumerate(zip(parts, qs)):
+        _check_state(c, q, f"{name}[{i}]")
+    return n, (ctypes.c_void_p * n)(*parts), (ctypes.c_void_p * n)(*[q.data_ptr() for q in qs])
+
+
+def dg_group_rk3_step(parts, qs, dt, nsteps=1, stream=None):
+    n, pa, qa = _group_arrays(parts, qs)
+    check(lib().dg_group_rk3_step(pa, n, qa, float(dt), int(nsteps), stream_ptr(stream)))
+
+
+def dg_group_rhs(parts, qs, dqdts, stream=None):
+    n, pa, qa = _group_arrays(parts, qs)
+    _, _, da = _group_arrays(parts, dqdts, "dqdt")
+    check(lib().dg_group_rhs(pa, n, qa, da, stream_ptr(stream)))
+
+
+def dg_group_diagnostics(parts, qs, stream=None, raise_nonfinite=True):
+    n, pa, qa = _group_arrays(parts, qs)
+    d = dg_diag()
+    st = lib().dg_group_diagnostics(pa, n, qa, ctypes.byref(d), stream_ptr(stream))
+    if st != DG_ERR_NONFINITE or raise_nonfinite:
+        check(st)
+    return d.as_dict()
+
+
+def dg_diag_combine(diags, raise_nonfinite=True):
+    """Combines the slabs' diagnostics (dicts as returned by dg_diagnostics), in order."""
+    n = len(diags)
+    arr = (dg_diag * n)()
+    for a, d in zip(arr, diags):
+        a.mass, a.energy, a.ke, a.dke_dt, a.max_wave = d["mass"], d["energy"], d["ke"], d["dke_dt"], d["max_wave"]
+        a.nonfinite = int(d["nonfinite"])
+        for k in range(3):
+            a.momentum[k] = d["momentum"][k]
+            a.e_inf[k] = d["e_inf"][k]
+    out = dg_diag()
+    st = lib().dg_diag_combine(arr, n, ctypes.byref(out))
+    if st != DG_ERR_NONFINITE or raise_nonfinite:
+        check(st)
+    return out.as_dict()

@@ -61,12 +61,15 @@ class Run:
         self.einf = []
         self.diverged_at = None
         self.fallback_at = None
+        self.active_time = 0.0   # time units advanced with the network forcing on
 
     def advance(self, interval):
         if self.diverged_at is not None:
             return
         n = max(1, math.ceil(interval / self.dt_max - 1e-9))
         dt = interval / n
+        if self.net is not None:
+            self.active_time += interval
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         dg.dg_rk3_step(self.ctx, self.q, dt, n, forcing=self.net)
@@ -365,6 +368,10 @@ def run(args):
                "errors": run_errors(r, ref.t, ref.dke, ref.ke, bar_ke),
                "diverged_at": r.diverged_at, "fallback_at": r.fallback_at}
         rec["dke_error"] = rec["errors"]["dke"]
+        if r is runs[0]:
+            # the share of the evaluation horizon over which the network forcing was on (the
+            # rest ran as the uncorrected solver after the guard's fallback)
+            rec["forcing_active_fraction"] = r.active_time / (args.t_end - t0)
         if r.P == args.P_lo:
             rec["einf_mean"] = (float(np.mean([e for e in r.einf if e is not None]))
                                 if r.diverged_at is None else float("inf"))
@@ -373,7 +380,9 @@ def run(args):
     out["speedup_vs_plain_at_equal_error"] = {}
     for key in ("dke", "ke", "dke_filtered"):
         sp, lower = speedup_at_equal_error(corr, plain, key)
-        out["speedup_vs_plain_at_equal_error"][key] = {"speedup": sp, "lower_bound": lower}
+        out["speedup_vs_plain_at_equal_error"][key] = {"speedup": sp, "lower_bound": lower,
+                                                       "forcing_active_fraction": corr["forcing_active_fraction"]}
+    out["forcing_active_fraction"] = corr["forcing_active_fraction"]
     p6 = [r for r in plain if r["P"] == 6]
     if p6:
         out["speedup_vs_P6"] = p6[0]["ms"] / corr["ms"]
@@ -401,6 +410,7 @@ def main(argv=None):
     summary["runs"] = [(r["name"], {k: round(v, 4) for k, v in r["errors"].items()}, round(r["ms"], 1),
                         r["diverged_at"], r["fallback_at"]) for r in out["runs"]]
     summary["speedup_vs_P6"] = out.get("speedup_vs_P6")
+    summary["forcing_active_fraction"] = out["forcing_active_fraction"]
     print(json.dumps(summary))
 
 

@@ -14,7 +14,9 @@ and the device time per RK3 step of each operator.
 
     python -m paper_2207_11571_gb300.precision_run --K 32 --P 3 --t_end 10 --out r.json
 
---max_seconds bounds the wall time of the time loop; the run then stops at the last
+--split runs both operators with the kinetic-energy-preserving split-form volume term
+(the standard form without a closure is not stable on the under-resolved Re 1600 meshes
+past the dissipation peak).  --max_seconds bounds the wall time of the time loop; the run then stops at the last
 completed sample time (reported as t_reached).  A run whose state turns non-finite
 (the standard-form operator on an under-resolved mesh without a closure) stops there:
 diverged_at gives the first sample time at which each diverged run was non-finite, and
@@ -31,9 +33,11 @@ import torch
 from . import dg, inputs
 
 
-def run(K, P, Re=1600.0, Mach=0.1, Pr=0.71, les=False, cfl=0.7, t_end=10.0, sample=0.1, max_seconds=0.0):
+def run(K, P, Re=1600.0, Mach=0.1, Pr=0.71, les=False, cfl=0.7, t_end=10.0, sample=0.1, max_seconds=0.0,
+        split=False):
     precs = {"fp32": dg.DG_PREC_FP32, "fp64": dg.DG_PREC_FP64}
-    ctx = {k: dg.dg_create(K, P, Re, Mach, Pr, int(les), precision=p) for k, p in precs.items()}
+    ctx = {k: dg.dg_create(K, P, Re, Mach, Pr, int(les), precision=p, volume_flux=int(split))
+           for k, p in precs.items()}
     try:
         N = dg.dg_sizes(ctx["fp64"])[0]
         pert = torch.from_numpy(inputs.perturbation((5, N)).ravel()).cuda()
@@ -95,7 +99,7 @@ def run(K, P, Re=1600.0, Mach=0.1, Pr=0.71, les=False, cfl=0.7, t_end=10.0, samp
     e32, e64 = np.array(hist["fp32"]["eps"][:m]), np.array(hist["fp64"]["eps"][:m])
     i32, i64 = int(np.argmax(e32)), int(np.argmax(e64))
     return {
-        "mesh": f"{K}^3/P{P}", "nodes": N, "Re": Re, "Mach": Mach, "les": les, "cfl": cfl,
+        "mesh": f"{K}^3/P{P}", "nodes": N, "Re": Re, "Mach": Mach, "les": les, "split_form": split, "cfl": cfl,
         "t_end": t_end, "t_reached": hist["t"][m - 1], "diverged_at": diverged or None, "steps": steps,
         "elems_per_block": tuned,
         "ke_rel_max": float(np.max(np.abs(ke32 - ke64) / ke64)),
@@ -116,6 +120,8 @@ def main(argv=None):
     ap.add_argument("--Mach", type=float, default=0.1)
     ap.add_argument("--Pr", type=float, default=0.71)
     ap.add_argument("--les", action="store_true")
+    ap.add_argument("--split", action="store_true",
+                    help="kinetic-energy-preserving split-form volume term (dg_opts.volume_flux = 1)")
     ap.add_argument("--cfl", type=float, default=0.7)
     ap.add_argument("--t_end", type=float, default=10.0)
     ap.add_argument("--sample", type=float, default=0.1)
@@ -123,7 +129,7 @@ def main(argv=None):
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     dg.lib()
-    r = run(a.K, a.P, a.Re, a.Mach, a.Pr, a.les, a.cfl, a.t_end, a.sample, a.max_seconds)
+    r = run(a.K, a.P, a.Re, a.Mach, a.Pr, a.les, a.cfl, a.t_end, a.sample, a.max_seconds, a.split)
     if a.out:
         with open(a.out, "w") as f:
             json.dump(r, f)

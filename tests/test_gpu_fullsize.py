@@ -16,12 +16,11 @@ import pytest
 
 from oracle import dgsem, physics
 from paper_2207_11571_gb300 import inputs
+from tests import fp32_bounds
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-FP32_RTOL_MOMENTUM = 1e-3
-FP32_RTOL_ENERGY = 1e-2
 MESHES = [(32, 3), (16, 6), (16, 8)]
 
 
@@ -42,14 +41,25 @@ def samples(K):
     return fixed + [tuple(int(v) for v in rng.integers(0, K, 3)) for _ in range(7)]
 
 
-def patch_rhs(q, mesh, flow, centre):
-    """Oracle operator at one element from the 5^3 block of elements around it."""
-    K = mesh.K
+def patch_state(q, K, centre):
+    """The 5^3 block of elements around one element, cut from the full state."""
     idx = [[(c - 2 + i) % K for i in range(5)] for c in centre]
-    qp = np.take(np.take(np.take(q, idx[0], axis=1), idx[1], axis=2), idx[2], axis=3)
+    return np.take(np.take(np.take(q, idx[0], axis=1), idx[1], axis=2), idx[2], axis=3)
+
+
+def patch_mesh(mesh, dtype=np.float64):
     mp = dgsem.Mesh(5, mesh.P)
     mp.h = mesh.h
-    return dgsem.rhs(qp, mp, flow)[:, 2, 2, 2]
+    if dtype != np.float64:   # the same FP64 tables, evaluated in extended precision
+        mp.w, mp.xi, mp.D = (np.asarray(a, dtype) for a in (mp.w, mp.xi, mp.D))
+        mp.h = dtype(mesh.h)
+    return mp
+
+
+def patch_rhs(q, mesh, flow, centre, dtype=np.float64):
+    """Oracle operator at one element from the 5^3 block of elements around it."""
+    qp = np.asarray(patch_state(q, mesh.K, centre), dtype)
+    return dgsem.rhs(qp, patch_mesh(mesh, dtype), flow)[:, 2, 2, 2]
 
 
 @pytest.fixture(scope="module")
@@ -88,23 +98,34 @@ def test_fp32_operator_at_full_size_matches_oracle_on_sampled_elements(dg, cases
     R = gpu_rhs(dg, K, P, q, dg.DG_PREC_FP32)
     got = np.stack([R[:, ez, ey, ex] for ez, ey, ex in ref])
     want = np.stack(list(ref.values()))
-    err = [np.linalg.norm(got[:, v] - want[:, v]) / np.linalg.norm(want[:, v]) for v in range(5)]
-    assert max(err[1:4]) < FP32_RTOL_MOMENTUM, err
-    assert err[4] < FP32_RTOL_ENERGY, err
-    assert np.linalg.norm(got[:, 0] - want[:, 0]) < FP32_RTOL_MOMENTUM * np.linalg.norm(want[:, 1]), err
+    fp32_bounds.check(f"fullsize K{K} P{P}", got, want, axis_vars=1)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.longdouble)
+    b = np.asarray(b, np.longdouble)
+    return float(np.sqrt(np.sum((a - b) ** 2)) / np.sqrt(np.sum(b ** 2)))
 
 
 @pytest.mark.parametrize("K,P", MESHES)
 def test_fp64_operator_at_full_size_matches_oracle_on_sampled_elements(dg, cases, K, P):
+    """FP64 parity bar of the operator tests: 1e-12 relative L2 against the FP64 oracle, or,
+    where the FP64 arithmetic floor of the case itself exceeds 1e-12 (Mach 0.1, the
+    background pressure and energy cancel in the derivatives), the GPU no farther from the
+    extended-precision oracle than the FP64 oracle is (x 1.5), on the same sampled
+    elements."""
     q, ref = cases[(K, P)]
     R = gpu_rhs(dg, K, P, q, dg.DG_PREC_FP64)
     got = np.stack([R[:, ez, ey, ex] for ez, ey, ex in ref])
     want = np.stack(list(ref.values()))
-    err = np.linalg.norm(got - want) / np.linalg.norm(want)
-    # GPU and oracle round the same operations; the FP64 operator's own rounding floor at
-    # Mach 0.1 is 0.4e-12 (P3) to 8.5e-12 (P6) (measured against extended precision on
-    # small meshes), so agreement is asked within that floor
-    assert err < 2e-11, err
+    direct = rel_l2(got, want)
+    if direct < 1e-12:
+        return
+    flow = physics.Flow(Re=1600.0, Mach=0.1, Pr=0.71)
+    mesh = dgsem.Mesh(K, P)
+    ext = np.stack([patch_rhs(q, mesh, flow, s, np.longdouble) for s in ref])
+    e_gpu, e_or = rel_l2(got, ext), rel_l2(want, ext)
+    assert e_or > 1e-12 and e_gpu <= 1.5 * e_or, (direct, e_gpu, e_or)
 
 
 @pytest.mark.parametrize("K,P", MESHES)

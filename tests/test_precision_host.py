@@ -24,7 +24,7 @@ class _Event:
 def _fake_dg(diverge_fp32_below=None):
     ctxs = {}
 
-    def create(K, P, Re, Mach, Pr, les, precision=0):
+    def create(K, P, Re, Mach, Pr, les, precision=0, volume_flux=0):
         ctxs[len(ctxs) + 1] = {"N": K ** 3 * (P + 1) ** 3, "fp32": precision == 1}
         return len(ctxs)
 
