@@ -34,6 +34,9 @@ RE, MACH, PR, CFL = 1600.0, 0.1, 0.71, 0.7
 METRIC = "DOF-stage updates/s (TGV 32^3/P3, 16^3/P6, 16^3/P8 per RK3 step)"
 UNIT = "DOF-stage updates/s"
 CPU_SAMPLE = [(8, 3), (8, 6), (8, 8)]
+# Algorithmic floor of one DOF-stage update: read the FP64 state (5 x 8 B), read and write
+# the FP64 RK register (2 x 5 x 8 B), write the state (5 x 8 B)
+FLOOR_BYTES = 160.0
 KERNEL_SOURCES = ["dg_kernels.cuh", "dg_device.cuh", "dg_launch.cuh"]
 
 
@@ -45,6 +48,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-instances key of the default line")
+    ap.add_argument("--no-algorithm1", action="store_true", help="skip the algorithm1 key of the default line")
     ap.add_argument("--workload", choices=["tgv3", "batched"], default="tgv3",
                     help="tgv3: the three TGV meshes (default); batched: 12 independent TGV instances "
                          "(Re from {30, 200, 1600}, meshes 8^3-16^3, P in {3, 6}) in one batch")
@@ -142,25 +147,72 @@ def nn_measure(stream, steps=100):
     q = torch.empty(5 * N, dtype=torch.float64, device="cuda")
     dg.dg_init_tgv(c, q)
     s = torch.empty(5 * N, dtype=torch.float32, device="cuda")
-    for i in range(5):
-        nn.nn_forcing_infer(net, c, q, s, stream)
-    e0.record(stream)
-    for i in range(steps):
-        nn.nn_forcing_infer(net, c, q, s, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    infer_us = e0.elapsed_time(e1) / steps * 1e3
+
+    def timed(fn, n):
+        for _ in range(5):
+            fn()
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n * 1e3   # us
+
+    infer = {}
+    for name, mode in (("cluster", nn.NN_INFER_CLUSTER), ("layers", nn.NN_INFER_LAYERS)):
+        nn.nn_set_fused(net, mode)
+        infer[name] = timed(lambda: nn.nn_forcing_infer(net, c, q, s, stream), steps)
+    nn.nn_set_fused(net, nn.NN_INFER_CLUSTER)
+    # the corrected RK3 step (forcing on every stage state) against the plain one, 16^3 P=3
+    dt = dg.dg_stable_dt(c, q, CFL)
+    plain_us = timed(lambda: dg.dg_rk3_step(c, q, dt, 1, None, stream), 50)
+    corrected_us = timed(lambda: dg.dg_rk3_step(c, q, dt, 1, net, stream), 50)
     dg.dg_destroy(c)
     nn.nn_destroy(net)
     peak, kind = bf16_peak()
     tr = 3 * flop_fwd / (train_us * 1e-6) / 1e12
-    inf = flop_fwd / (infer_us * 1e-6) / 1e12
+    inf = {k: flop_fwd / (v * 1e-6) / 1e12 for k, v in infer.items()}
     return {"network": "320-512x4-320, batch 4096 (16^3 elements at P=3)",
             "train_step_us": round(train_us, 1), "train_tflops": round(tr, 1),
-            "forcing_infer_us": round(infer_us, 1), "forcing_infer_tflops": round(inf, 1),
-            "note": "forcing_infer includes the phase-A stage-state launch; tensor work is the 5 GEMMs",
+            "forcing_infer_us": round(infer["cluster"], 1), "forcing_infer_tflops": round(inf["cluster"], 1),
+            "forcing_infer_layers_us": round(infer["layers"], 1),
+            "forcing_infer_layers_tflops": round(inf["layers"], 1),
+            "rk3_step_16cubed_P3_us": {"plain": round(plain_us, 1), "corrected": round(corrected_us, 1),
+                                       "ratio": round(corrected_us / plain_us, 3)},
+            "note": "forcing_infer (nn_forcing_infer on an FP32 context) includes the phase-A launch that forms "
+                    "the stage state; cluster = one launch (features, 5 layers, unscaling), layers = feature "
+                    "launch + 5 GEMMs; the corrected step evaluates the forcing on each of the 3 stage states",
             "roofline": {"bound": "tensor", "peak": peak, "unit": "TFLOP/s", "peak_source": kind,
-                         "train_frac": round(tr / peak, 4), "infer_frac": round(inf / peak, 4)}}
+                         "train_frac": round(tr / peak, 4), "infer_frac": round(inf["cluster"] / peak, 4)}}
+
+
+# Algorithm 1 in the paper's own acceleration setting (Sec. 3.5, Fig. 6, Table 2): Taylor-
+# Green at Re 1600, Mach 0.08, 8^3 elements, P8 data over t in [7, 7.2], a network of 8
+# layers trained 30 epochs on the momenta, the corrected P3 run against plain P3..P6 to
+# t = 8 (split-form volume term, post-step forcing, no fallback guard)
+ALG1_ARGS = ["--K", "8", "--P_hi", "8", "--P_lo", "3", "--plain", "3,4,5,6", "--Re", "1600", "--Mach", "0.08",
+             "--t_train", "7", "--t_train_end", "7.2", "--t_end", "8", "--io", "momentum", "--width", "256",
+             "--hidden", "7", "--epochs", "30", "--batch", "4096", "--sample", "0.05", "--forcing", "post",
+             "--split_lo", "--split_hi", "--no_guard", "--out", ""]
+
+
+def algorithm1_measure():
+    """One bounded run of Algorithm 1 through the C ABI (high-order run, pairs, GPU
+    training, corrected and plain low-order runs timed with CUDA events): the corrected
+    run's errors and cost against the plain orders, and the speed-up at equal error."""
+    from paper_2207_11571_gb300 import experiment
+    out = experiment.run(experiment.parse(ALG1_ARGS))
+    runs = {r["name"]: {"ms": round(r["ms"], 2), "dke_error": round(r["errors"]["dke"], 4),
+                        "einf_error": round(r["errors"]["einf"], 4)} for r in out["runs"]}
+    sp = out["speedup_vs_plain_at_equal_error"]
+    return {"setting": "TGV Re 1600 Mach 0.08, 8^3, P8 -> P3, training window [7, 7.2], eval [7.2, 8], momenta, "
+                       "8 layers x 256, 30 epochs, post-step forcing, split form",
+            "runs": runs, "train_seconds": round(out["train_seconds"], 2), "n_pairs": out["n_pairs"],
+            "speedup_at_equal_error": {k: (None if v["speedup"] is None else round(v["speedup"], 3))
+                                       for k, v in sp.items()},
+            "forcing_active_fraction": out["forcing_active_fraction"],
+            "cost_P6_over_corrected": round(out.get("speedup_vs_P6", float("nan")), 3),
+            "seconds": round(out["total_seconds"], 1)}
 
 
 def peaks():
@@ -223,8 +275,13 @@ class Clocks:
 
 # ----------------------------------------------------------------------------- CPU oracle
 
+CPU_MESHES = [(8, 3), (8, 6), (8, 8), (16, 3), (16, 6), (16, 8)]
+CPU_STEPS = 3
+
+
 def oracle_sample_rate(repeats=1):
-    """FP64 oracle (numpy, single thread) on one RK3 stage of an 8^3 mesh at each order."""
+    """FP64 oracle (numpy, single thread) on one RK3 stage of an 8^3 mesh at each order:
+    the per-step sample of the reference arm."""
     import numpy as np
 
     from oracle import dgsem, physics
@@ -243,6 +300,107 @@ def oracle_sample_rate(repeats=1):
         del q, g
     return total_nodes / total_s, total_s, "one RK3 stage of the FP64 oracle on 8^3 elements at P=3, 6, 8 " \
                                            "(same per-DOF work as the benchmark meshes)"
+
+
+def _slab_rhs_worker(task):
+    """Pool worker of the all-core oracle leg: the oracle operator on element layers
+    [z0, z1) of the periodic mesh, evaluated on those layers plus two ghost layers on each
+    side (the operator at an element reads elements at most two face steps away) and
+    written into the shared result array.  The state and result live in shared memory."""
+    import numpy as np
+    from multiprocessing import shared_memory
+
+    from oracle import dgsem, physics
+    q_name, r_name, shape, K, P, z0, z1 = task
+    qs, rs = shared_memory.SharedMemory(name=q_name), shared_memory.SharedMemory(name=r_name)
+    try:
+        q = np.ndarray(shape, np.float64, buffer=qs.buf)
+        R = np.ndarray(shape, np.float64, buffer=rs.buf)
+        layers = [(z - 2) % K for z in range(z0, z1 + 4)]
+        mesh = dgsem.Mesh(K, P)
+        R[:, z0:z1] = dgsem.rhs(np.take(q, layers, axis=1), mesh, physics.Flow(Re=RE, Mach=MACH, Pr=PR))[:, 2:-2]
+    finally:
+        qs.close()
+        rs.close()
+    return z1 - z0
+
+
+def oracle_rk3_rate(K, P, pool=None, workers=1):
+    """DOF-stage updates/s of the FP64 oracle over CPU_STEPS full RK3 steps (after one
+    warm-up operator evaluation) on the K^3 mesh at order P.  pool is None: one thread
+    (the oracle as it stands); otherwise the operator of every stage is split into z-slabs
+    of the mesh evaluated by the pool's processes (the RK update stays in this process)."""
+    import numpy as np
+    from multiprocessing import shared_memory
+
+    from oracle import dgsem, physics
+    flow = physics.Flow(Re=RE, Mach=MACH, Pr=PR)
+    mesh = dgsem.Mesh(K, P)
+    q0 = dgsem.tgv_state(mesh, flow)
+    dt = dgsem.stable_dt(q0, mesh, flow, CFL)
+    shm = []
+    if pool is None:
+        def rhs(z):
+            return dgsem.rhs(z, mesh, flow)
+    else:
+        shm = [shared_memory.SharedMemory(create=True, size=q0.nbytes) for _ in range(2)]
+        qs = np.ndarray(q0.shape, np.float64, buffer=shm[0].buf)
+        rs = np.ndarray(q0.shape, np.float64, buffer=shm[1].buf)
+        bounds = np.linspace(0, K, workers + 1).round().astype(int)
+        tasks = [(shm[0].name, shm[1].name, q0.shape, K, P, int(a), int(b)) for a, b in zip(bounds, bounds[1:]) if b > a]
+
+        def rhs(z):
+            qs[...] = z
+            pool.map(_slab_rhs_worker, tasks)
+            return rs.copy()
+    try:
+        rhs(q0)                                  # warm-up
+        t0 = time.perf_counter()
+        q = q0
+        for _ in range(CPU_STEPS):
+            q = dgsem.rk3_step(q, dt, rhs)
+        secs = time.perf_counter() - t0
+    finally:
+        for m in shm:
+            m.close()
+            m.unlink()
+    return 3 * CPU_STEPS * q0[0].size / secs, secs
+
+
+def cpu_baseline():
+    """The oracle timed on this host: single thread, and its operator split over element
+    slabs on every core, at 8^3 and 16^3 elements for P = 3, 6, 8 (3 RK3 steps each after
+    a warm-up).  The pool starts with 'spawn' (this process already holds a CUDA context)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    single, multi = {}, {}
+    t_single = t_multi = 0.0
+    nodes_total = 0
+    for K, P in CPU_MESHES:
+        rate, secs = oracle_rk3_rate(K, P)
+        single[f"{K}^3/P{P}"] = rate
+        t_single += secs
+        nodes_total += 3 * CPU_STEPS * K ** 3 * (P + 1) ** 3
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_limit_threads) as pool:
+        for K, P in CPU_MESHES:
+            rate, secs = oracle_rk3_rate(K, P, pool=pool, workers=min(cores, K))
+            multi[f"{K}^3/P{P}"] = rate
+            t_multi += secs
+    sample = (f"{CPU_STEPS} full RK3 steps of the FP64 oracle (after one warm-up operator evaluation) on each of "
+              f"8^3 and 16^3 elements at P = 3, 6, 8, TGV Re 1600 Mach 0.1; value = all-core rate over the six meshes")
+    return {"value": nodes_total / t_multi, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "seconds": round(t_single + t_multi, 1),
+            "single_thread": {"value": nodes_total / t_single, "cores": 1, "per_mesh": single},
+            "all_cores": {"value": nodes_total / t_multi, "cores": cores, "nproc": cores, "per_mesh": multi,
+                          "how": "process pool ('spawn'), the operator of each stage over z-slabs of min(cores, K) "
+                                 "element layers with two ghost layers each (shared-memory state); RK update in "
+                                 "the parent"}}
+
+
+def _limit_threads():
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
 
 
 def run_reference(args, rank, ws):
@@ -316,6 +474,21 @@ def run_ours(args, rank, ws):
     ms = max_over_ranks(e0.elapsed_time(e1), ws)
     value = updates_per_step * args.steps * ws / (ms / 1e3)
 
+    peak, peak_kind = peaks()
+    # per-mesh rates: each mesh's RK3 steps timed alone (CUDA events on the launching stream)
+    per_mesh = {}
+    n_alone = max(3, args.steps // 3)
+    for (K, P), c, q, dt, N in zip(WORKLOAD, ctxs, states, dts, nodes):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        dg.dg_rk3_step(c, q, dt, n_alone, None, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rate = 3 * N * n_alone / (a.elapsed_time(b) / 1e3)
+        per_mesh[f"{K}^3/P{P}"] = {"nodes": N, "dof_stage_per_s": rate, "ms_per_step": a.elapsed_time(b) / n_alone,
+                                   "floor_achieved_gbs": FLOOR_BYTES * rate / 1e9,
+                                   "frac": FLOOR_BYTES * rate / 1e9 / peak}
+
     # per-kernel device times (CUDA events around each launch, on the launching stream)
     prof = []
     for (K, P), c, q, dt in zip(WORKLOAD, ctxs, states, dts):
@@ -329,22 +502,36 @@ def run_ours(args, rank, ws):
             kernels.append({"kernel": "k_flux" if kind == "flux" else "k_gradient", "workload": p["workload"],
                             "ms": p[f"ms_{kind}"], "launches": p[f"launches_{kind}"],
                             "bytes_per_launch": p[f"{kind}_bytes_per_launch"],
-                            "share": p[f"ms_{kind}"] / total_ms})
+                            "share": p[f"ms_{kind}"] / total_ms,
+                            "traffic_per_launch": measured_traffic("k_flux" if kind == "flux" else "k_gradient",
+                                                                   p["workload"])})
     dom = max(kernels, key=lambda k: k["ms"])
-    peak, peak_kind = peaks()
-    achieved = dom["bytes_per_launch"] / (dom["ms"] / dom["launches"] / 1e3) / 1e9
-    traffic = measured_traffic(dom["kernel"], dom["workload"])
+    dom_achieved = dom["bytes_per_launch"] / (dom["ms"] / dom["launches"] / 1e3) / 1e9
+    # Headline: the algorithmic floor of the method per DOF-stage (read q, read and write
+    # the FP64 RK register, write q: 160 B) times the DOF-stage rate of the timed region.
+    # One unit of work = one RK stage of the three meshes (both launches of each mesh).
+    unit_bytes = FLOOR_BYTES * sum(nodes)
+    achieved = FLOOR_BYTES * value / ws / 1e9   # per GPU
+    traffics = [k["traffic_per_launch"] for k in kernels]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": peak_kind, "kernel": f'{dom["kernel"]} {dom["workload"]}',
-                "traffic": traffic}
-    # the whole timed step on the same bytes: every launch of one RK3 step of every mesh
-    # (3 stages x both phases, stage-averaged bytes per launch) over the timed ms per step
+                "peak_source": peak_kind, "bytes_per_dof_stage": FLOOR_BYTES,
+                "kernel": "one RK stage of the three meshes (k_gradient + k_flux per mesh)",
+                "bytes_per_launch": unit_bytes,
+                "traffic": sum(traffics) if all(t is not None for t in traffics) else None,
+                "per_mesh": {m: round(v["frac"], 4) for m, v in per_mesh.items()},
+                "note": "algorithmic floor 160 B per DOF-stage (q read, RK register read + write, q write, "
+                        "FP64); traffic = ncu DRAM bytes of the six launches of one stage, null unless taken "
+                        "on the current kernel sources"}
+    # the implementation's own bytes (stage state, stored stresses, FP32 increments: each
+    # value read or written once) over the whole timed step and for the dominant kernel
     step_bytes = sum(3 * (p["flux_bytes_per_launch"] + p["gradient_bytes_per_launch"]) for p in prof)
     step_gbs = step_bytes / (ms / args.steps / 1e3) / 1e9
-    roofline["step"] = {"achieved": step_gbs, "frac": step_gbs / peak,
-                        "bytes_per_dof_stage": step_bytes / updates_per_step,
-                        "note": "all launches of the timed steps, including the gaps between them"}
-    per_kernel =[{k: (round(v, 5) if isinstance(v, float) else v) for k, v in kk.items()} for kk in kernels]
+    roofline["implementation"] = {
+        "bytes_per_dof_stage": step_bytes / updates_per_step, "achieved": step_gbs, "frac": step_gbs / peak,
+        "dominant_kernel": f'{dom["kernel"]} {dom["workload"]}', "dominant_achieved": dom_achieved,
+        "dominant_frac": dom_achieved / peak, "dominant_bytes_per_launch": dom["bytes_per_launch"],
+        "dominant_traffic": dom["traffic_per_launch"]}
+    per_kernel = [{k: (round(v, 5) if isinstance(v, float) else v) for k, v in kk.items()} for kk in kernels]
 
     # end to end through the C ABI with HOST buffers (pinned), copies inside the timed region
     host = [torch.empty(5 * n, dtype=torch.float64, pin_memory=True) for n in nodes]
@@ -378,15 +565,22 @@ def run_ours(args, rank, ws):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, secs, sample = oracle_sample_rate(repeats=4)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-               "seconds": round(secs, 2)}
+        cpu = cpu_baseline()
 
     nn_line = nn_measure(stream)
+    alg1 = None if args.no_algorithm1 else algorithm1_measure()
+    batched = None
+    if not args.no_batched:
+        batched = batched_measure(args, rank, ws, max(10, args.steps // 3))
+        batched.pop("clocks", None)
+        batched["workload"] = BATCH_NAME
 
     per_workload = {}
     for (K, P), n, p in zip(WORKLOAD, nodes, prof):
-        per_workload[f"{K}^3/P{P}"] = {"nodes": n, "dof_stage_per_s_kernels":
+        m = per_mesh[f"{K}^3/P{P}"]
+        per_workload[f"{K}^3/P{P}"] = {"nodes": n, "dof_stage_per_s": m["dof_stage_per_s"],
+                                       "ms_per_step": m["ms_per_step"], "floor_frac": m["frac"],
+                                       "dof_stage_per_s_kernels_events_between":
                                        3 * 3 * n / ((p["ms_gradient"] + p["ms_flux"]) / 1e3)}
     shapes = ["cube 2x2x2" if dg.dg_blocking(c)[1] else "row" for c in ctxs]
     for c in ctxs:
@@ -402,7 +596,9 @@ def run_ours(args, rank, ws):
                            "elems_per_block": tuned,
                            "block_shape": shapes,
                            "parallelism": f"replicas x{ws}", "per_workload": per_workload},
-                "roofline": roofline, "kernels": per_kernel, "network": nn_line, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "kernels": per_kernel, "network": nn_line, "batched": batched,
+                "algorithm1": alg1,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 6 * len(WORKLOAD) * args.steps, "clocks": clk}
         print(json.dumps(line), flush=True)
     return 0
@@ -412,16 +608,17 @@ def run_ours(args, rank, ws):
 
 # FP32-operator algorithmic bytes per node of one RK3 step (both launches of all stages)
 STEP_BYTES_PER_NODE = 676.0
+BATCH_NAME = ("12 independent TGV instances, (K, P, Re) drawn with seed 12 from {8,12,16} x {3,6} x "
+              "{30,200,1600}, Mach 0.1, one batch, graph replay")
 
 
-def run_batched(args, rank, ws):
+def batched_measure(args, rank, ws, steps, with_clocks=False):
+    """Config-3 batch: 12 independent TGV instances advanced by dg_batch_rk3_step (graph
+    replay).  Returns the measurements as a dict (rates, per-step time, the same members one
+    at a time, end to end from pinned host states, roofline on the 160 B floor)."""
     import torch
 
-    from paper_2207_11571_gb300 import build as _build
     from paper_2207_11571_gb300 import dg, inputs
-    if not os.path.exists(_build.LIB):
-        _build.build()
-    dg.lib()
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
     members = inputs.batch_members()
@@ -441,23 +638,35 @@ def run_batched(args, rank, ws):
 
     dg.dg_batch_rk3_step(b, qs, dts, args.warmup, 0, stream)
     torch.cuda.synchronize()
-    clocks = Clocks(dev)
+    clocks = Clocks(dev) if with_clocks else None
     barrier(ws)
     torch.cuda.synchronize()
-    clocks.start()
+    if clocks:
+        clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    dg.dg_batch_rk3_step(b, qs, dts, args.steps, 0, stream)
+    dg.dg_batch_rk3_step(b, qs, dts, steps, 0, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(ws)
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     ms = max_over_ranks(e0.elapsed_time(e1), ws)
-    value = updates_per_step * args.steps * ws / (ms / 1e3)
+    value = updates_per_step * steps * ws / (ms / 1e3)
+
+    # one persistent cooperative launch per RK stage for every member (both orders)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dg.dg_batch_rk3_step(b, qs, dts, 2, dg.DG_BATCH_PERSISTENT, stream)
+    p0.record(stream)
+    dg.dg_batch_rk3_step(b, qs, dts, steps, dg.DG_BATCH_PERSISTENT, stream)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    persistent = {"value": updates_per_step * steps / (p0.elapsed_time(p1) / 1e3), "unit": UNIT,
+                  "ms_per_step": p0.elapsed_time(p1) / steps,
+                  "call": "dg_batch_rk3_step(..., DG_BATCH_PERSISTENT): 3 cooperative launches per step"}
 
     # the same members advanced one at a time (dg_rk3_step per member), for comparison
     u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n_cmp = max(1, args.steps // 4)
+    n_cmp = max(1, steps // 4)
     u0.record(stream)
     for _ in range(n_cmp):
         for i, q in enumerate(qs):
@@ -486,25 +695,41 @@ def run_batched(args, rank, ws):
            "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state,
            "call": "dg_batch_rk3_step (pinned host states copied in and out every step)"}
     peak, peak_kind = peaks()
-    achieved = STEP_BYTES_PER_NODE * sum(nodes) * args.steps / (ms / 1e3) / 1e9
+    floor = FLOOR_BYTES * value / ws / 1e9
+    impl = STEP_BYTES_PER_NODE * sum(nodes) * steps / (ms / 1e3) / 1e9
     groups = len({P for _, P, _ in members})
     dg.dg_batch_destroy(b)
+    return {"value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "clocks": clk,
+            "members": [f"{K}^3/P{P}/Re{int(Re)}" for K, P, Re in members], "nodes": sum(nodes),
+            "one_at_a_time": {"value": one_at_a_time, "unit": UNIT, "call": "dg_rk3_step per member"},
+            "persistent": persistent,
+            "roofline": {"bound": "hbm", "achieved": floor, "peak": peak, "unit": "GB/s", "frac": floor / peak,
+                         "peak_source": peak_kind, "bytes_per_dof_stage": FLOOR_BYTES,
+                         "kernel": "whole batched step (all launches)", "traffic": None,
+                         "implementation": {"bytes_per_dof_stage": STEP_BYTES_PER_NODE / 3, "achieved": impl,
+                                            "frac": impl / peak}},
+            "e2e": e2e, "gpu_launches": 6 * groups * steps}
+
+
+def run_batched(args, rank, ws):
+    from paper_2207_11571_gb300 import build as _build
+    from paper_2207_11571_gb300 import dg
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    dg.lib()
+    r = batched_measure(args, rank, ws, args.steps, with_clocks=True)
     if rank == 0:
-        line = {"metric": "DOF-stage updates/s (12 batched TGV instances per RK3 step)", "value": value,
+        line = {"metric": "DOF-stage updates/s (12 batched TGV instances per RK3 step)", "value": r["value"],
                 "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32 operator / f64 state",
                 "data": "synthetic (closed-form TGV fields + seeded 1e-6 perturbations)",
-                "config": {"workload": "12 independent TGV instances, (K, P, Re) drawn with seed 12 from "
-                                       "{8,12,16} x {3,6} x {30,200,1600}, Mach 0.1, one batch, graph replay",
-                           "members": [f"{K}^3/P{P}/Re{int(Re)}" for K, P, Re in members], "nodes": sum(nodes),
+                "config": {"workload": BATCH_NAME, "members": r["members"], "nodes": r["nodes"],
                            "l2": "working set ~260 B/node x 2.9M nodes > 129 MB L2 (no flush)",
                            "parallelism": f"replicas x{ws}"},
-                "one_at_a_time": {"value": one_at_a_time, "unit": UNIT, "call": "dg_rk3_step per member"},
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "peak_source": peak_kind,
-                             "kernel": "whole batched step (all launches)", "traffic": None},
-                "e2e": e2e, "gpu_launches": 6 * groups * args.steps, "clocks": clk}
+                "one_at_a_time": r["one_at_a_time"], "persistent": r["persistent"], "roofline": r["roofline"],
+                "e2e": r["e2e"],
+                "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
         print(json.dumps(line), flush=True)
     return 0
 

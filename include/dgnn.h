@@ -170,6 +170,8 @@ typedef struct {
 
 #define DG_BATCH_MAX 16
 #define DG_BATCH_NO_GRAPH 1 /* dg_batch_rk3_step flag: launch directly, no graph replay */
+#define DG_BATCH_PERSISTENT 2 /* dg_batch_rk3_step flag: one persistent launch per RK stage for every
+                                 member (FP32 operator, orders 1..6; else DG_ERR_UNSUPPORTED) */
 
 /* Creates n (1..DG_BATCH_MAX) members from desc (host array of n), all with the same
  * opts (NULL = defaults; the precision and elements-per-block apply to every member).
@@ -191,7 +193,12 @@ int dg_batch_member(dg_batch* batch, int i, dg_ctx** out);
  * parallel branches.  Unless flags has DG_BATCH_NO_GRAPH, one step is recorded as a CUDA
  * graph on the batch's private streams (the first call, and again whenever the q
  * pointers, dt values or elements-per-block change) and replayed nsteps times on stream;
- * the call must then not be made while that stream is being captured. */
+ * the call must then not be made while that stream is being captured.  With
+ * DG_BATCH_PERSISTENT each RK stage of every member, of every order, is one cooperative
+ * launch whose blocks walk the gradient phase of all members, meet at a grid barrier
+ * (a bounded wait: on expiry the first member's error flag is set, reported by its
+ * dg_diagnostics as DG_ERR_TIMEOUT) and walk the flux phase; the per-element arithmetic
+ * is that of dg_rk3_step. */
 int dg_batch_rk3_step(dg_batch* batch, double* const* q, const double* dt, int nsteps, int flags,
                       void* stream);
 

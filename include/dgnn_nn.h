@@ -66,17 +66,27 @@ int nn_compute_scalers(nn_model* net, const float* X, const float* Y, int64_t ro
  * n_out (DEVICE float).  rows <= max_batch. */
 int nn_forward(const nn_model* net, const float* X, float* S, int rows, void* stream);
 
-/* Implementation switch, no counterpart in the paper: enable != 0 runs inference
- * (nn_forward, nn_forcing_infer, forcing inside dg_rhs / dg_rk3_step) through one fused
- * kernel that keeps every layer's activations on the SM (128 rows per CTA), when every
- * width is a multiple of 16 in [16, 512] and n_hidden <= 8; 0 (the default) runs one
- * tensor-core GEMM per layer.  Both compute the same network in BF16 with FP32
- * accumulation. */
-int nn_set_fused(nn_model* net, int enable);
+/* Implementation switch of inference, no counterpart in the paper (all modes compute the
+ * same network in BF16 with FP32 accumulation):
+ *   NN_INFER_CLUSTER (the default): the forcing of a solver state (nn_forcing_infer, and
+ *     the forcing inside dg_rhs / dg_rk3_step / dg_diagnostics) runs in one launch that
+ *     forms the element features from the stage state, carries 128 elements per cluster of
+ *     1, 2 or 4 CTAs through every layer (each CTA owns a slice of every layer's output
+ *     columns and shares its activations through distributed shared memory) and writes
+ *     the unscaled forcing; it needs every width a multiple of 16 C in [16 C, 512] and
+ *     n_hidden <= 8, else (and for nn_forward) one tensor-core GEMM per layer;
+ *   NN_INFER_FUSED: nn_forward and the forcing through one fused kernel of 128 rows per
+ *     CTA that keeps every layer's activations on the SM (widths multiples of 16 in
+ *     [16, 512], n_hidden <= 8);
+ *   NN_INFER_LAYERS: one tensor-core GEMM per layer.
+ * DG_ERR_INVALID_ARG for another mode. */
+enum { NN_INFER_LAYERS = 0, NN_INFER_FUSED = 1, NN_INFER_CLUSTER = 2 };
+int nn_set_fused(nn_model* net, int mode);
 
 /* s = forcing of every element of the state q of context ctx (dgnn.h layout), written as
  * rows e = 0 .. K^3 - 1 of n_vars (P+1)^3 floats (DEVICE).  Requires n_in = n_out =
- * n_vars (P+1)^3.  Elements are processed in chunks of max_batch. */
+ * n_vars (P+1)^3.  Elements are processed in chunks of max_batch (per-layer paths) or all
+ * in one launch (NN_INFER_CLUSTER). */
 int nn_forcing_infer(const nn_model* net, const dg_ctx* ctx, const double* q, float* s, void* stream);
 
 /* One optimisation step (Sec. 2.1, "Train corrective forcing"): forward on rows idx[0..batch)

@@ -100,4 +100,13 @@ cudaError_t batch_prepare_f64(int P, int E);
 cudaError_t batch_stage_f64(int P, dg_ctx* const* ctx, double* const* q, const double* dt, int n, int k, double A,
                             double B, double invB1, cudaStream_t st);
 
+// Persistent batched RK stage (dg_batch_persist.cu, FP32 operator, orders 1..6): one
+// cooperative launch per stage for every member; bar: the grid barrier's two counters
+// (zero before the first stage of a step).  prepare sets the kernels' shared-memory
+// attribute for the orders present and returns the shared memory and co-resident grid.
+bool batch_persistent_ok(int P);
+cudaError_t batch_persistent_prepare(const int* orders, int n, size_t* smem, int* grid);
+cudaError_t batch_persistent_stage(dg_ctx* const* ctx, double* const* q, const double* dt, int n, int k, double A,
+                                   double B, double invB1, unsigned* bar, size_t smem, int grid, cudaStream_t st);
+
 }  // namespace dgnn

@@ -30,7 +30,10 @@ struct GraphKey {
   std::vector<double*> q;
   std::vector<double> dt;
   std::vector<int> E;
-  bool operator==(const GraphKey& o) const { return q == o.q && dt == o.dt && E == o.E; }
+  int persistent = 0;
+  bool operator==(const GraphKey& o) const {
+    return q == o.q && dt == o.dt && E == o.E && persistent == o.persistent;
+  }
 };
 
 }  // namespace
@@ -45,6 +48,7 @@ struct dg_batch {
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t exec = nullptr;
   dgnn::GraphKey key;
+  unsigned* bar = nullptr;           // grid barrier of the persistent stage kernel (2 counters)
 };
 
 namespace dgnn {
@@ -87,9 +91,40 @@ cudaError_t step_direct(const dg_batch* b, double* const* q, const double* dt, c
   return cudaSuccess;
 }
 
+// One RK3 step of every member as three persistent launches (one per stage, every order
+// together), after a reset of the grid barrier's counters.
+cudaError_t step_persistent(const dg_batch* b, double* const* q, const double* dt, size_t smem, int grid,
+                            cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), st);
+  const int n = (int)b->inst.size();
+  const double invB1 = 1.0 / kB[0];
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+    e = batch_persistent_stage(b->inst.data(), q, dt, n, k, kA[k], kB[k], invB1, b->bar, smem, grid, st);
+  return e;
+}
+
+int prepare_persistent(const dg_batch* b, size_t* smem, int* grid) {
+  if (b->precision != DG_PREC_FP32)
+    return fail(DG_ERR_UNSUPPORTED, "dg_batch_rk3_step: the persistent stage kernel runs the FP32 operator");
+  std::vector<int> orders;
+  for (const dg_ctx* c : b->inst) {
+    if (!batch_persistent_ok(c->P))
+      return fail(DG_ERR_UNSUPPORTED, "dg_batch_rk3_step: the persistent stage kernel takes orders 1 to 6");
+    orders.push_back(c->P);
+  }
+  DG_CUDA(batch_persistent_prepare(orders.data(), (int)orders.size(), smem, grid));
+  return DG_OK;
+}
+
 // Records one step with the groups as parallel branches: fork from cap[0], each group on
-// its own stream, join back into cap[0].
-int record_step(dg_batch* b, double* const* q, const double* dt) {
+// its own stream, join back into cap[0].  persistent: three cooperative launches on cap[0].
+int record_step(dg_batch* b, double* const* q, const double* dt, bool persistent) {
+  size_t psmem = 0;
+  int pgrid = 0;
+  if (persistent) {
+    int rc = prepare_persistent(b, &psmem, &pgrid);
+    if (rc) return rc;
+  }
   // kernel attributes (dynamic shared memory) are set outside the recording
   cudaError_t ea = prepare_groups(b);
   if (ea != cudaSuccess) return cuda_fail(ea, "dg_batch_rk3_step: kernel attributes");
@@ -100,7 +135,8 @@ int record_step(dg_batch* b, double* const* q, const double* dt) {
   cudaStream_t s0 = b->cap[0];
   DG_CUDA(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaEventRecord(b->fork, s0);
-  for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+  if (persistent && e == cudaSuccess) e = step_persistent(b, q, dt, psmem, pgrid, s0);
+  for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess && !persistent; ++gi) {
     cudaStream_t s = b->cap[gi];
     if (gi > 0) e = cudaStreamWaitEvent(s, b->fork, 0);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = stage_group(b, b->groups[gi], q, dt, k, s);
@@ -120,8 +156,9 @@ int record_step(dg_batch* b, double* const* q, const double* dt) {
   return DG_OK;
 }
 
-GraphKey key_of(const dg_batch* b, double* const* q, const double* dt) {
+GraphKey key_of(const dg_batch* b, double* const* q, const double* dt, bool persistent) {
   GraphKey k;
+  k.persistent = persistent;
   const size_t n = b->inst.size();
   k.q.assign(q, q + n);
   k.dt.assign(dt, dt + n);
@@ -144,6 +181,7 @@ int dg_batch_destroy(dg_batch* b) {
   for (cudaEvent_t e : b->join)
     if (e) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
+  if (b->bar) cudaFree(b->bar);
   for (dg_ctx* c : b->inst) {
     c->borrowed = false;
     dg_destroy(c);
@@ -197,9 +235,11 @@ int dg_create_batch(const dg_instance_desc* desc, int n, const dg_opts* opts, dg
     e = cudaStreamCreateWithFlags(&b->cap[gi], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[gi], cudaEventDisableTiming);
   }
+  if (e == cudaSuccess) e = cudaMalloc(&b->bar, 2 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(b->bar, 0, 2 * sizeof(unsigned));
   if (e != cudaSuccess) {
     dg_batch_destroy(b);
-    return cuda_fail(e, "dg_create_batch: streams and events");
+    return cuda_fail(e, "dg_create_batch: streams, events and barrier");
   }
   *out = b;
   return DG_OK;
@@ -221,7 +261,9 @@ int dg_batch_member(dg_batch* b, int i, dg_ctx** out) {
 int dg_batch_rk3_step(dg_batch* b, double* const* q, const double* dt, int nsteps, int flags, void* stream) {
   if (!b || !q || !dt) return fail(DG_ERR_INVALID_ARG, "dg_batch_rk3_step: NULL argument");
   if (nsteps < 0) return fail(DG_ERR_INVALID_ARG, "dg_batch_rk3_step: nsteps < 0");
-  if (flags & ~DG_BATCH_NO_GRAPH) return fail(DG_ERR_INVALID_ARG, "dg_batch_rk3_step: unknown flags");
+  if (flags & ~(DG_BATCH_NO_GRAPH | DG_BATCH_PERSISTENT))
+    return fail(DG_ERR_INVALID_ARG, "dg_batch_rk3_step: unknown flags");
+  const bool persistent = (flags & DG_BATCH_PERSISTENT) != 0;
   for (size_t i = 0; i < b->inst.size(); ++i) {
     if (!q[i]) return fail(DG_ERR_INVALID_ARG, "dg_batch_rk3_step: NULL member state");
     if (!std::isfinite(dt[i])) return fail(DG_ERR_INVALID_ARG, "dg_batch_rk3_step: non-finite dt");
@@ -230,13 +272,21 @@ int dg_batch_rk3_step(dg_batch* b, double* const* q, const double* dt, int nstep
   }
   cudaStream_t st = (cudaStream_t)stream;
   if (flags & DG_BATCH_NO_GRAPH) {
+    if (persistent) {
+      size_t smem = 0;
+      int grid = 0;
+      int rc = prepare_persistent(b, &smem, &grid);
+      if (rc) return rc;
+      for (int s = 0; s < nsteps; ++s) DG_CUDA(step_persistent(b, q, dt, smem, grid, st));
+      return DG_OK;
+    }
     for (int s = 0; s < nsteps; ++s) DG_CUDA(step_direct(b, q, dt, st));
     return DG_OK;
   }
   if (nsteps == 0) return DG_OK;
-  GraphKey k = key_of(b, q, dt);
+  GraphKey k = key_of(b, q, dt, persistent);
   if (!b->exec || !(k == b->key)) {
-    int rc = record_step(b, q, dt);
+    int rc = record_step(b, q, dt, persistent);
     if (rc) return rc;
     b->key = k;
   }

@@ -12,6 +12,7 @@
 #include "dg_common.h"
 #include "dg_device.cuh"
 #include "nn_bridge.h"
+#include "nn_forcing.h"
 #include "nn_gemm.h"
 #include "nn_mlp.h"
 
@@ -45,7 +46,7 @@ struct nn_model {
   double* loss_host = nullptr;  // pinned
   int* err = nullptr;           // device error flag of the tensor-core kernels
   int maxdim = 0;
-  bool fused = false;           // inference through the fused multi-layer kernel (nn_set_fused)
+  int fused = NN_INFER_CLUSTER; // inference path (nn_set_fused)
   // input means for scaling network inputs taken from solver states: in FP64 (FP64 state)
   // and shifted by the reference state of an FP32 context (cached for one reference)
   double* mean_in_d = nullptr;
@@ -353,7 +354,7 @@ cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream
 // Forward through all layers for `rows` rows whose scaled inputs are in act[0].
 // last: if S != null, unscaled forcing into S (ld n_out); else scaled output into m->y.
 int forward_layers(const nn_model* m, int rows, float* S, cudaStream_t st) {
-  if (S && m->fused && mlp_fused_ok(m->dims, m->L)) {
+  if (S && m->fused == NN_INFER_FUSED && mlp_fused_ok(m->dims, m->L)) {
     // inference: all layers in one kernel, activations kept on the SM
     const bf16* W[kMlpMaxLayers];
     const float* B[kMlpMaxLayers];
@@ -518,13 +519,24 @@ int nn_forcing_on_state(const nn_model* m, const dg_ctx* c, const double* q, flo
   const int feat = m->d.n_vars * c->np;
   if (m->d.n_in != feat || m->d.n_out != feat)
     return fail(DG_ERR_INVALID_ARG, "forcing: network features do not match n_vars (P+1)^3 of the context");
+  const bool f32 = c->opts.precision == DG_PREC_FP32;
+  if (f32) {
+    // the stage state of the FP32 operator is the reference-shifted copy written by phase A
+    int rc = ensure_shift(const_cast<nn_model*>(m), c);
+    if (rc) return rc;
+  }
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    DG_CUDA(cudaGetDevice(&dev));
+    DG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  // the one-launch network path writes the forcing rows as 16-byte vectors
+  const bool aligned = (reinterpret_cast<uintptr_t>(s) & 15) == 0;
   for (int e0 = 0; e0 < c->nel; e0 += m->d.max_batch) {
     const int rows = std::min(m->d.max_batch, c->nel - e0);
     const long long tot = (long long)rows * m->pad[0];
-    if (c->opts.precision == DG_PREC_FP32) {
-      // the stage state of the FP32 operator is the reference-shifted copy written by phase A
-      int rc = ensure_shift(const_cast<nn_model*>(m), c);
-      if (rc) return rc;
+    if (f32) {
       DG_CUDA(pdl_launch(k_prep_state_f32, dim3(blocks_for(tot, 256)), dim3(256), st, static_cast<const float*>(c->qf), c->N, c->np,
                                                              m->d.first_var, m->d.n_vars, e0, rows, m->pad[0],
                                                              m->mean_shift, m->std_in, m->act[0]));
@@ -533,8 +545,30 @@ int nn_forcing_on_state(const nn_model* m, const dg_ctx* c, const double* q, flo
                                                          m->pad[0], m->mean_in_d, m->std_in, m->act[0]));
     }
     DG_CUDA(cudaGetLastError());
-    int rc = forward_layers(m, rows, s + (long long)e0 * feat, st);
-    if (rc) return rc;
+    const int C = (m->fused == NN_INFER_CLUSTER && aligned) ? forcing_cluster_size(m->dims, m->L, rows, sms) : 0;
+    if (C > 0) {
+      // every layer in one launch: clusters of C CTAs share the activations on chip
+      ForcingLaunch f;
+      f.act0 = m->act[0];
+      f.ld0 = m->pad[0];
+      f.Wb = m->Wb;
+      f.ldw = m->pad;
+      f.bias = m->b;
+      f.dims = m->dims;
+      f.L = m->L;
+      f.rows = rows;
+      f.csize = C;
+      f.scale = m->std_out;
+      f.shift = m->mean_out;
+      f.out = s + (long long)e0 * feat;
+      f.ldo = feat;
+      f.err = m->err;
+      int rc = forcing_fused(f, st);
+      if (rc) return rc;
+    } else {
+      int rc = forward_layers(m, rows, s + (long long)e0 * feat, st);
+      if (rc) return rc;
+    }
   }
   if (first_var) *first_var = m->d.first_var;
   if (n_vars) *n_vars = m->d.n_vars;
@@ -648,9 +682,11 @@ int nn_compute_scalers(nn_model* m, const float* X, const float* Y, int64_t rows
   return means_changed(m);
 }
 
-int nn_set_fused(nn_model* m, int enable) {
+int nn_set_fused(nn_model* m, int mode) {
   if (!m) return fail(DG_ERR_INVALID_ARG, "nn_set_fused: NULL model");
-  m->fused = enable != 0;
+  if (mode != NN_INFER_LAYERS && mode != NN_INFER_FUSED && mode != NN_INFER_CLUSTER)
+    return fail(DG_ERR_INVALID_ARG, "nn_set_fused: unknown mode");
+  m->fused = mode;
   return DG_OK;
 }
 
@@ -870,10 +906,13 @@ uint64_t fnv1a(const unsigned char* p, size_t n) {
 
 const char kMagic[8] = {'D', 'G', 'N', 'N', 'N', 'E', 'T', '1'};
 
-std::vector<float> to_host(const float* d, size_t n) {
+// Appends n device floats to the blob; false (with the CUDA error in *err) if the copy fails.
+bool put_device(Blob& b, const float* d, size_t n, cudaError_t* err) {
   std::vector<float> h(n);
-  cudaMemcpy(h.data(), d, n * 4, cudaMemcpyDeviceToHost);
-  return h;
+  *err = cudaMemcpy(h.data(), d, n * 4, cudaMemcpyDeviceToHost);
+  if (*err != cudaSuccess) return false;
+  b.put(h.data(), n * 4);
+  return true;
 }
 
 }  // namespace
@@ -886,13 +925,17 @@ extern "C" int nn_save(const nn_model* m, const char* path) {
   b.put(&version, 4);
   b.put(&m->d, sizeof(nn_desc));
   b.put(&m->adam_t, 4);
-  for (const float* p : {m->mean_in, m->std_in}) b.put(to_host(p, m->d.n_in).data(), m->d.n_in * 4);
-  for (const float* p : {m->mean_out, m->std_out}) b.put(to_host(p, m->d.n_out).data(), m->d.n_out * 4);
-  for (int l = 0; l < m->L; ++l) {
+  // every device copy is checked: a failed copy must not be written under a valid checksum
+  cudaError_t ce = cudaSuccess;
+  bool copied = true;
+  for (const float* p : {m->mean_in, m->std_in}) copied = copied && put_device(b, p, m->d.n_in, &ce);
+  for (const float* p : {m->mean_out, m->std_out}) copied = copied && put_device(b, p, m->d.n_out, &ce);
+  for (int l = 0; copied && l < m->L; ++l) {
     const size_t w = (size_t)m->dims[l] * m->dims[l + 1], o = m->dims[l + 1];
-    for (const float* p : {m->W[l], m->mW[l], m->vW[l]}) b.put(to_host(p, w).data(), w * 4);
-    for (const float* p : {m->b[l], m->mb[l], m->vb[l]}) b.put(to_host(p, o).data(), o * 4);
+    for (const float* p : {m->W[l], m->mW[l], m->vW[l]}) copied = copied && put_device(b, p, w, &ce);
+    for (const float* p : {m->b[l], m->mb[l], m->vb[l]}) copied = copied && put_device(b, p, o, &ce);
   }
+  if (!copied) return cuda_fail(ce, "nn_save: device-to-host copy (no file written)");
   const uint64_t h = fnv1a(b.bytes.data(), b.bytes.size());
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(DG_ERR_IO, std::string("nn_save: cannot open ") + path);

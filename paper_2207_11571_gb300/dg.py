@@ -55,6 +55,7 @@ class dg_instance_desc(ctypes.Structure):
 
 DG_BATCH_MAX = 16
 DG_BATCH_NO_GRAPH = 1
+DG_BATCH_PERSISTENT = 2
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int

@@ -134,10 +134,17 @@ def nn_forward(net, X, S, stream=None):
     dg.check(dg.lib().nn_forward(_h(net), dg.ptr(X), dg.ptr(S), rows, dg.stream_ptr(stream)))
 
 
-def nn_set_fused(net, enable=True):
-    """Inference through the fused multi-layer kernel (default) or one GEMM per layer."""
+NN_INFER_LAYERS, NN_INFER_FUSED, NN_INFER_CLUSTER = 0, 1, 2
+
+
+def nn_set_fused(net, mode=NN_INFER_FUSED):
+    """Inference path: NN_INFER_CLUSTER (the default: the forcing of a solver state in one
+    cluster launch), NN_INFER_FUSED (one fused kernel of 128 rows per CTA) or
+    NN_INFER_LAYERS (one GEMM per layer).  True / False select FUSED / LAYERS."""
+    if mode is True or mode is False:
+        mode = NN_INFER_FUSED if mode else NN_INFER_LAYERS
     dg = _dg()
-    dg.check(dg.lib().nn_set_fused(_h(net), int(bool(enable))))
+    dg.check(dg.lib().nn_set_fused(_h(net), int(mode)))
 
 
 def nn_forcing_infer(net, ctx, q, s, stream=None):

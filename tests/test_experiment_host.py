@@ -30,11 +30,12 @@ def test_run_errors_of_a_diverged_run_are_infinite_and_exact_run_is_zero():
     t = np.linspace(0.0, 1.0, 11)
     ke = 0.125 * np.exp(-t)
     dke = -0.125 * np.exp(-t)
-    same = types.SimpleNamespace(diverged_at=None, dke=dke, ke=ke)
+    einf = [0.5 * (i + 1) for i in range(11)]   # e_n samples: their mean is the einf error
+    same = types.SimpleNamespace(diverged_at=None, dke=dke, ke=ke, einf=einf)
     e = experiment.run_errors(same, t, dke, ke, ke)
-    assert e == {"dke": 0.0, "ke": 0.0, "dke_filtered": 0.0}
-    gone = types.SimpleNamespace(diverged_at=0.3, dke=dke, ke=ke)
+    assert e == {"dke": 0.0, "ke": 0.0, "dke_filtered": 0.0, "einf": 3.0}
+    gone = types.SimpleNamespace(diverged_at=0.3, dke=dke, ke=ke, einf=einf)
     assert all(math.isinf(v) for v in experiment.run_errors(gone, t, dke, ke, ke).values())
     # a 1 % uniform error in the dissipation history is a 1 % relative L2 error
-    off = types.SimpleNamespace(diverged_at=None, dke=1.01 * dke, ke=ke)
+    off = types.SimpleNamespace(diverged_at=None, dke=1.01 * dke, ke=ke, einf=einf)
     assert experiment.run_errors(off, t, dke, ke, ke)["dke"] == pytest.approx(0.01, rel=1e-12)

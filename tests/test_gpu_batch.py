@@ -145,3 +145,52 @@ def test_batch_rejects_shared_states(dg):
         assert e.value.status == dg.DG_ERR_INVALID_ARG
     finally:
         dg.dg_batch_destroy(b)
+
+
+def test_persistent_stage_launch_equals_members_advanced_alone(dg):
+    """DG_BATCH_PERSISTENT: each RK stage of every member (orders 3, 4 and 6 together) is
+    one cooperative launch with a grid barrier between the gradient and flux phases.  The
+    per-element arithmetic is the single-mesh kernels', so the members come out as if
+    advanced alone by dg_rk3_step, within a rounding of the increments (the streamed
+    high-order kernel and the row kernel may contract a multiply-add differently); graph
+    replay equals direct launches bitwise."""
+    b = dg.dg_create_batch(MEMBERS, precision=1)
+    try:
+        qs = init_states(dg, b, MEMBERS)
+        dts = [dg.dg_stable_dt(dg.dg_batch_member(b, i), q, 0.7) for i, q in enumerate(qs)]
+        ref = alone(dg, b, qs, dts, 3)
+        graph = [q.clone() for q in qs]
+        dg.dg_batch_rk3_step(b, graph, dts, 3, flags=dg.DG_BATCH_PERSISTENT)
+        direct = [q.clone() for q in qs]
+        dg.dg_batch_rk3_step(b, direct, dts, 3, flags=dg.DG_BATCH_PERSISTENT | dg.DG_BATCH_NO_GRAPH)
+        torch.cuda.synchronize()
+        for i in range(len(MEMBERS)):
+            assert torch.isfinite(graph[i]).all(), i
+            assert torch.equal(graph[i], direct[i]), i
+            incr = (ref[i] - qs[i]).abs().max().item()
+            d = (graph[i] - ref[i]).abs().max().item()
+            assert d <= 1e-5 * incr, (i, d, incr)
+        for i in range(len(MEMBERS)):   # the barrier's error flag stayed clear
+            dg.dg_diagnostics(dg.dg_batch_member(b, i), graph[i])
+    finally:
+        dg.dg_batch_destroy(b)
+
+
+def test_persistent_stage_launch_refuses_what_it_does_not_run(dg):
+    b = dg.dg_create_batch(MEMBERS[:2], precision=0)          # FP64 operator
+    try:
+        qs = init_states(dg, b, MEMBERS[:2])
+        with pytest.raises(dg.DGError) as e:
+            dg.dg_batch_rk3_step(b, qs, [1e-3, 1e-3], 1, flags=dg.DG_BATCH_PERSISTENT)
+        assert e.value.status == dg.DG_ERR_UNSUPPORTED
+    finally:
+        dg.dg_batch_destroy(b)
+    members = [(2, 8, 200.0, 0.1, 0.71, 0), (2, 3, 200.0, 0.1, 0.71, 0)]
+    b = dg.dg_create_batch(members, precision=1)              # order 8
+    try:
+        qs = init_states(dg, b, members)
+        with pytest.raises(dg.DGError) as e:
+            dg.dg_batch_rk3_step(b, qs, [1e-3, 1e-3], 1, flags=dg.DG_BATCH_PERSISTENT)
+        assert e.value.status == dg.DG_ERR_UNSUPPORTED
+    finally:
+        dg.dg_batch_destroy(b)

@@ -205,10 +205,12 @@ def test_compute_scalers_matches_numpy(L):
     nn.nn_destroy(h)
 
 
+@pytest.mark.parametrize("mode", [0, 2])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_forcing_infer_matches_oracle_on_element_features(L, prec):
-    """Network forcing of every element of a solver state (chunks of max_batch) against the
-    oracle network on the FP64 element features (bf16 rounding points)."""
+def test_forcing_infer_matches_oracle_on_element_features(L, prec, mode):
+    """Network forcing of every element of a solver state (per-layer GEMMs in chunks of
+    max_batch, or the one-launch cluster kernel) against the oracle network on the FP64
+    element features (bf16 rounding points)."""
     from paper_2207_11571_gb300 import dg, nn
     K, P = 3, 3
     ctx = dg.dg_create(K, P, 1600.0, 0.1, 0.71, 0, precision=prec)
@@ -220,10 +222,47 @@ def test_forcing_infer_matches_oracle_on_element_features(L, prec):
     sc32 = (feats.mean(0).astype(np.float32), (feats.std(0) + 1e-3).astype(np.float32),
             np.zeros(320, np.float32), np.full(320, 0.01, np.float32))
     nn.nn_set_scalers(h, *sc32)
+    nn.nn_set_fused(h, mode)
     s = torch.empty(K ** 3 * 320, dtype=torch.float32, device="cuda")
     nn.nn_forcing_infer(h, ctx, q, s)
     ref = mlp.infer(params, tuple(a.astype(np.float64) for a in sc32), feats, bf16=True)
     assert rel(s.cpu().numpy().reshape(27, 320), ref) < NN_RTOL
+    nn.nn_destroy(h)
+    dg.dg_destroy(ctx)
+
+
+# (K, P, n_vars, width, hidden, precision): 64 elements (one tile), 125 (a ragged tile),
+# 216 (two tiles, ragged), 512 (four tiles); momentum-only I/O (192 features); the
+# benchmark network on 16^3 elements (4096, 32 clusters of 4 CTAs)
+CLUSTER_CASES = [(4, 3, 5, 256, 2, 1), (5, 3, 5, 512, 4, 0), (6, 3, 3, 256, 3, 1), (8, 3, 5, 512, 4, 1),
+                 (8, 3, 3, 512, 6, 0), (16, 3, 5, 512, 4, 1)]
+
+
+@pytest.mark.parametrize("K,P,nv,width,hidden,prec", CLUSTER_CASES)
+def test_cluster_forcing_equals_per_layer_gemms(L, K, P, nv, width, hidden, prec):
+    """The one-launch forcing (features, every layer and the unscaling in clusters of CTAs
+    that share activations through distributed shared memory) computes what the per-layer
+    path computes: the same bf16 features and weights, FP32 accumulation; only the
+    accumulation order inside the tensor core may differ."""
+    from paper_2207_11571_gb300 import dg, nn
+    ctx = dg.dg_create(K, P, 1600.0, 0.1, 0.71, 0, precision=prec)
+    N = dg.dg_sizes(ctx)[0]
+    first = 0 if nv == 5 else 1
+    feat = nv * (P + 1) ** 3
+    q = torch.empty(5 * N, dtype=torch.float64, device="cuda")
+    dg.dg_init_tgv(ctx, q, torch.from_numpy(inputs.perturbation((5, N), eps=1e-3).ravel()).cuda())
+    h, _ = make_net(nn, feat, width, hidden, seed=40 + K, max_batch=512, first_var=first, n_vars=nv)
+    set_random_scalers(nn, h, feat, 6)
+    out = {}
+    for mode in (0, 2):
+        nn.nn_set_fused(h, mode)
+        s = torch.full((K ** 3 * feat,), float("nan"), dtype=torch.float32, device="cuda")
+        nn.nn_forcing_infer(h, ctx, q, s)
+        torch.cuda.synchronize()
+        out[mode] = s
+    assert torch.isfinite(out[2]).all()
+    err = ((out[2] - out[0]).norm() / out[0].norm()).item()
+    assert err < 1e-5, err
     nn.nn_destroy(h)
     dg.dg_destroy(ctx)
 
@@ -322,6 +361,59 @@ def test_rk3_with_post_step_forcing_matches_oracle(L):
     assert np.linalg.norm(got[1:4] - stage[1:4]) < 0.05 * np.linalg.norm(ref[1:4] - plain[1:4])
     nn.nn_destroy(h)
     dg.dg_destroy(ctx)
+
+
+def test_training_resumes_after_save_and_load_with_the_adam_state(L, tmp_path):
+    """Transfer learning warm-starts from a saved network (Sec. 3.6): nn_save keeps the
+    weights, scalers, Adam moments m, v and step count t, so the first step after nn_load
+    is the step the saved network would have taken.  Checked against the oracle's Adam
+    with the restored t = 2, m, v (accumulated from the library's own gradients of the two
+    steps before the save); a restart from zero moments would move the weights by lr
+    sign(g) instead, which the bound separates."""
+    from paper_2207_11571_gb300 import nn
+    n, width, nh, B = 192, 128, 2, 256
+    h, _ = make_net(nn, n, width, nh, seed=31, max_batch=B, first_var=1, n_vars=3)
+    set_random_scalers(nn, h, n, 4)
+    X = inputs.normal((600, n), 13).astype(np.float32)
+    Y = (0.3 * inputs.normal((600, n), 14)).astype(np.float32)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+    idx = [torch.from_numpy(np.random.default_rng(s).permutation(600)[:B].astype(np.int64)).cuda() for s in (1, 2, 3)]
+    layers = range(nh + 1)
+
+    def params_of(net):
+        return [tuple(a.astype(np.float64) for a in nn.nn_get_params(net, l)) for l in layers]
+
+    def grads_of(net):
+        return [tuple(a.astype(np.float64) for a in nn.nn_get_grads(net, l)) for l in layers]
+
+    state = {}
+    for k in range(2):
+        before = params_of(h)
+        nn.nn_train_step(h, Xd, Yd, idx[k], lr=1e-3)
+        mlp.adam_step(before, grads_of(h), state, lr=1e-3, eps=1e-7)
+    assert state["t"] == 2
+    path = tmp_path / "net.bin"
+    nn.nn_save(h, path)
+    h2 = nn.nn_load(path, max_batch=B)
+    before = params_of(h2)
+    nn.nn_train_step(h2, Xd, Yd, idx[2], lr=1e-3)
+    g3 = grads_of(h2)
+    fresh = mlp.adam_step(before, g3, {}, lr=1e-3, eps=1e-7)
+    want = mlp.adam_step(before, g3, state, lr=1e-3, eps=1e-7)
+    sep = 0.0
+    for l in layers:
+        W, b = nn.nn_get_params(h2, l)
+        np.testing.assert_allclose(W, want[l][0], rtol=0, atol=2e-6 * max(1.0, np.abs(W).max()))
+        np.testing.assert_allclose(b, want[l][1], rtol=0, atol=2e-6)
+        sep = max(sep, np.abs(fresh[l][0] - want[l][0]).max())
+    assert sep > 1e-4, sep   # the check would see lost moments
+    # the saved network itself takes the same step
+    nn.nn_train_step(h, Xd, Yd, idx[2], lr=1e-3)
+    for l in layers:
+        for a, b in zip(nn.nn_get_params(h, l), nn.nn_get_params(h2, l)):
+            np.testing.assert_array_equal(a, b)
+    nn.nn_destroy(h)
+    nn.nn_destroy(h2)
 
 
 def test_save_load_roundtrip_and_corruption_detection(L, tmp_path):
