@@ -83,12 +83,14 @@ static void stage_bytes(const dg_ctx* c, int k, double* grad, double* flux) {
   }
 }
 
-// Evaluates the network forcing on the current state q (all elements) into c->s_buf.
-static int forcing_for(dg_ctx* c, const double* q, const nn_model* net, Forcing* f, cudaStream_t st) {
+// Evaluates the network forcing on the current state q (all elements) into c->s_buf;
+// features_ready: the phase-A launch before it wrote the network's input features.
+static int forcing_for(dg_ctx* c, const double* q, const nn_model* net, Forcing* f, cudaStream_t st,
+                       bool features_ready = false) {
   *f = Forcing{};
   if (!net) return DG_OK;
   int first = 0, nv = 0;
-  int rc = nn_forcing_on_state(net, c, q, c->s_buf, &first, &nv, st);
+  int rc = nn_forcing_on_state(net, c, q, c->s_buf, &first, &nv, st, features_ready);
   if (rc) return rc;
   f->s = c->s_buf;
   f->first_var = first;
@@ -132,10 +134,15 @@ static int rhs_into_n(dg_ctx* const* cs, int n, double* const* qs, double* const
                       cudaStream_t st) {
   int rc = exchange_traces(cs, n, qs, phase_a_what(cs[0], 0), st);
   if (rc) return rc;
-  for (int i = 0; i < n; ++i) DG_CUDA(launch_gradient(cs[i], qs[i], 0, st));
+  const bool feats = n == 1 && net && nn_phase_a_features(net, cs[0], &cs[0]->feat_out);
+  for (int i = 0; i < n; ++i) {
+    const cudaError_t e = launch_gradient(cs[i], qs[i], 0, st);
+    cs[i]->feat_out = FeatureOut{};
+    DG_CUDA(e);
+  }
   Forcing f;
   if (n == 1) {
-    rc = forcing_for(cs[0], qs[0], net, &f, st);
+    rc = forcing_for(cs[0], qs[0], net, &f, st, feats);
     if (rc) return rc;
   }
   rc = exchange_traces(cs, n, qs, kWhatPhaseB, st);
@@ -165,10 +172,17 @@ static int rk3_steps_n(dg_ctx* const* cs, int n, double* const* qs, double dt, i
       stage_plan(c, k, &src, &mode);
       int rc = exchange ? exchange_traces(cs, n, qs, phase_a_what(c, src), st) : DG_OK;
       if (rc) return rc;
-      for (int i = 0; i < n; ++i) DG_CUDA(launch_gradient(cs[i], qs[i], src, st));
+      // the forcing's input features come out of the phase-A launch when the network allows
+      const bool want = net && (!post || k == 0);
+      const bool feats = want && n == 1 && nn_phase_a_features(net, c, &c->feat_out);
+      for (int i = 0; i < n; ++i) {
+        const cudaError_t e = launch_gradient(cs[i], qs[i], src, st);
+        cs[i]->feat_out = FeatureOut{};
+        DG_CUDA(e);
+      }
       Forcing f;
-      if (!post || k == 0) {
-        rc = forcing_for(c, qs[0], net, &f, st);
+      if (want) {
+        rc = forcing_for(c, qs[0], net, &f, st, feats);
         if (rc) return rc;
       }
       if (post) {

@@ -68,6 +68,21 @@ struct Phys {
   double theta_ref;  // p_ref / rho_ref
 };
 
+// Network features that a phase-A launch writes besides its outputs (Sec. 2.2: the
+// element's scaled state): out[e * ld + slot * n^3 + node] = bf16((s_v - mean_f) / sd_f)
+// for v = first_var + slot, from the stage state s the launch forms; mean_f is taken
+// relative to the operator's reference state (shift32, FP32 operator) or as is (mean64,
+// FP64 operator).  out == nullptr: none.
+struct FeatureOut {
+  void* out = nullptr;   // bf16
+  int ld = 0;
+  int first_var = 0;
+  int n_vars = 0;
+  const float* shift32 = nullptr;
+  const double* mean64 = nullptr;
+  const float* sd = nullptr;
+};
+
 // Optional forcing source added to the operator: s[e * stride + slot * n^3 + node]
 // for variables first_var .. first_var + n_vars - 1.
 struct Forcing {
@@ -117,6 +132,7 @@ struct dg_ctx {
   bool host_diag_pending = false;  // dg_advance_host_async enqueued diagnostics not yet collected
   int forcing_mode = DG_FORCING_STAGE;  // where dg_rk3_step applies a network forcing
   float* s_buf = nullptr;      // forcing buffer [nel][5 n^3]
+  dgnn::FeatureOut feat_out;   // features the next phase-A launch also writes (set per launch)
   double* filter_dev[dgnn::kMaxP + 1] = {};  // filter G to each lower order (dg_project)
   double* prolong_dev[dgnn::kMaxP + 1] = {};  // interpolation to each higher order (dg_prolong)
   bool borrowed = false;       // member of a dg_batch: released by dg_batch_destroy only

@@ -30,6 +30,8 @@
 // node except where the FP64 state is read or written.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <type_traits>
 
 #include "dg_device.cuh"
@@ -65,6 +67,7 @@ struct OpConst {
   T mu, lam, csd2, lam_t;         // transport
   int les;
   double drho_ref, dE_ref;        // references for shifting the FP64 state
+  FeatureOut feat;                // network features written by phase A (feat.out may be NULL)
   T D[kMaxN1 * kMaxN1];
 };
 
@@ -325,6 +328,21 @@ __device__ __forceinline__ void gradient_block(int blk, const double* __restrict
     if (SRC == 0 && qn32_out != nullptr) {
 #pragma unroll
       for (int v = 0; v < 5; ++v) qn32_out[v * N + gi] = float(s[v]);
+    }
+    if (C.feat.out != nullptr) {
+      // the forcing network's input features of this node, from the stage state just
+      // formed: the same arithmetic as the separate feature kernels of the network
+      __nv_bfloat16* fo = static_cast<__nv_bfloat16*>(C.feat.out) + (long long)e * C.feat.ld + node;
+#pragma unroll
+      for (int v = 0; v < 5; ++v) {
+        const int slot = v - C.feat.first_var;
+        if (slot < 0 || slot >= C.feat.n_vars) continue;
+        const int f = slot * np + node;
+        float x;
+        if constexpr (sizeof(T) == 4) x = (float(s[v]) - C.feat.shift32[f]) / C.feat.sd[f];
+        else x = d2f_rn(double(s[v]) - C.feat.mean64[f]) / C.feat.sd[f];
+        fo[slot * np] = __float2bfloat16_rn(x);
+      }
     }
     w = prim_c(s, C);
     gradient_vars(s, w, C.theta_ref, U);

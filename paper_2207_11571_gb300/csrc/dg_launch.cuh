@@ -48,6 +48,7 @@ OpConst<T> make_const(const dg_ctx* c) {
   k.les = ph.les;
   k.drho_ref = ph.rho_ref;
   k.dE_ref = ph.E_ref;
+  k.feat = c->feat_out;
   for (int i = 0; i < kMaxN1 * kMaxN1; ++i) k.D[i] = T(c->geom.D[i]);
   return k;
 }

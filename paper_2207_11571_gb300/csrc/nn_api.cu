@@ -513,8 +513,33 @@ int refresh_bf16(nn_model* m, int l, cudaStream_t st) {
 
 }  // namespace
 
+static int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 0;
+  }
+  return sms;
+}
+
+bool nn_phase_a_features(const nn_model* m, const dg_ctx* c, FeatureOut* out) {
+  const int feat = m->d.n_vars * c->np;
+  if (m->fused != NN_INFER_CLUSTER || c->nel > m->d.max_batch || m->d.n_in != feat || feat != m->pad[0]) return false;
+  if (forcing_cluster_size(m->dims, m->L, c->nel, sm_count()) <= 0) return false;
+  if (c->opts.precision == DG_PREC_FP32 && ensure_shift(const_cast<nn_model*>(m), c) != DG_OK) return false;
+  out->out = m->act[0];
+  out->ld = m->pad[0];
+  out->first_var = m->d.first_var;
+  out->n_vars = m->d.n_vars;
+  out->shift32 = m->mean_shift;
+  out->mean64 = m->mean_in_d;
+  out->sd = m->std_in;
+  return true;
+}
+
 int nn_forcing_on_state(const nn_model* m, const dg_ctx* c, const double* q, float* s, int* first_var, int* n_vars,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool features_ready) {
   if (!m || !c || !q || !s) return fail(DG_ERR_INVALID_ARG, "forcing: NULL argument");
   const int feat = m->d.n_vars * c->np;
   if (m->d.n_in != feat || m->d.n_out != feat)
@@ -525,18 +550,15 @@ int nn_forcing_on_state(const nn_model* m, const dg_ctx* c, const double* q, flo
     int rc = ensure_shift(const_cast<nn_model*>(m), c);
     if (rc) return rc;
   }
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    DG_CUDA(cudaGetDevice(&dev));
-    DG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
+  const int sms = sm_count();
   // the one-launch network path writes the forcing rows as 16-byte vectors
   const bool aligned = (reinterpret_cast<uintptr_t>(s) & 15) == 0;
   for (int e0 = 0; e0 < c->nel; e0 += m->d.max_batch) {
     const int rows = std::min(m->d.max_batch, c->nel - e0);
     const long long tot = (long long)rows * m->pad[0];
-    if (f32) {
+    if (features_ready && rows == c->nel) {
+      // the phase-A launch before this call wrote the features (nn_phase_a_features)
+    } else if (f32) {
       DG_CUDA(pdl_launch(k_prep_state_f32, dim3(blocks_for(tot, 256)), dim3(256), st, static_cast<const float*>(c->qf), c->N, c->np,
                                                              m->d.first_var, m->d.n_vars, e0, rows, m->pad[0],
                                                              m->mean_shift, m->std_in, m->act[0]));

@@ -267,6 +267,36 @@ def test_cluster_forcing_equals_per_layer_gemms(L, K, P, nv, width, hidden, prec
     dg.dg_destroy(ctx)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_corrected_rk3_with_features_from_the_gradient_phase_equals_separate_features(L, prec):
+    """With the one-launch network path, the forcing's input features come out of the
+    gradient phase of each RK stage (no feature launch); the corrected RK3 steps equal those
+    of the per-layer path with its separate feature kernel (same bf16 features; only the
+    tensor core's accumulation order may differ)."""
+    from paper_2207_11571_gb300 import dg, nn
+    K, P = 4, 3
+    ctx = dg.dg_create(K, P, 200.0, 0.1, 0.71, 0, precision=prec)
+    N = dg.dg_sizes(ctx)[0]
+    q0 = torch.empty(5 * N, dtype=torch.float64, device="cuda")
+    dg.dg_init_tgv(ctx, q0, torch.from_numpy(inputs.perturbation((5, N), eps=1e-3).ravel()).cuda())
+    h, _ = make_net(nn, 192, 256, 3, seed=17, max_batch=128, first_var=1, n_vars=3)
+    set_random_scalers(nn, h, 192, 9)
+    out = {}
+    for mode in (nn.NN_INFER_LAYERS, nn.NN_INFER_CLUSTER):
+        nn.nn_set_fused(h, mode)
+        q = q0.clone()
+        dg.dg_rk3_step(ctx, q, 2e-3, 3, forcing=h)
+        torch.cuda.synchronize()
+        out[mode] = q
+    plain = q0.clone()
+    dg.dg_rk3_step(ctx, plain, 2e-3, 3)
+    d = (out[nn.NN_INFER_CLUSTER] - out[nn.NN_INFER_LAYERS]).norm().item()
+    effect = (out[nn.NN_INFER_LAYERS] - plain).norm().item()   # what the forcing changed
+    assert effect > 0 and d < 1e-5 * effect, (d, effect)
+    nn.nn_destroy(h)
+    dg.dg_destroy(ctx)
+
+
 @pytest.mark.parametrize("block_shape", [0, 1])
 def test_rhs_and_rk3_with_forcing_match_oracle(L, block_shape):
     """dq/dt = p_LO(q) + s(q) (Eq. 4) and RK3 with s in every stage, FP64 operator, with
