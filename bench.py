@@ -208,8 +208,8 @@ def algorithm1_measure():
     return {"setting": "TGV Re 1600 Mach 0.08, 8^3, P8 -> P3, training window [7, 7.2], eval [7.2, 8], momenta, "
                        "8 layers x 256, 30 epochs, post-step forcing, split form",
             "runs": runs, "train_seconds": round(out["train_seconds"], 2), "n_pairs": out["n_pairs"],
-            "speedup_at_equal_error": {k: (None if v["speedup"] is None else round(v["speedup"], 3))
-                                       for k, v in sp.items()},
+            "speedup_at_equal_error": {k: {"speedup": None if v["speedup"] is None else round(v["speedup"], 3),
+                                           "kind": v["kind"]} for k, v in sp.items()},
             "forcing_active_fraction": out["forcing_active_fraction"],
             "cost_P6_over_corrected": round(out.get("speedup_vs_P6", float("nan")), 3),
             "seconds": round(out["total_seconds"], 1)}

@@ -45,12 +45,22 @@ int cuda_fail(cudaError_t err, const char* what) {
 }
 
 cudaError_t launch_gradient(const dg_ctx* c, const double* q, int src, cudaStream_t st) {
-  return c->opts.precision == DG_PREC_FP32 ? gradient_f32(c, q, src, st) : gradient_f64(c, q, src, st);
+  const bool f32 = c->opts.precision == DG_PREC_FP32;
+  if (c->part) return f32 ? gradient_f32_slab(c, q, src, st) : gradient_f64_slab(c, q, src, st);
+  return f32 ? gradient_f32(c, q, src, st) : gradient_f64(c, q, src, st);
 }
 
 cudaError_t launch_flux(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
                         double dt, cudaStream_t st) {
   const double invB1 = 1.0 / kRkB[0];
+  if (c->part) {
+    const bool f32 = c->opts.precision == DG_PREC_FP32;
+    if (c->geom.split)
+      return f32 ? flux_split_f32_slab(c, q, dqdt, f, mode, A, B, dt, invB1, st)
+                 : flux_split_f64_slab(c, q, dqdt, f, mode, A, B, dt, invB1, st);
+    return f32 ? flux_f32_slab(c, q, dqdt, f, mode, A, B, dt, invB1, st)
+               : flux_f64_slab(c, q, dqdt, f, mode, A, B, dt, invB1, st);
+  }
   if (c->geom.split)
     return c->opts.precision == DG_PREC_FP32 ? flux_split_f32(c, q, dqdt, f, mode, A, B, dt, invB1, st)
                                              : flux_split_f64(c, q, dqdt, f, mode, A, B, dt, invB1, st);
@@ -356,6 +366,13 @@ int dg_create_part(int K, int P, double Re, double Mach, double Pr, int closure,
   dg_ctx* c = nullptr;
   int rc = dg_create_local(K, P, Re, Mach, Pr, closure, &o, z_count + 2, &c);
   if (rc) return rc;
+  if (o.precision == DG_PREC_FP32) {
+    const cudaError_t ec = prepare_f32_slab_constants();
+    if (ec != cudaSuccess) {
+      dg_destroy(c);
+      return cuda_fail(ec, "dg_create_part: constant tables");
+    }
+  }
   c->part = 1;
   c->z_begin = z_begin;
   c->z_count = z_count;

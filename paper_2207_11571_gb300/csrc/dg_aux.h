@@ -84,6 +84,19 @@ cudaError_t flux_split_f64(const dg_ctx* c, double* q, double* dqdt, const Forci
 cudaError_t flux_f64(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
                      double dt, double invB1, cudaStream_t st);
 
+// The same for slab contexts (dg_kernels_f32_slab.cu, dg_kernels_f64_slab.cu).
+cudaError_t gradient_f32_slab(const dg_ctx* c, const double* q, int src, cudaStream_t st);
+cudaError_t gradient_f64_slab(const dg_ctx* c, const double* q, int src, cudaStream_t st);
+cudaError_t flux_f32_slab(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                          double dt, double invB1, cudaStream_t st);
+cudaError_t flux_f64_slab(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
+                          double dt, double invB1, cudaStream_t st);
+cudaError_t flux_split_f32_slab(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A,
+                                double B, double dt, double invB1, cudaStream_t st);
+cudaError_t flux_split_f64_slab(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A,
+                                double B, double dt, double invB1, cudaStream_t st);
+cudaError_t prepare_f32_slab_constants();
+
 // Derivative matrices in the constant memory of the FP32 kernels (dg_kernels_f32.cu,
 // dg_batch_f32.cu); once per device, before the first FP32 launch.
 cudaError_t prepare_f32_constants();

@@ -294,8 +294,10 @@ __device__ __forceinline__ void transport_c(const OpConst<T>& C, T rho, const T 
 
 // Phase A of block `blk` of one mesh (the body of k_gradient and k_gradient_batch).
 // CUBE: the block is a 2 x 2 x 2 cube of elements; the halo holds only the external
-// faces, internal faces take the neighbour's values from the own tile.
-template <int P, typename T, int SRC, bool CUBE = false>
+// faces, internal faces take the neighbour's values from the own tile.  SLAB: a slab of
+// element layers (owned range from C.e_begin, C.Kz local layers); a whole mesh compiles
+// without it.  FEAT: also write the forcing network's input features (C.feat).
+template <int P, typename T, int SRC, bool CUBE = false, bool SLAB = false, bool FEAT = false>
 __device__ __forceinline__ void gradient_block(int blk, const double* __restrict__ q,
                                                const float* __restrict__ qn32_in, const float* __restrict__ dlt,
                                                T* __restrict__ qf, float* __restrict__ qn32_out,
@@ -308,7 +310,7 @@ __device__ __forceinline__ void gradient_block(int blk, const double* __restrict
   T* sD = reinterpret_cast<T*>(smem_raw);
   T* sU = sD + n2;            // [4][E np]
   T* sH = sU + 4 * tileN;     // [4][haloN]: neighbours' gradient variables on the (external) faces
-  const int e0 = C.e_begin + blk * E;
+  const int e0 = (SLAB ? C.e_begin : 0) + blk * E;
   const BlockCoords bc = CUBE ? cube_coords(blk, C.K) : block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
 
@@ -329,7 +331,7 @@ __device__ __forceinline__ void gradient_block(int blk, const double* __restrict
 #pragma unroll
       for (int v = 0; v < 5; ++v) qn32_out[v * N + gi] = float(s[v]);
     }
-    if (C.feat.out != nullptr) {
+    if (FEAT) {
       // the forcing network's input features of this node, from the stage state just
       // formed: the same arithmetic as the separate feature kernels of the network
       __nv_bfloat16* fo = static_cast<__nv_bfloat16*>(C.feat.out) + (long long)e * C.feat.ld + node;
@@ -354,7 +356,7 @@ __device__ __forceinline__ void gradient_block(int blk, const double* __restrict
     const Item<P> it = CUBE ? cube_item_of<P>(t) : item_of<P>(t);
     if (!CUBE && e0 + it.hl >= C.nel) continue;
     const int enb = CUBE ? cube_neighbour(bc, it.hl, C.K, it.d, it.side ? 1 : -1)
-                         : neighbour_of(bc, it.hl, C.K, C.Kz, it.d, it.side ? 1 : -1);
+                         : neighbour_of(bc, it.hl, C.K, SLAB ? C.Kz : C.K, it.d, it.side ? 1 : -1);
     const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
     T sn[5], Un[4];
     stage_state<T, SRC>(q, qn32_in, dlt, N, gnb, C, sn);
@@ -442,13 +444,13 @@ __device__ __forceinline__ void gradient_block(int blk, const double* __restrict
   for (int c = 0; c < 9; ++c) vis[c * N + gi] = out[c];
 }
 
-template <int P, typename T, int SRC, bool CUBE = false>
+template <int P, typename T, int SRC, bool CUBE = false, bool SLAB = false, bool FEAT = false>
 __global__ void __launch_bounds__(max_threads_for(P))
 k_gradient(const double* __restrict__ q, const float* __restrict__ qn32_in, const float* __restrict__ dlt,
            T* __restrict__ qf, float* __restrict__ qn32_out, T* __restrict__ vis, const OpConst<T> C) {
   pdl_wait();
   pdl_release();
-  gradient_block<P, T, SRC, CUBE>(blockIdx.x, q, qn32_in, dlt, qf, qn32_out, vis, C);
+  gradient_block<P, T, SRC, CUBE, SLAB, FEAT>(blockIdx.x, q, qn32_in, dlt, qf, qn32_out, vis, C);
 }
 
 // Per-launch RK data of phase B in the arithmetic of the update.
@@ -637,7 +639,7 @@ __host__ __device__ constexpr bool flux_early(int P, int tsize) { return tsize =
 // 2 sum_m D_im F#(q_i, q_m) along each line with Pirozzoli's two-point flux F# (mass flux
 // {rho}{v_d}; momentum m {v_j} + {p'} delta_jd; energy m {H}), from a tile of primitives;
 // the viscous part and the surface terms keep the standard form.
-template <int P, typename T, int MODE, bool CUBE = false, bool SPLIT = false>
+template <int P, typename T, int MODE, bool CUBE = false, bool SPLIT = false, bool SLAB = false>
 __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, const T* __restrict__ qf,
                                            const T* __restrict__ vis, double* __restrict__ dqdt,
                                            T* __restrict__ greg, float* __restrict__ dlt, const Forcing& fc,
@@ -662,7 +664,7 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   T* sH = kEarlyF ? sF + kTileComponents * tileN : sX + kTileComponents * tileN;  // [9][E 6 n2]
   T* sS = sH + FC * haloN;                // [5][E 6 n2]: lifted interface terms
   T* sW = sS + 5 * faceN;                 // SPLIT: primitives [6][E np] (rho, v, p', H)
-  const int e0 = C.e_begin + blk * E;
+  const int e0 = (SLAB ? C.e_begin : 0) + blk * E;
   const BlockCoords bc = CUBE ? cube_coords(blk, C.K) : block_coords(e0, C.K);
   for (int t = threadIdx.x; t < n2; t += blockDim.x) sD[t] = C.D[t];
   const long long N = C.N;
@@ -733,7 +735,7 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
       const Item<P> it = CUBE ? cube_item_of<P>(t) : item_of<P>(t);
       if (!CUBE && e0 + it.hl >= C.nel) continue;
       const int enb = CUBE ? cube_neighbour(bc, it.hl, C.K, it.d, it.side ? 1 : -1)
-                           : neighbour_of(bc, it.hl, C.K, C.Kz, it.d, it.side ? 1 : -1);
+                           : neighbour_of(bc, it.hl, C.K, SLAB ? C.Kz : C.K, it.d, it.side ? 1 : -1);
       const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
       switch (it.d) {
         case 0: load_face_data<0>(qf, vis, N, gnb, sH + t, haloN); break;
@@ -954,13 +956,13 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
   }
 }
 
-template <int P, typename T, int MODE, bool CUBE = false, bool SPLIT = false>
+template <int P, typename T, int MODE, bool CUBE = false, bool SPLIT = false, bool SLAB = false>
 __global__ void __launch_bounds__(flux_max_threads(P), min_blocks_for(P, sizeof(T)))
 k_flux(double* __restrict__ q, const T* __restrict__ qf, const T* __restrict__ vis, double* __restrict__ dqdt,
        T* __restrict__ greg, float* __restrict__ dlt, Forcing fc, const OpConst<T> C, RkArgs<T> rk) {
   pdl_wait();
   pdl_release();
-  flux_block<P, T, MODE, CUBE, SPLIT>(blockIdx.x, q, qf, vis, dqdt, greg, dlt, fc, C, rk);
+  flux_block<P, T, MODE, CUBE, SPLIT, SLAB>(blockIdx.x, q, qf, vis, dqdt, greg, dlt, fc, C, rk);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1180,7 +1182,7 @@ __device__ __forceinline__ void flux_stream(const Src& src, int n_items) {
     T* h = b + 14 * kTS;
     for (int t = threadIdx.x; t < haloN; t += blockDim.x) {
       const Item<P> it = item_of<P>(t);
-      const int enb = neighbour_of(bc, 0, m.C->K, m.C->Kz, it.d, it.side ? 1 : -1);
+      const int enb = neighbour_of(bc, 0, m.C->K, Src::kSlab ? m.C->Kz : m.C->K, it.d, it.side ? 1 : -1);
       const long long gnb = (long long)enb * np + face_node<P>(it.d, it.side ? 0 : P, it.ab);
       switch (it.d) {
         case 0: copy_face_data<0>(m.qf, m.vis, N, gnb, h + t, haloN); break;
@@ -1366,26 +1368,30 @@ struct StreamMesh {
   int* err;  // device error flag (may be NULL)
 };
 
+template <bool SLAB>
 struct SingleSource {
+  static constexpr bool kSlab = SLAB;
   const StreamMesh& m;
   __device__ __forceinline__ StreamItem at(int item) const {
-    return StreamItem{m.q, m.qf, m.vis, m.dqdt, m.greg, m.dlt, &m.C, &m.rk, m.fc, m.C.e_begin + item, m.bulk, m.err};
+    return StreamItem{m.q, m.qf, m.vis, m.dqdt, m.greg, m.dlt, &m.C, &m.rk, m.fc, (SLAB ? m.C.e_begin : 0) + item,
+                      m.bulk, m.err};
   }
 };
 
 struct BatchSource {
+  static constexpr bool kSlab = false;
   const BatchTable<float>& tb;
   __device__ __forceinline__ StreamItem at(int item) const {
     const int i = batch_instance(tb.block_start, tb.n, item);
     return StreamItem{tb.q[i], tb.qf[i], tb.vis[i], nullptr, tb.g[i], tb.dlt[i], &tb.C[i], &tb.rk[i], Forcing{},
-                      tb.C[i].e_begin + item - tb.block_start[i], tb.bulk[i], tb.err[i]};
+                      item - tb.block_start[i], tb.bulk[i], tb.err[i]};
   }
 };
 
-template <int P, int MODE>
+template <int P, int MODE, bool SLAB = false>
 __global__ void __launch_bounds__(stream_threads(P), stream_min_blocks(P))
 k_flux_stream(const __grid_constant__ StreamMesh mesh) {
-  flux_stream<P, MODE>(SingleSource{mesh}, mesh.C.nel - mesh.C.e_begin);
+  flux_stream<P, MODE>(SingleSource<SLAB>{mesh}, mesh.C.nel - (SLAB ? mesh.C.e_begin : 0));
 }
 
 // Batched streamed phase B: members of order P, one element per work item

@@ -127,29 +127,40 @@ size_t flux_smem(int E) {
   return sizeof(T) * (n2 + tile * E * np + (kFaceComponents + 5) * E * 6 * n2);
 }
 
-template <int P, typename T, int SRC>
-cudaError_t gradient_p(const dg_ctx* c, const double* q, cudaStream_t st) {
-  if constexpr (cube_ok(P)) {
+// Phase A.  SLAB: a slab context (owned range, local z extent; no network features);
+// whole meshes pick the variant that also writes the network's features when the context
+// asks for them (c->feat_out), so that the plain kernel compiles as it did without them.
+template <int P, typename T, int SRC, bool SLAB, bool FEAT>
+cudaError_t gradient_launch(const dg_ctx* c, const double* q, cudaStream_t st) {
+  if constexpr (cube_ok(P) && !SLAB) {
     if (c->geom.cube) {
       const size_t smem = gradient_smem_cube<P, T>();
-      auto kern = k_gradient<P, T, SRC, true>;
+      auto kern = k_gradient<P, T, SRC, true, false, FEAT>;
       cudaError_t e = set_smem(kern, smem);
       if (e != cudaSuccess) return e;
       const int h = c->K / 2;
-      return launch_pdl(kern, dim3(h * h * h), dim3(block_threads(P, kCubeElems)), smem, st, 
+      return launch_pdl(kern, dim3(h * h * h), dim3(block_threads(P, kCubeElems)), smem, st,
           q, c->qn32, c->dlt, static_cast<T*>(c->qf), SRC == 0 ? c->qn32 : nullptr, static_cast<T*>(c->vis),
           make_const<T>(c));
     }
   }
   const int E = c->geom.E;
   const size_t smem = gradient_smem<P, T>(E);
-  auto kern = k_gradient<P, T, SRC>;
+  auto kern = k_gradient<P, T, SRC, false, SLAB, FEAT>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = (owned_elems(c) + E - 1) / E;
   return launch_pdl(kern, dim3(grid), dim3(block_threads(P, E)), smem, st, q, c->qn32, c->dlt, static_cast<T*>(c->qf),
                                                 SRC == 0 ? c->qn32 : nullptr, static_cast<T*>(c->vis),
                                                 make_const<T>(c));
+}
+
+template <int P, typename T, int SRC, bool SLAB>
+cudaError_t gradient_p(const dg_ctx* c, const double* q, cudaStream_t st) {
+  if constexpr (!SLAB) {
+    if (c->feat_out.out != nullptr) return gradient_launch<P, T, SRC, false, true>(c, q, st);
+  }
+  return gradient_launch<P, T, SRC, SLAB, false>(c, q, st);
 }
 
 // Grid of a persistent streamed launch: resident blocks on every SM, at most one per item.
@@ -178,11 +189,11 @@ inline int stream_bulk_ok(const dg_ctx* c) {
 }
 
 // Streamed phase B (FP32 operator, P >= 6, one element per block step).
-template <int P, int MODE>
+template <int P, int MODE, bool SLAB>
 cudaError_t flux_stream_launch(const dg_ctx* c, double* q, double* dqdt, const Forcing& f,
                                const RkArgs<float>& rk, cudaStream_t st) {
   const size_t smem = sizeof(float) * stream_smem_floats<P>();
-  auto kern = k_flux_stream<P, MODE>;
+  auto kern = k_flux_stream<P, MODE, SLAB>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int grid = 0;
@@ -202,13 +213,13 @@ cudaError_t flux_stream_launch(const dg_ctx* c, double* q, double* dqdt, const F
   return launch_pdl(kern, dim3(grid), dim3(stream_threads(P)), smem, st, m);
 }
 
-template <int P, typename T, int MODE>
+template <int P, typename T, int MODE, bool SLAB>
 cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, const RkArgs<T>& rk,
                    cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value && P >= 6 && MODE != 1) {
-    if (c->geom.E == 1) return flux_stream_launch<P, MODE>(c, q, dqdt, f, rk, st);
+    if (c->geom.E == 1) return flux_stream_launch<P, MODE, SLAB>(c, q, dqdt, f, rk, st);
   }
-  if constexpr (cube_ok(P)) {
+  if constexpr (cube_ok(P) && !SLAB) {
     if (c->geom.cube) {
       const size_t smem = flux_smem_cube<P, T>();
       auto kern = k_flux<P, T, MODE, true>;
@@ -222,7 +233,7 @@ cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, c
   }
   const int E = c->geom.E;
   const size_t smem = flux_smem<P, T>(E);
-  auto kern = k_flux<P, T, MODE>;
+  auto kern = k_flux<P, T, MODE, false, false, SLAB>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = (owned_elems(c) + E - 1) / E;
@@ -231,23 +242,23 @@ cudaError_t flux_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, c
 }
 
 // FP64 operator: modes 0 (dq/dt) and 1 (FP64 RK stage).  FP32 operator: modes 0, 2, 3, 4.
-template <int P, typename T>
+template <int P, typename T, bool SLAB>
 cudaError_t flux_dispatch_mode(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode,
                                const RkArgs<T>& rk, cudaStream_t st) {
   switch (mode) {
-    case 0: return flux_p<P, T, 0>(c, q, dqdt, f, rk, st);
-    case 1: return flux_p<P, T, 1>(c, q, dqdt, f, rk, st);
-    case 2: return flux_p<P, T, 2>(c, q, dqdt, f, rk, st);
-    case 3: return flux_p<P, T, 3>(c, q, dqdt, f, rk, st);
-    case 4: return flux_p<P, T, 4>(c, q, dqdt, f, rk, st);
+    case 0: return flux_p<P, T, 0, SLAB>(c, q, dqdt, f, rk, st);
+    case 1: return flux_p<P, T, 1, SLAB>(c, q, dqdt, f, rk, st);
+    case 2: return flux_p<P, T, 2, SLAB>(c, q, dqdt, f, rk, st);
+    case 3: return flux_p<P, T, 3, SLAB>(c, q, dqdt, f, rk, st);
+    case 4: return flux_p<P, T, 4, SLAB>(c, q, dqdt, f, rk, st);
   }
   return cudaErrorInvalidValue;
 }
 
-template <int P, typename T>
+template <int P, typename T, bool SLAB>
 cudaError_t gradient_dispatch_src(const dg_ctx* c, const double* q, int src, cudaStream_t st) {
-  if (src == 0) return gradient_p<P, T, 0>(c, q, st);
-  return gradient_p<P, T, 1>(c, q, st);
+  if (src == 0) return gradient_p<P, T, 0, SLAB>(c, q, st);
+  return gradient_p<P, T, 1, SLAB>(c, q, st);
 }
 
 #define DG_FOR_EACH_P(CALL)        \
@@ -263,18 +274,18 @@ cudaError_t gradient_dispatch_src(const dg_ctx* c, const double* q, int src, cud
   }                                \
   return cudaErrorInvalidValue;
 
-template <typename T>
+template <typename T, bool SLAB = false>
 cudaError_t gradient_t(const dg_ctx* c, const double* q, int src, cudaStream_t st) {
-#define DG_G(PP) gradient_dispatch_src<PP, T>(c, q, src, st)
+#define DG_G(PP) gradient_dispatch_src<PP, T, SLAB>(c, q, src, st)
   DG_FOR_EACH_P(DG_G)
 #undef DG_G
 }
 
-template <typename T>
+template <typename T, bool SLAB = false>
 cudaError_t flux_t(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
                    double dt, double invB1, cudaStream_t st) {
   const RkArgs<T> rk{T(A), T(B), T(dt), T(invB1)};
-#define DG_F(PP) flux_dispatch_mode<PP, T>(c, q, dqdt, f, mode, rk, st)
+#define DG_F(PP) flux_dispatch_mode<PP, T, SLAB>(c, q, dqdt, f, mode, rk, st)
   DG_FOR_EACH_P(DG_F)
 #undef DG_F
 }
@@ -282,13 +293,13 @@ cudaError_t flux_t(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, i
 // ---------------------------------------------------------------------------------------
 // Split-form phase B (rows of E elements, every order, both precisions): k_flux with the
 // two-point-flux volume term and a tile of primitives [6][E np] on top of flux_smem.
-template <int P, typename T, int MODE>
+template <int P, typename T, int MODE, bool SLAB>
 cudaError_t flux_split_p(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, const RkArgs<T>& rk,
                          cudaStream_t st) {
   constexpr int np = (P + 1) * (P + 1) * (P + 1);
   const int E = c->geom.E;
   const size_t smem = flux_smem<P, T>(E) + sizeof(T) * 6 * E * np;
-  auto kern = k_flux<P, T, MODE, false, true>;
+  auto kern = k_flux<P, T, MODE, false, true, SLAB>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = (owned_elems(c) + E - 1) / E;
@@ -296,30 +307,30 @@ cudaError_t flux_split_p(const dg_ctx* c, double* q, double* dqdt, const Forcing
                                                 static_cast<T*>(c->g), c->dlt, f, make_const<T>(c), rk);
 }
 
-template <int P, typename T>
+template <int P, typename T, bool SLAB>
 cudaError_t flux_split_dispatch_mode(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode,
                                      const RkArgs<T>& rk, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value) {
     switch (mode) {
-      case 0: return flux_split_p<P, T, 0>(c, q, dqdt, f, rk, st);
-      case 2: return flux_split_p<P, T, 2>(c, q, dqdt, f, rk, st);
-      case 3: return flux_split_p<P, T, 3>(c, q, dqdt, f, rk, st);
-      case 4: return flux_split_p<P, T, 4>(c, q, dqdt, f, rk, st);
+      case 0: return flux_split_p<P, T, 0, SLAB>(c, q, dqdt, f, rk, st);
+      case 2: return flux_split_p<P, T, 2, SLAB>(c, q, dqdt, f, rk, st);
+      case 3: return flux_split_p<P, T, 3, SLAB>(c, q, dqdt, f, rk, st);
+      case 4: return flux_split_p<P, T, 4, SLAB>(c, q, dqdt, f, rk, st);
     }
   } else {
     switch (mode) {
-      case 0: return flux_split_p<P, T, 0>(c, q, dqdt, f, rk, st);
-      case 1: return flux_split_p<P, T, 1>(c, q, dqdt, f, rk, st);
+      case 0: return flux_split_p<P, T, 0, SLAB>(c, q, dqdt, f, rk, st);
+      case 1: return flux_split_p<P, T, 1, SLAB>(c, q, dqdt, f, rk, st);
     }
   }
   return cudaErrorInvalidValue;
 }
 
-template <typename T>
+template <typename T, bool SLAB = false>
 cudaError_t flux_split_t(const dg_ctx* c, double* q, double* dqdt, const Forcing& f, int mode, double A, double B,
                          double dt, double invB1, cudaStream_t st) {
   const RkArgs<T> rk{T(A), T(B), T(dt), T(invB1)};
-#define DG_S(PP) flux_split_dispatch_mode<PP, T>(c, q, dqdt, f, mode, rk, st)
+#define DG_S(PP) flux_split_dispatch_mode<PP, T, SLAB>(c, q, dqdt, f, mode, rk, st)
   DG_FOR_EACH_P(DG_S)
 #undef DG_S
 }

@@ -201,17 +201,35 @@ def run_errors(run, ref_t, ref_dke, ref_ke, bar_ke):
 
 
 def speedup_at_equal_error(corr, plain, key):
-    """Cost of the plain-order curve interpolated (log-log) at the corrected run's error,
-    over the corrected run's cost.  Below the smallest plain error the curve is not
-    extrapolated and the result is a lower bound."""
-    pts = sorted([(r["errors"][key], r["ms"]) for r in plain if math.isfinite(r["errors"][key])])
+    """Cost of the plain orders at the corrected run's error, over the corrected run's cost,
+    and how that cost was found:
+      "interpolated": the plain runs' error falls as their cost grows; their error/cost
+          curve is interpolated log-log at the corrected error;
+      "lower_bound": the corrected error is below every plain error (no extrapolation:
+          the cost of the most accurate plain run);
+      "cheapest_plain_is_more_accurate": the corrected error is above every plain error;
+          the cost of the cheapest plain run, which is already more accurate (the speed-up
+          at equal error is at most this);
+      "pareto": the plain errors do not fall with cost (e.g. saturated errors); the cost of
+          the cheapest plain run at least as accurate as the corrected one."""
+    pts = sorted([(r["ms"], r["errors"][key]) for r in plain if math.isfinite(r["errors"][key])])
     e = corr["errors"][key]
     if not pts or not math.isfinite(e):
         return None, None
-    le = np.log([p[0] for p in pts])
-    lc = np.log([p[1] for p in pts])
-    cost = float(math.exp(np.interp(math.log(e), le, lc)))
-    return cost / corr["ms"], bool(math.log(e) < le.min())
+    costs = [p[0] for p in pts]
+    errs = [p[1] for p in pts]
+    if e > max(errs):
+        return min(costs) / corr["ms"], "cheapest_plain_is_more_accurate"
+    if all(b < a for a, b in zip(errs, errs[1:])):
+        if e < errs[-1]:
+            return costs[-1] / corr["ms"], "lower_bound"
+        le = np.log(errs[::-1])
+        lc = np.log(costs[::-1])
+        return float(math.exp(np.interp(math.log(e), le, lc))) / corr["ms"], "interpolated"
+    ok = [c for c, er in pts if er <= e]
+    if not ok:
+        return max(costs) / corr["ms"], "lower_bound"
+    return min(ok) / corr["ms"], "pareto"
 
 
 def parse(argv=None):
@@ -391,8 +409,8 @@ def run(args):
     corr, plain = out["runs"][0], out["runs"][1:]
     out["speedup_vs_plain_at_equal_error"] = {}
     for key in ("dke", "ke", "dke_filtered", "einf"):
-        sp, lower = speedup_at_equal_error(corr, plain, key)
-        out["speedup_vs_plain_at_equal_error"][key] = {"speedup": sp, "lower_bound": lower,
+        sp, kind = speedup_at_equal_error(corr, plain, key)
+        out["speedup_vs_plain_at_equal_error"][key] = {"speedup": sp, "kind": kind,
                                                        "forcing_active_fraction": corr["forcing_active_fraction"]}
     out["forcing_active_fraction"] = corr["forcing_active_fraction"]
     p6 = [r for r in plain if r["P"] == 6]

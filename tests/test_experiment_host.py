@@ -17,13 +17,23 @@ def run_record(err, ms):
 def test_speedup_interpolates_a_power_law_exactly():
     # plain orders on cost = 0.4 / error: log-log linear, so interpolation is exact
     plain = [run_record(0.4, 1.0), run_record(0.2, 2.0), run_record(0.1, 4.0), run_record(float("inf"), 0.5)]
-    s, below = experiment.speedup_at_equal_error(run_record(0.4 / 2.83, 1.0), plain, "dke")
-    assert s == pytest.approx(2.83, rel=1e-12) and below is False
+    s, kind = experiment.speedup_at_equal_error(run_record(0.4 / 2.83, 1.0), plain, "dke")
+    assert s == pytest.approx(2.83, rel=1e-12) and kind == "interpolated"
     # below the smallest plain error: no extrapolation, the result is a lower bound
-    s, below = experiment.speedup_at_equal_error(run_record(0.05, 2.0), plain, "dke")
-    assert s == pytest.approx(2.0, rel=1e-12) and below is True
+    s, kind = experiment.speedup_at_equal_error(run_record(0.05, 2.0), plain, "dke")
+    assert s == pytest.approx(2.0, rel=1e-12) and kind == "lower_bound"
+    # above every plain error: the cheapest plain run is already more accurate
+    s, kind = experiment.speedup_at_equal_error(run_record(0.8, 4.0), plain, "dke")
+    assert s == pytest.approx(0.25, rel=1e-12) and kind == "cheapest_plain_is_more_accurate"
     # a diverged corrected run has no speed-up
     assert experiment.speedup_at_equal_error(run_record(float("inf"), 1.0), plain, "dke") == (None, None)
+
+
+def test_speedup_with_errors_that_do_not_fall_with_cost_takes_the_cheapest_as_accurate_run():
+    # saturated errors: 0.99 at cost 1, 0.78 at 2, 1.13 at 3, 1.03 at 5 (not monotone)
+    plain = [run_record(0.99, 1.0), run_record(0.78, 2.0), run_record(1.13, 3.0), run_record(1.03, 5.0)]
+    s, kind = experiment.speedup_at_equal_error(run_record(0.9, 2.0), plain, "dke")
+    assert s == pytest.approx(1.0, rel=1e-12) and kind == "pareto"   # the cost-2 run (0.78 <= 0.9)
 
 
 def test_run_errors_of_a_diverged_run_are_infinite_and_exact_run_is_zero():
