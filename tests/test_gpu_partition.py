@@ -205,3 +205,28 @@ def test_slab_argument_checks(dg):
         assert e.value.status == dg.DG_ERR_INVALID_ARG
     finally:
         s.close()
+
+
+def test_autotuned_slabs_still_equal_the_whole_mesh(dg):
+    """dg_autotune on a slab times its kernels without exchanging traces (on a scratch
+    copy) and only changes the blocking: the group's steps stay equal to the whole mesh's."""
+    K, P = 4, 3
+    whole = dg.dg_create(K, P, 1600.0, 0.1, 0.71, 0, precision=1)
+    s = Slabs(dg, K, P, 2, precision=1)
+    try:
+        N = dg.dg_sizes(whole)[0]
+        q = tgv(dg, whole, N, eps=1e-3)
+        qs = s.scatter(q)
+        dt = dg.dg_stable_dt(whole, q, 0.7)
+        for c, x in zip(s.parts, qs):
+            before = x.clone()
+            E, ms = dg.dg_autotune(c, x, dt)
+            assert E >= 1 and ms > 0 and torch.equal(x, before)
+            assert dg.dg_blocking(c)[1] == 0          # rows: slabs take no cube blocks
+        dg.dg_rk3_step(whole, q, dt, 2)
+        dg.dg_group_rk3_step(s.parts, qs, dt, 2)
+        torch.cuda.synchronize()
+        assert torch.equal(s.gather(qs), q)
+    finally:
+        s.close()
+        dg.dg_destroy(whole)
