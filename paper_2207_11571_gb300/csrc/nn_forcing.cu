@@ -17,11 +17,17 @@
 // (one TMEM lane = one element per thread), taking alternate 16-column groups.  The layers'
 // biases and the output scaling of this CTA's slices sit in shared memory.  Cross-CTA
 // ordering uses mbarriers only:
-//   act_ready: one local arrival (this CTA's slice is written) with the expected bytes of
-//       the C - 1 incoming slices, which the peers' bulk copies complete;
+//   act_own: one local arrival, this CTA's slice of the next input is written (a CTA's own
+//       panels are free once its own MMAs of the layer have completed);
+//   act_from[k] (k != own rank): one local arrival carrying the bytes of CTA k's slice,
+//       which CTA k's bulk copy completes;
 //   peers_done (C arrivals): every CTA's MMAs of the current layer have completed, so no
-//       tensor core still reads the panels that the next input overwrites, and every
+//       tensor core still reads the panels that the slice copies overwrite, and every
 //       earlier slice copy has landed (those MMAs waited for it).
+// A hidden layer's K loop starts on the CTA's own panels and then takes the peers' slices
+// in the order they are sent (CTA k copies to k - 1 first, then k - 2, ...), so the
+// tensor core works while the other slices are still in flight; the weight tiles stream
+// in the same order.
 // Every wait is bounded (about a second): on expiry a thread sets the error flag and the
 // CTA skips the rest of its work; all threads meet at a final cluster barrier, so that no
 // CTA leaves while a peer may still write into its shared memory.
@@ -48,6 +54,7 @@ constexpr int kPanelBytes = kRows * kPanel * 2;   // 16 KB
 constexpr int kTileBytes = kChunk * kPanel * 2;   // 16 KB (largest weight tile)
 constexpr int kMaxPanels = kMlpMaxWidth / kPanel; // 8
 constexpr int kRing = 5;
+constexpr int kMaxCluster = 4;
 constexpr int kEpiWarps = 8;                      // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kTmemCols = 512;
@@ -176,8 +183,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
   uint64_t* empty = full + kRing;
   uint64_t* a0_full = empty + kRing;
   uint64_t* mma_done = a0_full + 1;
-  uint64_t* act_ready = mma_done + 1;
-  uint64_t* peers_done = act_ready + 1;
+  uint64_t* act_own = mma_done + 1;
+  uint64_t* act_from = act_own + 1;          // [kMaxCluster], indexed by the sending CTA
+  uint64_t* peers_done = act_from + kMaxCluster;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(peers_done + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
@@ -193,7 +201,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
     }
     mbar_init(a0_full, 1);
     mbar_init(mma_done, 1);
-    mbar_init(act_ready, 1);       // the local issuer of the slice copies, plus the copies' bytes
+    mbar_init(act_own, 1);
+    for (int k = 0; k < kMaxCluster; ++k) mbar_init(&act_from[k], 1);   // local arrival + CTA k's bytes
     mbar_init(peers_done, C);      // one arrival per CTA
     *abort_flag = 0;
     mbar_fence_init();
@@ -219,9 +228,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
       bool ok = true;
       for (int l = 0; l < a.L && ok; ++l) {
         const int ns = a.dims[l + 1] / C, KP = panels_of(a.dims[l]);
+        const int own0 = l == 0 ? 0 : j * (KP / C);   // the K loop's first panel
         for (int c0 = 0; c0 < ns && ok; c0 += kChunk) {
           const int nc = min(kChunk, ns - c0);
-          for (int p = 0; p < KP; ++p) {
+          for (int i = 0; i < KP; ++i) {
+            const int p = (own0 + i) % KP;
             const int s = issued % kRing;
             const uint32_t ph = (issued / kRing) & 1;
             if (*(volatile int*)abort_flag || !mbar_wait(&empty[s], ph ^ 1)) {
@@ -246,8 +257,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
       int used = 0;
       bool ok = true;
       for (int l = 0; l < a.L && ok; ++l) {
-        // layer 0: the features by TMA; layer l > 0: the epilogues of every CTA
-        const bool in_ok = l == 0 ? mbar_wait(a0_full, 0) : wait_cluster(act_ready, (l - 1) & 1);
+        // layer 0: the features by TMA; layer l > 0: this CTA's own slice first, then each
+        // peer's slice when its copy has landed
+        const bool in_ok = l == 0 ? mbar_wait(a0_full, 0) : mbar_wait(act_own, (l - 1) & 1);
         if (*(volatile int*)abort_flag || !in_ok) {
           *(volatile int*)abort_flag = 1;
           atomicExch(err_flag, 23);
@@ -256,9 +268,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
         fence_async_smem();
         tc_fence_after();
         const int ns = a.dims[l + 1] / C, KP = panels_of(a.dims[l]);
+        const int pps = l == 0 ? KP : KP / C;   // panels per slice of the input
+        const int own0 = l == 0 ? 0 : j * pps;
+        uint32_t landed = 1u << j;              // bit k: CTA k's slice is in this CTA's panels
         for (int c0 = 0; c0 < ns && ok; c0 += kChunk) {
           const uint32_t idesc = idesc_bf16(kRows, min(kChunk, ns - c0));
-          for (int p = 0; p < KP; ++p) {
+          for (int i = 0; i < KP; ++i) {
+            const int p = (own0 + i) % KP;
+            if (l > 0 && !((landed >> (p / pps)) & 1u)) {
+              const int src = p / pps;
+              if (*(volatile int*)abort_flag || !wait_cluster(&act_from[src], (l - 1) & 1)) {
+                *(volatile int*)abort_flag = 1;
+                atomicExch(err_flag, 28);
+                ok = false;
+                break;
+              }
+              fence_async_smem();
+              tc_fence_after();
+              landed |= 1u << src;
+            }
             const int s = used % kRing;
             const uint32_t ph = (used / kRing) & 1;
             if (*(volatile int*)abort_flag || !mbar_wait(&full[s], ph)) {
@@ -271,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
             const uint32_t aa = smem_u32(act + p * kPanelBytes), bb = smem_u32(ring + s * kTileBytes);
 #pragma unroll
             for (int kk = 0; kk < kPanel / 16; ++kk)
-              umma_bf16(tmem + c0, sw128_desc(aa + kk * 32), sw128_desc(bb + kk * 32), idesc, (p | kk) != 0);
+              umma_bf16(tmem + c0, sw128_desc(aa + kk * 32), sw128_desc(bb + kk * 32), idesc, (i | kk) != 0);
             umma_commit(&empty[s]);
             ++used;
           }
@@ -324,18 +352,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
       }
       const int groups = ns / 16;
       if (!last) {
-        // the panels are free once every CTA's MMAs of this layer have completed (and so
-        // every copy of the previous slices, which those MMAs waited for, has landed)
-        if (ew == 0 && lane == 0)
+        const uint32_t slice = (uint32_t)(ns / kPanel) * kPanelBytes;
+        if (C > 1 && ew == 0 && lane == 0) {
+          // the next input's incoming slices (their bytes), and this CTA's MMAs of the
+          // layer are done: once every CTA's are, no tensor core reads the panels that the
+          // slice copies overwrite
+          for (int k = 0; k < C; ++k)
+            if (k != j) mbar_expect_tx(&act_from[k], slice);
           for (int k = 0; k < C; ++k) arrive_remote(peers_done, k);
-        ok = wait_cluster(peers_done, l & 1);
-        if (!__all_sync(0xffffffffu, ok)) {
-          *(volatile int*)abort_flag = 1;
-          atomicExch(err_flag, 26);
-          ok = false;
-          break;
         }
-        // this CTA's slice of the next layer's input into its own panels
+        // this CTA's slice of the next layer's input into its own panels (which only its
+        // own MMAs read)
 #pragma unroll 1
         for (int g = half; g < groups; g += 4) {
           // groups g and g + 2 of this warp: two TMEM loads, one wait
@@ -355,14 +382,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
         tc_fence_before();
         epilogue_sync();
         if (ew == 0 && lane == 0) {
-          // the slice (whole panels) to every other CTA of the cluster; this CTA's input
-          // is complete when its own slice is written (this arrival) and the other CTAs'
-          // slices have landed (their bytes)
-          const uint32_t slice = (uint32_t)(ns / kPanel) * kPanelBytes;
-          uint8_t* src = act + (cbase / kPanel) * kPanelBytes;
-          for (int k = 0; k < C; ++k)
-            if (k != j) bulk_to_peer(src, slice, act_ready, k);
-          mbar_expect_tx(act_ready, (uint32_t)(C - 1) * slice);
+          mbar_arrive(act_own);   // the next layer's MMAs may start on this slice
+          if (C > 1) {
+            // the slice (whole panels) to every other CTA of the cluster, CTA j - 1 first
+            // (the order in which the receivers' K loops take the slices), on the
+            // receivers' act_from[j]
+            if (wait_cluster(peers_done, l & 1) && !*(volatile int*)abort_flag) {
+              uint8_t* src = act + (cbase / kPanel) * kPanelBytes;
+              for (int i = 1; i < C; ++i) bulk_to_peer(src, slice, &act_from[j], (uint32_t)((j - i + C) % C));
+            } else {
+              *(volatile int*)abort_flag = 1;
+              atomicExch(err_flag, 26);
+            }
+          }
         }
       } else {
 #pragma unroll 1

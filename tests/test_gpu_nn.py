@@ -242,8 +242,12 @@ CLUSTER_CASES = [(4, 3, 5, 256, 2, 1), (5, 3, 5, 512, 4, 0), (6, 3, 3, 256, 3, 1
 def test_cluster_forcing_equals_per_layer_gemms(L, K, P, nv, width, hidden, prec):
     """The one-launch forcing (features, every layer and the unscaling in clusters of CTAs
     that share activations through distributed shared memory) computes what the per-layer
-    path computes: the same bf16 features and weights, FP32 accumulation; only the
-    accumulation order inside the tensor core may differ."""
+    path computes: the same bf16 features and weights, FP32 accumulation.  A CTA's K loop
+    starts on its own slice of the input (then the peers' slices), so the FP32 sums are
+    taken in another order, which flips the bf16 rounding of a few hidden activations by
+    one bf16 ulp (2^-8 relative); measured 9e-5 relative L2 on the output, bounded here at
+    5e-4, where a stale or missing panel gives O(1).  Two launches on the same input are
+    bitwise equal (no race between the slice copies and the tensor core)."""
     from paper_2207_11571_gb300 import dg, nn
     ctx = dg.dg_create(K, P, 1600.0, 0.1, 0.71, 0, precision=prec)
     N = dg.dg_sizes(ctx)[0]
@@ -254,15 +258,16 @@ def test_cluster_forcing_equals_per_layer_gemms(L, K, P, nv, width, hidden, prec
     h, _ = make_net(nn, feat, width, hidden, seed=40 + K, max_batch=512, first_var=first, n_vars=nv)
     set_random_scalers(nn, h, feat, 6)
     out = {}
-    for mode in (0, 2):
-        nn.nn_set_fused(h, mode)
+    for mode in (0, 2, 3):
+        nn.nn_set_fused(h, min(mode, 2))
         s = torch.full((K ** 3 * feat,), float("nan"), dtype=torch.float32, device="cuda")
         nn.nn_forcing_infer(h, ctx, q, s)
         torch.cuda.synchronize()
         out[mode] = s
     assert torch.isfinite(out[2]).all()
+    assert torch.equal(out[2], out[3])
     err = ((out[2] - out[0]).norm() / out[0].norm()).item()
-    assert err < 1e-5, err
+    assert err < 5e-4, err
     nn.nn_destroy(h)
     dg.dg_destroy(ctx)
 
@@ -271,8 +276,9 @@ def test_cluster_forcing_equals_per_layer_gemms(L, K, P, nv, width, hidden, prec
 def test_corrected_rk3_with_features_from_the_gradient_phase_equals_separate_features(L, prec):
     """With the one-launch network path, the forcing's input features come out of the
     gradient phase of each RK stage (no feature launch); the corrected RK3 steps equal those
-    of the per-layer path with its separate feature kernel (same bf16 features; only the
-    tensor core's accumulation order may differ)."""
+    of the per-layer path with its separate feature kernel (same bf16 features; the
+    tensor core's accumulation order differs, which flips a few bf16 roundings of hidden
+    activations: the two runs may differ by 5e-4 of what the forcing changed)."""
     from paper_2207_11571_gb300 import dg, nn
     K, P = 4, 3
     ctx = dg.dg_create(K, P, 200.0, 0.1, 0.71, 0, precision=prec)
@@ -292,7 +298,7 @@ def test_corrected_rk3_with_features_from_the_gradient_phase_equals_separate_fea
     dg.dg_rk3_step(ctx, plain, 2e-3, 3)
     d = (out[nn.NN_INFER_CLUSTER] - out[nn.NN_INFER_LAYERS]).norm().item()
     effect = (out[nn.NN_INFER_LAYERS] - plain).norm().item()   # what the forcing changed
-    assert effect > 0 and d < 1e-5 * effect, (d, effect)
+    assert effect > 0 and d < 5e-4 * effect, (d, effect)
     nn.nn_destroy(h)
     dg.dg_destroy(ctx)
 
