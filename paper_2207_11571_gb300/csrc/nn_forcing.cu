@@ -14,20 +14,27 @@
 //
 // Warps: 0 TMA producer (the feature tile, then weight tiles through a 5-stage ring),
 // 1 TMEM allocation and the MMA issuer, 2..9 epilogue: two warps per TMEM lane quarter
-// (one TMEM lane = one element per thread), taking alternate 16-column groups.  The layers'
-// biases and the output scaling of this CTA's slices sit in shared memory.  Cross-CTA
-// ordering uses mbarriers only:
-//   act_own: one local arrival, this CTA's slice of the next input is written (a CTA's own
-//       panels are free once its own MMAs of the layer have completed);
+// (one TMEM lane = one element per thread), taking alternate 16-column groups, one 64-column
+// panel of the CTA's slice after the other; 10 the exchange: the arrivals at the peers and
+// the slice copies, off the epilogue's path.  The layers' biases and the output scaling of
+// this CTA's slices sit in shared memory.  Ordering uses mbarriers only:
+//   panel_ready[i] (one arrival per epilogue thread): panel i of this CTA's slice of the
+//       next input is written (a CTA's own panels are free once its own MMAs of the layer
+//       have completed, since only they read them);
 //   act_from[k] (k != own rank): one local arrival carrying the bytes of CTA k's slice,
-//       which CTA k's bulk copy completes;
+//       which CTA k's bulk copies complete;
 //   peers_done (C arrivals): every CTA's MMAs of the current layer have completed, so no
 //       tensor core still reads the panels that the slice copies overwrite, and every
-//       earlier slice copy has landed (those MMAs waited for it).
-// A hidden layer's K loop starts on the CTA's own panels and then takes the peers' slices
-// in the order they are sent (CTA k copies to k - 1 first, then k - 2, ...), so the
-// tensor core works while the other slices are still in flight; the weight tiles stream
-// in the same order.
+//       earlier slice copy has landed (those MMAs waited for it);
+//   copies_landed (C - 1 arrivals, one from each receiver's exchange warp): this CTA's
+//       slice has landed everywhere, so the copy engine no longer reads the panels that
+//       the next slice overwrites.
+// A hidden layer's K loop starts on the CTA's own panels as each is written and then takes
+// the peers' slices in the order they are sent (CTA k copies each panel to k - 1 first,
+// then k - 2, ...), so the tensor core works while the other slices are still in flight;
+// the weight tiles stream in the same order.  Where a slice is at most 256 columns, layers
+// alternate between two TMEM accumulators, so the next layer's MMAs may start while the
+// epilogue still reads the last panels of this one.
 // Every wait is bounded (about a second): on expiry a thread sets the error flag and the
 // CTA skips the rest of its work; all threads meet at a final cluster barrier, so that no
 // CTA leaves while a peer may still write into its shared memory.
@@ -56,7 +63,8 @@ constexpr int kMaxPanels = kMlpMaxWidth / kPanel; // 8
 constexpr int kRing = 5;
 constexpr int kMaxCluster = 4;
 constexpr int kEpiWarps = 8;                      // two per TMEM lane quarter
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kXchgWarp = 2 + kEpiWarps;          // the warp that sends the slices
+constexpr int kThreads = 64 + 32 * kEpiWarps + 32;
 constexpr int kTmemCols = 512;
 constexpr int kActBytes = kMaxPanels * kPanelBytes;
 constexpr int kRingOffset = kActBytes;
@@ -168,6 +176,10 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float va[1
   }
 }
 
+// First TMEM column of layer l's accumulator (slice width ns): where a slice fits in 256
+// columns, layers alternate between columns 0 and 256; wider slices always start at 0.
+__device__ __forceinline__ uint32_t acc_column(int ns, int l) { return (ns <= 256 && (l & 1)) ? 256u : 0u; }
+
 // Named barrier of the epilogue warps only.
 __device__ __forceinline__ void epilogue_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");
@@ -183,10 +195,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
   uint64_t* empty = full + kRing;
   uint64_t* a0_full = empty + kRing;
   uint64_t* mma_done = a0_full + 1;
-  uint64_t* act_own = mma_done + 1;
-  uint64_t* act_from = act_own + 1;          // [kMaxCluster], indexed by the sending CTA
+  uint64_t* panel_ready = mma_done + 1;      // [kMaxPanels], panels of this CTA's slice
+  uint64_t* act_from = panel_ready + kMaxPanels;   // [kMaxCluster], indexed by the sending CTA
   uint64_t* peers_done = act_from + kMaxCluster;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(peers_done + 1);
+  uint64_t* copies_landed = peers_done + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(copies_landed + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -201,9 +214,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
     }
     mbar_init(a0_full, 1);
     mbar_init(mma_done, 1);
-    mbar_init(act_own, 1);
+    for (int i = 0; i < kMaxPanels; ++i) mbar_init(&panel_ready[i], 32 * kEpiWarps);
     for (int k = 0; k < kMaxCluster; ++k) mbar_init(&act_from[k], 1);   // local arrival + CTA k's bytes
     mbar_init(peers_done, C);      // one arrival per CTA
+    mbar_init(copies_landed, C > 1 ? C - 1 : 1);
     *abort_flag = 0;
     mbar_fence_init();
   }
@@ -257,9 +271,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
       int used = 0;
       bool ok = true;
       for (int l = 0; l < a.L && ok; ++l) {
-        // layer 0: the features by TMA; layer l > 0: this CTA's own slice first, then each
-        // peer's slice when its copy has landed
-        const bool in_ok = l == 0 ? mbar_wait(a0_full, 0) : mbar_wait(act_own, (l - 1) & 1);
+        const int ns = a.dims[l + 1] / C, KP = panels_of(a.dims[l]);
+        const int pps = l == 0 ? KP : KP / C;   // panels per slice of the input
+        const int own0 = l == 0 ? 0 : j * pps;
+        const uint32_t acc = acc_column(ns, l);
+        // layer 0: the features by TMA.  Layer l > 0: this CTA's own panels as the epilogue
+        // writes them, then each peer's slice when its copies have landed; where this
+        // layer's accumulator overlaps the previous one, first the epilogue's last panel
+        // (it has read the whole accumulator then).
+        uint32_t have = l == 0 ? 0xFFu : 0u;    // bit p: input panel p is in shared memory
+        bool in_ok = true;
+        if (l == 0) {
+          in_ok = mbar_wait(a0_full, 0);
+        } else {
+          const int pns = a.dims[l] / C;
+          const uint32_t pacc = acc_column(pns, l - 1);
+          if (pacc < acc + ns && acc < pacc + pns) in_ok = mbar_wait(&panel_ready[pps - 1], (l - 1) & 1);
+        }
         if (*(volatile int*)abort_flag || !in_ok) {
           *(volatile int*)abort_flag = 1;
           atomicExch(err_flag, 23);
@@ -267,17 +295,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
         }
         fence_async_smem();
         tc_fence_after();
-        const int ns = a.dims[l + 1] / C, KP = panels_of(a.dims[l]);
-        const int pps = l == 0 ? KP : KP / C;   // panels per slice of the input
-        const int own0 = l == 0 ? 0 : j * pps;
-        uint32_t landed = 1u << j;              // bit k: CTA k's slice is in this CTA's panels
         for (int c0 = 0; c0 < ns && ok; c0 += kChunk) {
           const uint32_t idesc = idesc_bf16(kRows, min(kChunk, ns - c0));
           for (int i = 0; i < KP; ++i) {
             const int p = (own0 + i) % KP;
-            if (l > 0 && !((landed >> (p / pps)) & 1u)) {
+            if (!((have >> p) & 1u)) {
               const int src = p / pps;
-              if (*(volatile int*)abort_flag || !wait_cluster(&act_from[src], (l - 1) & 1)) {
+              const bool got = src == j ? mbar_wait(&panel_ready[p - own0], (l - 1) & 1)
+                                        : wait_cluster(&act_from[src], (l - 1) & 1);
+              if (*(volatile int*)abort_flag || !got) {
                 *(volatile int*)abort_flag = 1;
                 atomicExch(err_flag, 28);
                 ok = false;
@@ -285,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
               }
               fence_async_smem();
               tc_fence_after();
-              landed |= 1u << src;
+              have |= src == j ? (1u << p) : (((1u << pps) - 1u) << (src * pps));
             }
             const int s = used % kRing;
             const uint32_t ph = (used / kRing) & 1;
@@ -299,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
             const uint32_t aa = smem_u32(act + p * kPanelBytes), bb = smem_u32(ring + s * kTileBytes);
 #pragma unroll
             for (int kk = 0; kk < kPanel / 16; ++kk)
-              umma_bf16(tmem + c0, sw128_desc(aa + kk * 32), sw128_desc(bb + kk * 32), idesc, (i | kk) != 0);
+              umma_bf16(tmem + acc + c0, sw128_desc(aa + kk * 32), sw128_desc(bb + kk * 32), idesc, (i | kk) != 0);
             umma_commit(&empty[s]);
             ++used;
           }
@@ -308,6 +334,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
       }
     }
     __syncwarp();
+  } else if (warp == kXchgWarp) {
+    if (C > 1) {
+      // per hidden layer: once this CTA's MMAs are done, expect the peers' slices and
+      // announce it to every CTA; once every CTA's are done, copy each panel of this CTA's
+      // slice to every peer as the epilogue finishes it; then tell each peer when its
+      // slice has landed here.  Lane k talks to CTA k (lane i >= 1 copies to CTA j - i),
+      // so the remote operations of one step fly together.
+      bool ok = true;
+      for (int l = 0; l + 1 < a.L && ok; ++l) {
+        const int ns = a.dims[l + 1] / C, pps = ns / kPanel;
+        const uint32_t slice = (uint32_t)pps * kPanelBytes;
+        ok = mbar_wait(mma_done, l & 1) && !*(volatile int*)abort_flag;
+        if (ok) {
+          if (lane < C && lane != j) mbar_expect_tx(&act_from[lane], slice);
+          __syncwarp();
+          if (lane < C) arrive_remote(peers_done, (uint32_t)lane);
+          ok = wait_cluster(peers_done, l & 1) && !*(volatile int*)abort_flag;
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        for (int pi = 0; pi < pps && ok; ++pi) {
+          ok = __all_sync(0xffffffffu, mbar_wait(&panel_ready[pi], l & 1) && !*(volatile int*)abort_flag);
+          if (ok && lane >= 1 && lane < C)
+            bulk_to_peer(act + (j * pps + pi) * kPanelBytes, kPanelBytes, &act_from[j], (uint32_t)((j - lane + C) % C));
+        }
+        if (ok && lane >= 1 && lane < C) {
+          const uint32_t k = (uint32_t)((j + lane) % C);
+          ok = wait_cluster(&act_from[k], l & 1);
+          if (ok) arrive_remote(copies_landed, k);
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok && lane == 0) {
+          *(volatile int*)abort_flag = 1;
+          atomicExch(err_flag, 26);
+        }
+      }
+    }
   } else {
     // epilogue: warp w owns TMEM lanes (rows) 32 (w % 4) .. +31 and the 16-column groups
     // g of each slice with g % 2 == half
@@ -351,24 +413,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
         break;
       }
       const int groups = ns / 16;
+      const uint32_t lane_acc = lane_base + acc_column(ns, l);
       if (!last) {
-        const uint32_t slice = (uint32_t)(ns / kPanel) * kPanelBytes;
-        if (C > 1 && ew == 0 && lane == 0) {
-          // the next input's incoming slices (their bytes), and this CTA's MMAs of the
-          // layer are done: once every CTA's are, no tensor core reads the panels that the
-          // slice copies overwrite
-          for (int k = 0; k < C; ++k)
-            if (k != j) mbar_expect_tx(&act_from[k], slice);
-          for (int k = 0; k < C; ++k) arrive_remote(peers_done, k);
+        // this CTA's slice of the next layer's input into its own panels, one panel after
+        // the other: its own MMAs of this layer are done, and (from the second hidden layer
+        // on) the copy engine has sent the slice these panels hold
+        if (C > 1 && l > 0) {
+          ok = mbar_wait(copies_landed, (l - 1) & 1) && !*(volatile int*)abort_flag;
+          if (!__all_sync(0xffffffffu, ok)) {
+            *(volatile int*)abort_flag = 1;
+            atomicExch(err_flag, 29);
+            ok = false;
+            break;
+          }
         }
-        // this CTA's slice of the next layer's input into its own panels (which only its
-        // own MMAs read)
 #pragma unroll 1
         for (int g = half; g < groups; g += 4) {
           // groups g and g + 2 of this warp: two TMEM loads, one wait
           const bool two = g + 2 < groups;
           float va[16], vb[16];
-          tmem_ld16x2(lane_base + 16 * g, lane_base + 16 * (two ? g + 2 : g), va, vb);
+          tmem_ld16x2(lane_acc + 16 * g, lane_acc + 16 * (two ? g + 2 : g), va, vb);
 #pragma unroll
           for (int i = 0; i < 16; ++i) va[i] = fmaxf(va[i] + cb[16 * g + i], 0.f);
           put16_local(act, r, cbase + 16 * g, va);
@@ -377,30 +441,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_forcing_cluster(const __grid_co
             for (int i = 0; i < 16; ++i) vb[i] = fmaxf(vb[i] + cb[16 * (g + 2) + i], 0.f);
             put16_local(act, r, cbase + 16 * (g + 2), vb);
           }
-        }
-        fence_async_smem();   // the slice is read by the copy engine and the tensor core
-        tc_fence_before();
-        epilogue_sync();
-        if (ew == 0 && lane == 0) {
-          mbar_arrive(act_own);   // the next layer's MMAs may start on this slice
-          if (C > 1) {
-            // the slice (whole panels) to every other CTA of the cluster, CTA j - 1 first
-            // (the order in which the receivers' K loops take the slices), on the
-            // receivers' act_from[j]
-            if (wait_cluster(peers_done, l & 1) && !*(volatile int*)abort_flag) {
-              uint8_t* src = act + (cbase / kPanel) * kPanelBytes;
-              for (int i = 1; i < C; ++i) bulk_to_peer(src, slice, &act_from[j], (uint32_t)((j - i + C) % C));
-            } else {
-              *(volatile int*)abort_flag = 1;
-              atomicExch(err_flag, 26);
-            }
-          }
+          // the panel is read by the copy engine and the tensor core
+          fence_async_smem();
+          tc_fence_before();
+          mbar_arrive(&panel_ready[g / 4]);
         }
       } else {
 #pragma unroll 1
         for (int g = half; g < groups; g += 2) {
           float v[16];
-          tmem_ld16(lane_base + 16 * g, v);
+          tmem_ld16(lane_acc + 16 * g, v);
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] = (v[i] + cb[16 * g + i]) * cs[16 * g + i] + ch[16 * g + i];
           if (row_ok) {
