@@ -100,10 +100,31 @@ int nn_forcing_infer(const nn_model* net, const dg_ctx* ctx, const double* q, fl
 int nn_train_step(nn_model* net, const float* X, const float* Y, const int64_t* idx, int batch,
                   const nn_adam* hp, float* loss_out, void* stream);
 
+/* The two halves of nn_train_step, for data-parallel training over ranks that each hold
+ * part of a batch (the MSE of Sec. 2.2 is a mean over rows, so its gradient is the sum of
+ * the ranks' shares):
+ *   nn_backward: forward, MSE and backward of rows idx[0..batch) of X and Y (as in
+ *     nn_train_step) into the model's gradient buffers, normalised over global_batch rows
+ *     (>= batch; = batch: the plain gradient of this batch).  loss_out (HOST, may be
+ *     NULL; synchronises the stream) receives this call's share of the loss, the sum of
+ *     its squared errors over global_batch x n_out.  No parameter changes.
+ *   nn_grad_buffers: DEVICE addresses of layer l's gradient buffers, dW [out][in] and db
+ *     [out] FP32, owned by the model and valid until nn_destroy; a caller may all-reduce
+ *     them in place between the two calls.
+ *   nn_adam_apply: one Adam step of every parameter from the gradient buffers (hp as in
+ *     nn_train_step), refreshing the BF16 copies.
+ * nn_train_step(batch) is nn_backward(batch, batch) followed by nn_adam_apply, with the
+ * same launches in the same order.  Errors as nn_train_step; DG_ERR_INVALID_ARG for
+ * global_batch < batch or a bad layer. */
+int nn_backward(nn_model* net, const float* X, const float* Y, const int64_t* idx, int batch, int global_batch,
+                float* loss_out, void* stream);
+int nn_grad_buffers(nn_model* net, int layer, float** dW, float** db);
+int nn_adam_apply(nn_model* net, const nn_adam* hp, void* stream);
+
 /* Layer l (0 .. n_hidden) weights [out][in] and biases [out], FP32 master copy (HOST). */
 int nn_get_params(const nn_model* net, int layer, float* W, float* b);
 int nn_set_params(nn_model* net, int layer, const float* W, const float* b);
-/* Gradients of layer l from the last nn_train_step (HOST). */
+/* Gradients of layer l from the last nn_train_step or nn_backward (HOST). */
 int nn_get_grads(const nn_model* net, int layer, float* dW, float* db);
 /* Description of the network (HOST). */
 int nn_get_desc(const nn_model* net, nn_desc* desc);

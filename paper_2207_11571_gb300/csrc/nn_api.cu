@@ -128,15 +128,17 @@ __global__ void k_prep_state_f32(const float* __restrict__ qf, long long N, int 
 }
 
 // MSE against scaled targets: dy = 2 (y - t_s) / (rows n), partial sums of (y - t_s)^2.
+// dL/dy of the MSE over norm_rows x n values, of which this launch holds rows x n (the
+// rest on other ranks of a data-parallel step; norm_rows = rows: the whole batch).
 __global__ void k_loss(const float* __restrict__ y, const float* __restrict__ Y, const int64_t* __restrict__ idx,
-                       int rows, int n, const float* __restrict__ mean, const float* __restrict__ sd,
+                       int rows, int norm_rows, int n, const float* __restrict__ mean, const float* __restrict__ sd,
                        float* __restrict__ dy, double* __restrict__ partial) {
   pdl_enter();
   // rows over blocks, features over threads; FP32 sums of a few squares per thread, a
   // warp-shuffle reduction, then the warps' sums added in FP64 in a fixed order
   __shared__ float wsum[kLossThreads / 32];
   float acc = 0.f;
-  const float g = 2.f / ((float)rows * (float)n);
+  const float g = 2.f / ((float)norm_rows * (float)n);
   for (int r = blockIdx.x; r < rows; r += gridDim.x) {
     const long long src = idx ? idx[r] : r;
     const float* Yr = Y + src * n;
@@ -599,6 +601,131 @@ int nn_forcing_on_state(const nn_model* m, const dg_ctx* c, const double* q, flo
 
 }  // namespace dgnn
 
+namespace dgnn {
+namespace {
+
+bool adam_ok(const nn_adam& a) {
+  return a.lr >= 0.f && std::isfinite(a.lr) && a.beta1 >= 0.f && a.beta1 < 1.f && a.beta2 >= 0.f && a.beta2 < 1.f &&
+         a.eps > 0.f && std::isfinite(a.eps);
+}
+
+// Forward, MSE and backward of `batch` rows into the model's gradient buffers, normalised
+// over norm_batch rows (a data-parallel step's global batch).  The loss share goes to
+// m->loss_dev.
+int backward_into_grads(nn_model* m, const float* X, const float* Y, const int64_t* idx, int batch, int norm_batch,
+                        cudaStream_t st) {
+  const int L = m->L, n_out = m->d.n_out;
+  // forward, keeping every layer input (bf16) in act[]
+  long long tot = (long long)batch * m->pad[0];
+  DG_CUDA(pdl_launch(k_prep_features, dim3(blocks_for(tot, 256)), dim3(256), st, X, idx, batch, m->d.n_in, m->pad[0], m->mean_in, m->std_in,
+                                                        m->act[0]));
+  DG_CUDA(cudaGetLastError());
+  int rc = forward_layers(m, batch, nullptr, st);
+  if (rc) return rc;
+  // loss and dL/dy
+  DG_CUDA(pdl_launch(k_loss, dim3(kLossBlocks), dim3(kLossThreads), st, m->y, Y, idx, batch, norm_batch, n_out, m->mean_out,
+                     m->std_out, m->dy, m->loss_part));
+  DG_CUDA(cudaGetLastError());
+  DG_CUDA(pdl_launch(k_sum_partials, dim3(1), dim3(kLossThreads), st, m->loss_part, kLossBlocks,
+                     1.0 / ((double)norm_batch * n_out), m->loss_dev));
+  DG_CUDA(cudaGetLastError());
+  // backward
+  float* g = m->dy;   // gradient w.r.t. the output of layer l, [batch][dims[l+1]]
+  float* gnext = m->dx;
+  for (int l = L - 1; l >= 0; --l) {
+    const int o = m->dims[l + 1], in = m->dims[l];
+    const int ldb = round_up(o, 64);
+    const int tiles = m->bpad / 32;
+    dim3 gp(ldb / 32, tiles), bt(32, 8);
+    DG_CUDA(pdl_launch(k_grad_prep, dim3(gp), dim3(bt), st, g, batch, o, ldb, m->bpad, m->dyb, m->dyT, m->gpart));
+    DG_CUDA(cudaGetLastError());
+    DG_CUDA(pdl_launch(k_col_sum, dim3((o + 31) / 32), dim3(dim3(32, 32)), st, m->gpart, tiles, o, m->gb[l]));
+    DG_CUDA(cudaGetLastError());
+    dim3 gt((in + 31) / 32, (m->bpad + 31) / 32);
+    DG_CUDA(pdl_launch(k_transpose_bf16, dim3(gt), dim3(bt), st, m->act[l], batch, in, m->pad[l], m->bpad, m->actT[l]));
+    DG_CUDA(cudaGetLastError());
+    // dW = g^T act : M = o, N = in, K = batch.  Few output tiles and a long K: split K
+    // so that the CTAs cover the SMs, then sum the partial products in a fixed order.
+    GemmEpilogue ew;
+    ew.kind = kGemmF32;
+    ew.ldo = in;
+    const int tiles_mn = ((o + 127) / 128) * ((in + gemm_pick_bn(o, in) - 1) / gemm_pick_bn(o, in));
+    const int kslices = (batch + 63) / 64;
+    const int splits = std::max(1, std::min({kMaxSplits, kslices, 152 / tiles_mn}));
+    if (splits > 1) {
+      ew.out = m->gws;
+      ew.splits = splits;
+      ew.split_stride = (long long)o * in;
+    } else {
+      ew.out = m->gW[l];
+    }
+    rc = gemm_bf16(m->dyT, m->bpad, m->actT[l], m->bpad, o, in, batch, ew, m->err, st);
+    if (rc) return rc;
+    if (splits > 1) {
+      const long long cnt = (long long)o * in;
+      DG_CUDA(pdl_launch(k_split_sum, dim3(blocks_for(cnt, 256)), dim3(256), st, m->gws, splits, cnt, m->gW[l]));
+      DG_CUDA(cudaGetLastError());
+    }
+    if (l > 0) {
+      // d act = g W, masked by the ReLU of the layer that produced act[l]
+      GemmEpilogue ex;
+      ex.kind = kGemmMaskF32;
+      ex.mask = m->act[l];
+      ex.ldm = m->pad[l];
+      ex.out = gnext;
+      ex.ldo = in;
+      rc = gemm_bf16(m->dyb, ldb, m->Wt[l], m->pad[l + 1], batch, in, o, ex, m->err, st);
+      if (rc) return rc;
+      std::swap(g, gnext);
+    }
+  }
+  return DG_OK;
+}
+
+// One Adam step of every parameter from the gradient buffers (also refreshes the bf16
+// copies of the weights).
+int adam_apply(nn_model* m, const nn_adam& a, cudaStream_t st) {
+  const int L = m->L;
+  ++m->adam_t;
+  const float bc1 = 1.f - std::pow(a.beta1, (float)m->adam_t);
+  const float bc2 = 1.f - std::pow(a.beta2, (float)m->adam_t);
+  AdamTable at{};
+  at.lr = a.lr;
+  at.b1 = a.beta1;
+  at.b2 = a.beta2;
+  at.eps = a.eps;
+  at.bc1 = bc1;
+  at.bc2 = bc2;
+  int blocks = 0;
+  for (int l = 0; l < L; ++l) {
+    const long long cw = (long long)m->dims[l] * m->dims[l + 1];
+    at.block_start[at.n] = blocks;
+    at.seg[at.n++] = AdamSeg{m->W[l], m->gW[l], m->mW[l], m->vW[l], cw, m->dims[l], m->Wb[l], m->pad[l], m->Wt[l],
+                             m->pad[l + 1]};
+    blocks += (int)blocks_for(cw, 256);
+    const long long cb = m->dims[l + 1];
+    at.block_start[at.n] = blocks;
+    at.seg[at.n++] = AdamSeg{m->b[l], m->gb[l], m->mb[l], m->vb[l], cb, 1, nullptr, 0, nullptr, 0};
+    blocks += (int)blocks_for(cb, 256);
+  }
+  at.block_start[at.n] = blocks;
+  DG_CUDA(pdl_launch(k_adam, dim3(blocks), dim3(256), st, at));
+  DG_CUDA(cudaGetLastError());
+  return DG_OK;
+}
+
+int loss_to_host(nn_model* m, float* loss_out, cudaStream_t st) {
+  if (!loss_out) return DG_OK;
+  DG_CUDA(cudaMemcpyAsync(m->loss_host, m->loss_dev, 8, cudaMemcpyDeviceToHost, st));
+  int rc = check_err(m, st);
+  if (rc) return rc;
+  *loss_out = (float)*m->loss_host;
+  return DG_OK;
+}
+
+}  // namespace
+}  // namespace dgnn
+
 using namespace dgnn;
 
 extern "C" {
@@ -737,107 +864,41 @@ int nn_train_step(nn_model* m, const float* X, const float* Y, const int64_t* id
   if (batch < 1 || batch > m->d.max_batch) return fail(DG_ERR_INVALID_ARG, "nn_train_step: batch outside [1, max_batch]");
   nn_adam a{1e-3f, 0.9f, 0.999f, 1e-7f};
   if (hp) a = *hp;
-  if (!(a.lr >= 0.f) || !std::isfinite(a.lr) || !(a.beta1 >= 0.f && a.beta1 < 1.f) ||
-      !(a.beta2 >= 0.f && a.beta2 < 1.f) || !(a.eps > 0.f) || !std::isfinite(a.eps))
+  if (!adam_ok(a))
     return fail(DG_ERR_INVALID_ARG, "nn_train_step: Adam needs lr >= 0, beta1 and beta2 in [0, 1), eps > 0 (finite)");
   cudaStream_t st = (cudaStream_t)stream;
-  const int L = m->L, n_out = m->d.n_out;
-  // forward, keeping every layer input (bf16) in act[]
-  long long tot = (long long)batch * m->pad[0];
-  DG_CUDA(pdl_launch(k_prep_features, dim3(blocks_for(tot, 256)), dim3(256), st, X, idx, batch, m->d.n_in, m->pad[0], m->mean_in, m->std_in,
-                                                        m->act[0]));
-  DG_CUDA(cudaGetLastError());
-  int rc = forward_layers(m, batch, nullptr, st);
+  int rc = backward_into_grads(m, X, Y, idx, batch, batch, st);
   if (rc) return rc;
-  // loss and dL/dy
-  DG_CUDA(pdl_launch(k_loss, dim3(kLossBlocks), dim3(kLossThreads), st, m->y, Y, idx, batch, n_out, m->mean_out, m->std_out, m->dy,
-                                               m->loss_part));
-  DG_CUDA(cudaGetLastError());
-  DG_CUDA(pdl_launch(k_sum_partials, dim3(1), dim3(kLossThreads), st, m->loss_part, kLossBlocks, 1.0 / ((double)batch * n_out), m->loss_dev));
-  DG_CUDA(cudaGetLastError());
-  // backward
-  float* g = m->dy;   // gradient w.r.t. the output of layer l, [batch][dims[l+1]]
-  float* gnext = m->dx;
-  for (int l = L - 1; l >= 0; --l) {
-    const int o = m->dims[l + 1], in = m->dims[l];
-    const int ldb = round_up(o, 64);
-    const int tiles = m->bpad / 32;
-    dim3 gp(ldb / 32, tiles), bt(32, 8);
-    DG_CUDA(pdl_launch(k_grad_prep, dim3(gp), dim3(bt), st, g, batch, o, ldb, m->bpad, m->dyb, m->dyT, m->gpart));
-    DG_CUDA(cudaGetLastError());
-    DG_CUDA(pdl_launch(k_col_sum, dim3((o + 31) / 32), dim3(dim3(32, 32)), st, m->gpart, tiles, o, m->gb[l]));
-    DG_CUDA(cudaGetLastError());
-    dim3 gt((in + 31) / 32, (m->bpad + 31) / 32);
-    DG_CUDA(pdl_launch(k_transpose_bf16, dim3(gt), dim3(bt), st, m->act[l], batch, in, m->pad[l], m->bpad, m->actT[l]));
-    DG_CUDA(cudaGetLastError());
-    // dW = g^T act : M = o, N = in, K = batch.  Few output tiles and a long K: split K
-    // so that the CTAs cover the SMs, then sum the partial products in a fixed order.
-    GemmEpilogue ew;
-    ew.kind = kGemmF32;
-    ew.ldo = in;
-    const int tiles_mn = ((o + 127) / 128) * ((in + gemm_pick_bn(o, in) - 1) / gemm_pick_bn(o, in));
-    const int kslices = (batch + 63) / 64;
-    const int splits = std::max(1, std::min({kMaxSplits, kslices, 152 / tiles_mn}));
-    if (splits > 1) {
-      ew.out = m->gws;
-      ew.splits = splits;
-      ew.split_stride = (long long)o * in;
-    } else {
-      ew.out = m->gW[l];
-    }
-    rc = gemm_bf16(m->dyT, m->bpad, m->actT[l], m->bpad, o, in, batch, ew, m->err, st);
-    if (rc) return rc;
-    if (splits > 1) {
-      const long long cnt = (long long)o * in;
-      DG_CUDA(pdl_launch(k_split_sum, dim3(blocks_for(cnt, 256)), dim3(256), st, m->gws, splits, cnt, m->gW[l]));
-      DG_CUDA(cudaGetLastError());
-    }
-    if (l > 0) {
-      // d act = g W, masked by the ReLU of the layer that produced act[l]
-      GemmEpilogue ex;
-      ex.kind = kGemmMaskF32;
-      ex.mask = m->act[l];
-      ex.ldm = m->pad[l];
-      ex.out = gnext;
-      ex.ldo = in;
-      rc = gemm_bf16(m->dyb, ldb, m->Wt[l], m->pad[l + 1], batch, in, o, ex, m->err, st);
-      if (rc) return rc;
-      std::swap(g, gnext);
-    }
-  }
-  // Adam
-  ++m->adam_t;
-  const float bc1 = 1.f - std::pow(a.beta1, (float)m->adam_t);
-  const float bc2 = 1.f - std::pow(a.beta2, (float)m->adam_t);
-  AdamTable at{};
-  at.lr = a.lr;
-  at.b1 = a.beta1;
-  at.b2 = a.beta2;
-  at.eps = a.eps;
-  at.bc1 = bc1;
-  at.bc2 = bc2;
-  int blocks = 0;
-  for (int l = 0; l < L; ++l) {
-    const long long cw = (long long)m->dims[l] * m->dims[l + 1];
-    at.block_start[at.n] = blocks;
-    at.seg[at.n++] = AdamSeg{m->W[l], m->gW[l], m->mW[l], m->vW[l], cw, m->dims[l], m->Wb[l], m->pad[l], m->Wt[l],
-                             m->pad[l + 1]};
-    blocks += (int)blocks_for(cw, 256);
-    const long long cb = m->dims[l + 1];
-    at.block_start[at.n] = blocks;
-    at.seg[at.n++] = AdamSeg{m->b[l], m->gb[l], m->mb[l], m->vb[l], cb, 1, nullptr, 0, nullptr, 0};
-    blocks += (int)blocks_for(cb, 256);
-  }
-  at.block_start[at.n] = blocks;
-  DG_CUDA(pdl_launch(k_adam, dim3(blocks), dim3(256), st, at));
-  DG_CUDA(cudaGetLastError());
-  if (loss_out) {
-    DG_CUDA(cudaMemcpyAsync(m->loss_host, m->loss_dev, 8, cudaMemcpyDeviceToHost, st));
-    rc = check_err(m, st);
-    if (rc) return rc;
-    *loss_out = (float)*m->loss_host;
-  }
+  rc = adam_apply(m, a, st);
+  if (rc) return rc;
+  return loss_to_host(m, loss_out, st);
+}
+
+int nn_backward(nn_model* m, const float* X, const float* Y, const int64_t* idx, int batch, int global_batch,
+                float* loss_out, void* stream) {
+  if (!m || !X || !Y) return fail(DG_ERR_INVALID_ARG, "nn_backward: NULL argument");
+  if (batch < 1 || batch > m->d.max_batch) return fail(DG_ERR_INVALID_ARG, "nn_backward: batch outside [1, max_batch]");
+  if (global_batch < batch) return fail(DG_ERR_INVALID_ARG, "nn_backward: global_batch < batch");
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = backward_into_grads(m, X, Y, idx, batch, global_batch, st);
+  if (rc) return rc;
+  return loss_to_host(m, loss_out, st);
+}
+
+int nn_grad_buffers(nn_model* m, int l, float** dW, float** db) {
+  if (!m || l < 0 || l >= m->L) return fail(DG_ERR_INVALID_ARG, "nn_grad_buffers: bad layer");
+  if (dW) *dW = m->gW[l];
+  if (db) *db = m->gb[l];
   return DG_OK;
+}
+
+int nn_adam_apply(nn_model* m, const nn_adam* hp, void* stream) {
+  if (!m) return fail(DG_ERR_INVALID_ARG, "nn_adam_apply: NULL model");
+  nn_adam a{1e-3f, 0.9f, 0.999f, 1e-7f};
+  if (hp) a = *hp;
+  if (!adam_ok(a))
+    return fail(DG_ERR_INVALID_ARG, "nn_adam_apply: Adam needs lr >= 0, beta1 and beta2 in [0, 1), eps > 0 (finite)");
+  return adam_apply(m, a, (cudaStream_t)stream);
 }
 
 int nn_get_params(const nn_model* m, int l, float* W, float* b) {

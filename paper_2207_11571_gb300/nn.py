@@ -34,6 +34,9 @@ _SIGS = {
     "nn_get_params": [_P, _I, _P, _P],
     "nn_set_params": [_P, _I, _P, _P],
     "nn_get_grads": [_P, _I, _P, _P],
+    "nn_backward": [_P, _P, _P, _P, _I, _I, ctypes.POINTER(ctypes.c_float), _P],
+    "nn_grad_buffers": [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P)],
+    "nn_adam_apply": [_P, ctypes.POINTER(nn_adam), _P],
     "nn_get_desc": [_P, ctypes.POINTER(nn_desc)],
     "nn_save": [_P, ctypes.c_char_p],
     "nn_load": [ctypes.c_char_p, _I, ctypes.POINTER(_P)],
@@ -174,6 +177,55 @@ def nn_train_step(net, X, Y, idx=None, batch=None, lr=1e-3, beta1=0.9, beta2=0.9
     dg.check(dg.lib().nn_train_step(_h(net), dg.ptr(X), dg.ptr(Y), dg.ptr(idx), int(batch), ctypes.byref(hp),
                                     ctypes.byref(loss) if want_loss else None, dg.stream_ptr(stream)))
     return loss.value if want_loss else None
+
+
+def nn_backward(net, X, Y, idx=None, batch=None, global_batch=None, want_loss=True, stream=None):
+    """Gradients of the MSE of rows idx of (X, Y) into the network's gradient buffers,
+    normalised over global_batch rows (default: this batch); returns this call's share of
+    the loss.  No parameter changes (nn_adam_apply does the update)."""
+    dg = _dg()
+    d = nn_get_desc(net)
+    rows = _check_rows(X, d.n_in, "X")
+    _check_rows(Y, d.n_out, "Y", rows)
+    if idx is not None:
+        _check_rows(idx, idx.numel(), "idx", rows=1, dtype="int64")
+    if batch is None:
+        batch = int(idx.numel()) if idx is not None else rows
+    if batch > (idx.numel() if idx is not None else rows):
+        raise ValueError(f"batch {batch} exceeds the rows available")
+    if global_batch is None:
+        global_batch = batch
+    loss = ctypes.c_float()
+    dg.check(dg.lib().nn_backward(_h(net), dg.ptr(X), dg.ptr(Y), dg.ptr(idx), int(batch), int(global_batch),
+                                  ctypes.byref(loss) if want_loss else None, dg.stream_ptr(stream)))
+    return loss.value if want_loss else None
+
+
+class _DeviceFloats:
+    """FP32 device memory of the library seen by torch (CUDA array interface, no copy)."""
+
+    def __init__(self, ptr, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(int(n) for n in shape), "typestr": "<f4",
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def nn_grad_buffers(net, layer):
+    """(dW [out][in], db [out]): torch views of layer `layer`'s gradient buffers on the
+    device (no copy), owned by the network; valid until nn_destroy."""
+    import torch
+    dg = _dg()
+    o, i = _layer_shape(net, layer)
+    pw, pb = ctypes.c_void_p(), ctypes.c_void_p()
+    dg.check(dg.lib().nn_grad_buffers(_h(net), int(layer), ctypes.byref(pw), ctypes.byref(pb)))
+    return (torch.as_tensor(_DeviceFloats(pw.value, (o, i)), device="cuda"),
+            torch.as_tensor(_DeviceFloats(pb.value, (o,)), device="cuda"))
+
+
+def nn_adam_apply(net, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-7, stream=None):
+    """One Adam step of every parameter from the gradient buffers."""
+    dg = _dg()
+    hp = nn_adam(lr, beta1, beta2, eps)
+    dg.check(dg.lib().nn_adam_apply(_h(net), ctypes.byref(hp), dg.stream_ptr(stream)))
 
 
 def _layer_shape(net, layer):

@@ -125,3 +125,59 @@ def gather_diagnostics(ctx, q, group=None, q_ref=None):
         parts.append({"mass": v[0], "momentum": v[1:4], "energy": v[4], "ke": v[5], "dke_dt": v[6],
                       "e_inf": v[7:10], "max_wave": v[10], "nonfinite": int(v[11])})
     return dg.dg_diag_combine(parts, raise_nonfinite=False)
+
+
+# ----------------------------------------------------------------------------- training
+
+def dp_train_step(backward, grads, apply, local_batch, group=None):
+    """One data-parallel optimisation step over the ranks of ``group``, each holding
+    ``local_batch`` rows of the batch.  The MSE of Sec. 2.2 is a mean over the batch's
+    rows, so its gradient is the sum over ranks of each rank's gradient normalised by the
+    global row count:
+
+    * ``backward(global_batch)`` computes this rank's share (gradients into the tensors
+      ``grads()`` returns, normalised over ``global_batch`` rows) and returns its share of
+      the loss;
+    * the gradient tensors are summed over the ranks in place (``all_reduce``; every rank
+      receives the same sums, so the parameters stay identical on every rank);
+    * ``apply()`` takes the optimiser step.
+
+    Returns the loss of the whole batch (the sum of the shares)."""
+    import torch
+    import torch.distributed as dist
+    cpu = dist.get_backend(group) == "gloo"
+    dev = "cpu" if cpu else "cuda"
+    n = torch.tensor([int(local_batch)], dtype=torch.int64, device=dev)
+    dist.all_reduce(n, group=group)
+    loss = backward(int(n.item()))
+    for t in grads():
+        if cpu and t.is_cuda:   # gloo reduces host tensors
+            h = t.cpu()
+            dist.all_reduce(h, group=group)
+            t.copy_(h)
+        else:
+            dist.all_reduce(t, group=group)
+    apply()
+    tot = torch.tensor([float(loss)], dtype=torch.float64, device=dev)
+    dist.all_reduce(tot, group=group)
+    return float(tot.item())
+
+
+def nn_dp_train_step(net, X, Y, idx=None, batch=None, group=None, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-7,
+                     stream=None):
+    """dp_train_step on the library's network: ``nn_backward`` normalised over the global
+    batch, an in-place all-reduce of every layer's gradient buffers, ``nn_adam_apply``."""
+    from . import nn
+    d = nn.nn_get_desc(net)
+    if batch is None:
+        batch = int(idx.numel()) if idx is not None else int(X.shape[0])
+    layers = d.n_hidden + 1
+
+    def bufs():
+        out = []
+        for layer in range(layers):
+            out.extend(nn.nn_grad_buffers(net, layer))
+        return out
+
+    return dp_train_step(lambda gb: nn.nn_backward(net, X, Y, idx, batch, gb, stream=stream), bufs,
+                         lambda: nn.nn_adam_apply(net, lr, beta1, beta2, eps, stream=stream), batch, group)

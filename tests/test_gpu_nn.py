@@ -478,3 +478,95 @@ def test_save_load_roundtrip_and_corruption_detection(L, tmp_path):
         nn.nn_load(tmp_path / "missing.bin")
     nn.nn_destroy(h)
     nn.nn_destroy(h2)
+
+
+def test_backward_then_adam_equals_train_step(L):
+    """nn_train_step is nn_backward (normalised over its own batch) followed by
+    nn_adam_apply: two networks with the same weights end bitwise equal after two steps,
+    with the same losses."""
+    from paper_2207_11571_gb300 import nn
+    n, B = 192, 200
+    X = torch.from_numpy(inputs.normal((B, n), 41).astype(np.float32)).cuda()
+    Y = torch.from_numpy(inputs.normal((B, n), 42).astype(np.float32)).cuda()
+    a, _ = make_net(nn, n, 128, 2, seed=43, max_batch=B, first_var=1, n_vars=3)
+    b, _ = make_net(nn, n, 128, 2, seed=43, max_batch=B, first_var=1, n_vars=3)
+    for h in (a, b):
+        nn.nn_compute_scalers(h, X, Y)
+    for _ in range(2):
+        la = nn.nn_train_step(a, X, Y, lr=2e-3)
+        lb = nn.nn_backward(b, X, Y)
+        nn.nn_adam_apply(b, lr=2e-3)
+        assert la == lb
+    for layer in range(3):
+        for x, y in zip(nn.nn_get_params(a, layer), nn.nn_get_params(b, layer)):
+            assert np.array_equal(x, y)
+    nn.nn_destroy(a)
+    nn.nn_destroy(b)
+
+
+def test_backward_shares_sum_to_the_batch_gradient(L):
+    """Data-parallel training on one device: two halves of a batch, each normalised over
+    the whole batch (nn_backward's global_batch), give gradients and loss shares that sum
+    to the whole batch's (FP32: the weight-gradient GEMMs sum the rows in other groups);
+    the gradient buffers seen through nn_grad_buffers are what nn_adam_apply reads (zeroed
+    gradients leave the parameters unchanged at Adam's first step)."""
+    from paper_2207_11571_gb300 import nn
+    n, B = 192, 256
+    X = torch.from_numpy(inputs.normal((B, n), 44).astype(np.float32)).cuda()
+    Y = torch.from_numpy(inputs.normal((B, n), 45).astype(np.float32)).cuda()
+    h, _ = make_net(nn, n, 256, 3, seed=46, max_batch=B, first_var=1, n_vars=3)
+    nn.nn_compute_scalers(h, X, Y)
+    idx = torch.arange(B, dtype=torch.int64, device="cuda")
+    full_loss = nn.nn_backward(h, X, Y, idx)
+    full = [g.clone() for layer in range(4) for g in nn.nn_grad_buffers(h, layer)]
+    l0 = nn.nn_backward(h, X, Y, idx[:100], global_batch=B)
+    part = [g.clone() for layer in range(4) for g in nn.nn_grad_buffers(h, layer)]
+    l1 = nn.nn_backward(h, X, Y, idx[100:], global_batch=B)
+    for f, p0, layer_g in zip(full, part, [g for layer in range(4) for g in nn.nn_grad_buffers(h, layer)]):
+        s = p0 + layer_g
+        assert ((s - f).norm() / f.norm()).item() < 1e-5
+    assert abs(l0 + l1 - full_loss) < 1e-6 * full_loss
+    before = [nn.nn_get_params(h, layer) for layer in range(4)]
+    for layer in range(4):
+        for g in nn.nn_grad_buffers(h, layer):
+            g.zero_()
+    nn.nn_adam_apply(h)
+    for layer in range(4):
+        for x, y in zip(before[layer], nn.nn_get_params(h, layer)):
+            assert np.array_equal(x, y)
+    nn.nn_destroy(h)
+
+
+def test_data_parallel_step_on_one_rank_equals_train_step(L):
+    """partition.nn_dp_train_step over a one-rank process group (the all-reduce is the
+    identity) equals nn_train_step bitwise."""
+    import socket
+
+    import torch.distributed as dist
+    from paper_2207_11571_gb300 import nn, partition
+    n, B = 192, 128
+    X = torch.from_numpy(inputs.normal((B, n), 47).astype(np.float32)).cuda()
+    Y = torch.from_numpy(inputs.normal((B, n), 48).astype(np.float32)).cuda()
+    a, _ = make_net(nn, n, 128, 2, seed=49, max_batch=B, first_var=1, n_vars=3)
+    b, _ = make_net(nn, n, 128, 2, seed=49, max_batch=B, first_var=1, n_vars=3)
+    for h in (a, b):
+        nn.nn_compute_scalers(h, X, Y)
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    group = None
+    own = not dist.is_initialized()
+    if own:
+        dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        la = nn.nn_train_step(a, X, Y)
+        lb = partition.nn_dp_train_step(b, X, Y, group=group)
+        assert abs(la - lb) <= 1e-7 * abs(la)
+        for layer in range(3):
+            for x, y in zip(nn.nn_get_params(a, layer), nn.nn_get_params(b, layer)):
+                assert np.array_equal(x, y)
+    finally:
+        if own:
+            dist.destroy_process_group()
+        nn.nn_destroy(a)
+        nn.nn_destroy(b)

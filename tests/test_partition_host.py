@@ -193,3 +193,69 @@ def test_diag_combine_sums_in_order_and_takes_maxima():
         dg.dg_diag_combine(parts)
     assert e.value.status == dg.DG_ERR_NONFINITE
     assert dg.dg_diag_combine(parts, raise_nonfinite=False)["nonfinite"] == 2
+
+
+def _dp_worker(rank, ws, port, q, shards, steps):
+    """Rank `rank` holds rows shards[rank] of the batch and runs dp_train_step with the
+    oracle MLP: its gradients normalised over the global batch, summed over ranks."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    from oracle import mlp
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        X, T, params, scalers = _dp_problem()
+        rows = np.asarray(shards[rank])
+        mean_in, std_in, mean_out, std_out = scalers
+        xs, ts = (X[rows] - mean_in) / std_in, (T[rows] - mean_out) / std_out
+        state, cur, losses = {}, [params], []
+        holder = {}
+
+        def backward(global_batch):
+            y, cache = mlp.forward(cur[0], xs)
+            diff = y - ts
+            g = mlp.backward(cur[0], cache, 2.0 * diff / (global_batch * diff.shape[1]))
+            holder["g"] = [torch.from_numpy(np.ascontiguousarray(a)) for gw, gb in g for a in (gw, gb)]
+            return float((diff ** 2).sum() / (global_batch * diff.shape[1]))
+
+        def apply():
+            t = [a.numpy() for a in holder["g"]]
+            cur[0] = mlp.adam_step(cur[0], [(t[2 * i], t[2 * i + 1]) for i in range(len(cur[0]))], state)
+
+        for _ in range(steps):
+            losses.append(partition.dp_train_step(backward, lambda: holder["g"], apply, len(rows)))
+        q.put((rank, [(W.copy(), b.copy()) for W, b in cur[0]], losses))
+    finally:
+        dist.destroy_process_group()
+
+
+def _dp_problem():
+    from oracle import mlp
+    dims = mlp.layer_dims(12, 12, 16, 2)
+    params = mlp.he_uniform_init(dims, inputs.uniform_draws(dims, 31))
+    X = inputs.normal((10, 12), 32)
+    T = inputs.normal((10, 12), 33)
+    scalers = (X.mean(0), X.std(0), T.mean(0), T.std(0))
+    return X, T, params, scalers
+
+
+@pytest.mark.parametrize("shards", [[range(0, 5), range(5, 10)], [range(0, 2), range(2, 9), range(9, 10)]])
+def test_data_parallel_training_equals_the_whole_batch(shards):
+    """Ranks holding uneven parts of a batch, each normalising its MSE gradient over the
+    global batch and summing the gradients over ranks, take the whole batch's Adam steps:
+    the parameters (identical on every rank) and the losses equal the oracle's
+    single-process train_step on all rows (FP64, to rounding of the reduction order)."""
+    from oracle import mlp
+    steps = 3
+    res = run_ranks(_dp_worker, len(shards), [list(s) for s in shards], steps)
+    X, T, params, scalers = _dp_problem()
+    state, ref_losses = {}, []
+    for _ in range(steps):
+        params, loss, _ = mlp.train_step(params, state, scalers, X, T)
+        ref_losses.append(loss)
+    for rank, got, losses in res:
+        for (W, b), (Wr, br) in zip(got, params):
+            np.testing.assert_allclose(W, Wr, rtol=0, atol=1e-12)
+            np.testing.assert_allclose(b, br, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(losses, ref_losses, rtol=1e-12)
+    for (_, a, _), (_, b, _) in zip(res, res[1:]):   # the same bits on every rank
+        assert all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1]) for x, y in zip(a, b))
