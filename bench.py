@@ -613,6 +613,8 @@ def run_ours(args, rank, ws):
                            "block_shape": shapes,
                            "streams": "one per mesh, forked from and joined to the timed stream every step",
                            "parallelism": f"replicas x{ws}", "per_workload": per_workload},
+                "value_x5_variables": {"value": 5 * value, "unit": "variable-stage updates/s",
+                                       "note": "the same rate counting each node's 5 conserved variables"},
                 "roofline": roofline, "kernels": per_kernel, "network": nn_line, "batched": batched,
                 "algorithm1": alg1,
                 "cpu_baseline": cpu, "e2e": e2e,
