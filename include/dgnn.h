@@ -213,14 +213,19 @@ int dg_advance_host(dg_ctx* ctx, double* q_host, double dt, int nsteps,
                     const nn_model* forcing, dg_diag* diag, void* stream);
 
 /* dg_advance_host in two calls, so that several contexts on several streams overlap
- * their copies with each other's kernels.  dg_advance_host_async enqueues on stream the
+ * their copies with each other's kernels, and a context's next call is queued before
+ * the previous one's results are read.  dg_advance_host_async enqueues on stream the
  * copy of q_host (HOST, 5 N doubles; pinned for the copies to run asynchronously) to
  * the context's device state, nsteps RK3 steps (as dg_rk3_step), the copy back into
- * q_host and, if want_diag != 0, the diagnostics of the final state into the context's
- * pinned buffer; it returns without waiting.  q_host must not be touched until
- * dg_advance_host_wait(ctx, diag, stream) returns: it synchronises stream and fills
- * *diag (HOST, may be NULL; non-NULL requires want_diag in the preceding async call,
- * else DG_ERR_INVALID_ARG).  One pending advance per context. */
+ * q_host and, if want_diag != 0, the diagnostics of the final state into a pinned slot
+ * of the context; it returns without waiting.  Up to two calls may be pending per
+ * context, both on the same stream (the second one's copy in follows the first one's
+ * copy back); a third call, or a second on another stream, returns DG_ERR_INVALID_ARG.
+ * dg_advance_host_wait(ctx, diag, stream) waits for the OLDEST pending call only (an
+ * event after its last copy; `stream` is used only when no call is pending, then it is
+ * synchronised) and fills *diag (HOST, may be NULL; non-NULL requires want_diag in that
+ * call, else DG_ERR_INVALID_ARG) from its slot.  A call's q_host must not be touched
+ * until its wait has returned; collect every pending call before dg_destroy. */
 int dg_advance_host_async(dg_ctx* ctx, double* q_host, double dt, int nsteps,
                           const nn_model* forcing, int want_diag, void* stream);
 int dg_advance_host_wait(dg_ctx* ctx, dg_diag* diag, void* stream);

@@ -213,10 +213,14 @@ static int rk3_steps(dg_ctx* c, double* q, double dt, int nsteps, const nn_model
   return rk3_steps_n(&c, 1, &q, dt, nsteps, net, st, exchange);
 }
 
-// Diagnostics in two parts: the reductions and the copy of their result into the
-// context's pinned buffer are enqueued on st; diag_collect waits for st and fills out.
+// Diagnostics in two parts: the reductions and the copy of their result into a pinned
+// host buffer (the context's, or a slot of its host-advance ring) are enqueued on st;
+// diag_collect waits for st and fills out from the context's buffer.
+constexpr int kHostSlot = kDiagLen + 1;   // the diagnostics and the error flag
+// slot: the device address of a mapped host-advance slot, or NULL for the context's buffer.
 static int diag_enqueue(dg_ctx* c, const double* q, const double* qref, const nn_model* net, bool with_rhs,
-                        cudaStream_t st) {
+                        cudaStream_t st, double* slot = nullptr) {
+  double* host = slot ? slot : c->red_host;
   const double* R = nullptr;
   if (with_rhs) {
     int rc = rhs_into(c, q, c->rhs_tmp, net, st);
@@ -225,21 +229,26 @@ static int diag_enqueue(dg_ctx* c, const double* q, const double* qref, const nn
   }
   double* dev_out = c->red + (size_t)c->red_blocks * kDiagLen;
   DG_CUDA(launch_diagnostics(c, q, R, qref, c->red, c->red_blocks, dev_out, st));
-  DG_CUDA(cudaMemcpyAsync(c->red_host, dev_out, kDiagLen * sizeof(double), cudaMemcpyDeviceToHost, st));
-  // the kernels' error flag rides along in the slot after the diagnostics
-  DG_CUDA(cudaMemcpyAsync(c->red_host + kDiagLen, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  // the kernels' error flag rides along in the slot after the diagnostics.  A host-advance
+  // slot is written by a kernel (its few bytes do not wait behind other streams' state
+  // copies on the copy engine); the synchronous paths copy.
+  if (slot) {
+    DG_CUDA(launch_store_host(dev_out, kDiagLen, c->err_dev, host, st));
+    return DG_OK;
+  }
+  DG_CUDA(cudaMemcpyAsync(host, dev_out, kDiagLen * sizeof(double), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaMemcpyAsync(host + kDiagLen, c->err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
   return DG_OK;
 }
 
-static int diag_collect(dg_ctx* c, bool with_rhs, bool with_ref, dg_diag* out, cudaStream_t st) {
-  DG_CUDA(cudaStreamSynchronize(st));
+// Fills out from the copied diagnostics r (and their error flag).
+static int diag_parse(dg_ctx* c, const double* r, bool with_rhs, bool with_ref, dg_diag* out) {
   int err = 0;
-  std::memcpy(&err, c->red_host + kDiagLen, sizeof(int));
+  std::memcpy(&err, r + kDiagLen, sizeof(int));
   if (err) {
     DG_CUDA(cudaMemset(c->err_dev, 0, sizeof(int)));
     return fail(DG_ERR_TIMEOUT, "a bounded wait in the streamed flux kernel expired (its results are invalid)");
   }
-  const double* r = c->red_host;
   const double vol = 8.0 * M_PI * M_PI * M_PI;
   std::memset(out, 0, sizeof(*out));
   out->mass = r[0];
@@ -251,6 +260,11 @@ static int diag_collect(dg_ctx* c, bool with_rhs, bool with_ref, dg_diag* out, c
   for (int i = 0; i < 3; ++i) out->e_inf[i] = with_ref ? r[8 + i] : 0.0;
   out->max_wave = r[11];
   return out->nonfinite ? fail(DG_ERR_NONFINITE, "state holds non-finite values") : DG_OK;
+}
+
+static int diag_collect(dg_ctx* c, bool with_rhs, bool with_ref, dg_diag* out, cudaStream_t st) {
+  DG_CUDA(cudaStreamSynchronize(st));
+  return diag_parse(c, c->red_host, with_rhs, with_ref, out);
 }
 
 static int diagnostics_into(dg_ctx* c, const double* q, const double* qref, const nn_model* net, bool with_rhs,
@@ -584,6 +598,9 @@ int dg_destroy(dg_ctx* c) {
   cudaFree(c->s_buf);
   cudaFree(c->q_dev);
   if (c->red_host) cudaFreeHost(c->red_host);
+  if (c->host_ring) cudaFreeHost(c->host_ring);
+  for (int i = 0; i < 2; ++i)
+    if (c->host_evt[i]) cudaEventDestroy(c->host_evt[i]);
   if (c->err_dev) cudaFree(c->err_dev);
   for (int i = 0; i <= kMaxP; ++i) cudaFree(c->filter_dev[i]);
   for (int i = 0; i <= kMaxP; ++i) cudaFree(c->prolong_dev[i]);
@@ -641,26 +658,49 @@ int dg_advance_host_async(dg_ctx* c, double* q_host, double dt, int nsteps, cons
   int prc = part_usable(c, forcing, "dg_advance_host_async");
   if (prc) return prc;
   cudaStream_t st = (cudaStream_t)stream;
+  if (c->host_pending == 2)
+    return fail(DG_ERR_INVALID_ARG, "dg_advance_host_async: two calls pending: collect one with dg_advance_host_wait");
+  if (c->host_pending == 1 && st != c->host_stream)
+    return fail(DG_ERR_INVALID_ARG, "dg_advance_host_async: a pending call is on another stream");
   const size_t bytes = 5 * c->N * sizeof(double);
   if (!c->q_dev) DG_CUDA(cudaMalloc(&c->q_dev, bytes));
+  if (!c->host_ring) {
+    DG_CUDA(cudaHostAlloc(&c->host_ring, 2 * kHostSlot * sizeof(double), cudaHostAllocMapped));
+    DG_CUDA(cudaHostGetDevicePointer(&c->host_ring_dev, c->host_ring, 0));
+    for (int i = 0; i < 2; ++i) DG_CUDA(cudaEventCreateWithFlags(&c->host_evt[i], cudaEventDisableTiming));
+  }
+  const int slot = (c->host_head + c->host_pending) % 2;
+  // a second pending call reuses the device state after the first's copy back (same stream)
   DG_CUDA(cudaMemcpyAsync(c->q_dev, q_host, bytes, cudaMemcpyHostToDevice, st));
   int rc = rk3_steps(c, c->q_dev, dt, nsteps, forcing, st);
   if (rc) return rc;
   DG_CUDA(cudaMemcpyAsync(q_host, c->q_dev, bytes, cudaMemcpyDeviceToHost, st));
-  c->host_diag_pending = want_diag != 0;
-  if (want_diag) return diag_enqueue(c, c->q_dev, nullptr, forcing, false, st);
+  if (want_diag) {
+    rc = diag_enqueue(c, c->q_dev, nullptr, forcing, false, st, c->host_ring_dev + slot * kHostSlot);
+    if (rc) return rc;
+  }
+  DG_CUDA(cudaEventRecord(c->host_evt[slot], st));
+  c->host_want[slot] = want_diag != 0;
+  c->host_stream = st;
+  ++c->host_pending;
   return DG_OK;
 }
 
 int dg_advance_host_wait(dg_ctx* c, dg_diag* diag, void* stream) {
   if (!c) return fail(DG_ERR_INVALID_ARG, "dg_advance_host_wait: NULL argument");
-  cudaStream_t st = (cudaStream_t)stream;
-  const bool pending = c->host_diag_pending;
-  c->host_diag_pending = false;
-  if (diag && pending) return diag_collect(c, false, false, diag, st);
-  DG_CUDA(cudaStreamSynchronize(st));
-  if (diag) return fail(DG_ERR_INVALID_ARG, "dg_advance_host_wait: no diagnostics were requested");
-  return DG_OK;
+  if (c->host_pending == 0) {
+    DG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (diag) return fail(DG_ERR_INVALID_ARG, "dg_advance_host_wait: no call is pending");
+    return DG_OK;
+  }
+  // the oldest pending call: its copy back and its diagnostics have landed after its event
+  const int slot = c->host_head;
+  c->host_head = (slot + 1) % 2;
+  --c->host_pending;
+  DG_CUDA(cudaEventSynchronize(c->host_evt[slot]));
+  if (!diag) return DG_OK;
+  if (!c->host_want[slot]) return fail(DG_ERR_INVALID_ARG, "dg_advance_host_wait: no diagnostics were requested");
+  return diag_parse(c, c->host_ring + slot * kHostSlot, false, false, diag);
 }
 
 int dg_advance_host(dg_ctx* c, double* q_host, double dt, int nsteps, const nn_model* forcing, dg_diag* diag,

@@ -188,6 +188,24 @@ cudaError_t launch_diagnostics(const dg_ctx* c, const double* q, const double* R
   return cudaGetLastError();
 }
 
+// n doubles and an int flag from device memory into pinned host memory (written by the
+// SMs through the coherent host mapping, not by the copy engine: a few bytes that must not
+// queue behind other streams' large copies).
+__global__ void k_store_host(const double* __restrict__ src, int n, const int* __restrict__ flag, double* host) {
+  const int i = threadIdx.x;
+  if (i < n) host[i] = src[i];
+  if (i == n) {
+    int f = *flag;
+    memcpy(host + n, &f, sizeof(int));
+  }
+}
+
+cudaError_t launch_store_host(const double* src, int n, const int* flag, double* host, cudaStream_t st) {
+  if (n < 0 || n >= 1024) return cudaErrorInvalidValue;
+  k_store_host<<<1, ((n + 1 + 31) / 32) * 32, 0, st>>>(src, n, flag, host);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- slab face traces
 
 // Components and element size of the traces of `what` (see launch_trace_pack).

@@ -48,6 +48,9 @@ cudaError_t launch_project(const dg_ctx* hi, const dg_ctx* lo, const double* qh,
 // The same tensor-product transform from the lower to the higher order (I: n_hi x n_lo).
 cudaError_t launch_prolong(const dg_ctx* lo, const dg_ctx* hi, const double* ql, double* qh, const double* Idev,
                            cudaStream_t st);
+// host[0..n) = src[0..n), then *flag as an int in the next slot; host is pinned host memory
+// (the SMs write it through the coherent mapping).  n < 1024.
+cudaError_t launch_store_host(const double* src, int n, const int* flag, double* host, cudaStream_t st);
 cudaError_t launch_diagnostics(const dg_ctx* c, const double* q, const double* R, const double* qref,
                                double* partial, int nblocks, double* out, cudaStream_t st);
 cudaError_t launch_make_pairs(const dg_ctx* lo, const double* qb_n, const double* qnn_np1, const double* qb_np1,

@@ -129,7 +129,15 @@ struct dg_ctx {
   double* red_host = nullptr;  // pinned host copy of the final reduction
   double* q_dev = nullptr;     // device state for dg_advance_host
   int* err_dev = nullptr;      // device error flag: a bounded wait in a kernel expired
-  bool host_diag_pending = false;  // dg_advance_host_async enqueued diagnostics not yet collected
+  // dg_advance_host_async calls in flight (at most two, on one stream), oldest at slot
+  // host_head: each has an event after its last copy and, if it asked for diagnostics,
+  // its results in its slot of the pinned ring [2][kHostSlot]
+  int host_pending = 0, host_head = 0;
+  bool host_want[2] = {};
+  cudaEvent_t host_evt[2] = {};
+  cudaStream_t host_stream = nullptr;
+  double* host_ring = nullptr;
+  double* host_ring_dev = nullptr;   // the ring's device address (cudaHostGetDevicePointer)
   int forcing_mode = DG_FORCING_STAGE;  // where dg_rk3_step applies a network forcing
   float* s_buf = nullptr;      // forcing buffer [nel][5 n^3]
   dgnn::FeatureOut feat_out;   // features the next phase-A launch also writes (set per launch)

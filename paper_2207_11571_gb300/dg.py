@@ -256,14 +256,16 @@ def dg_advance_host(ctx, q_host, dt, nsteps=1, forcing=None, stream=None, want_d
 
 def dg_advance_host_async(ctx, q_host, dt, nsteps=1, forcing=None, stream=None, want_diag=True):
     """Enqueues dg_advance_host on stream without waiting; q_host (pinned CPU tensor or
-    numpy float64) must stay untouched until dg_advance_host_wait returns."""
+    numpy float64) must stay untouched until the matching dg_advance_host_wait returns.
+    Up to two calls may be pending per context (on one stream)."""
     _check_host_state(ctx, q_host, "q_host")
     check(lib().dg_advance_host_async(ctypes.c_void_p(ctx), ptr(q_host), float(dt), int(nsteps), _net(forcing),
                                       int(bool(want_diag)), stream_ptr(stream)))
 
 
 def dg_advance_host_wait(ctx, stream=None, want_diag=True):
-    """Waits for the advance enqueued by dg_advance_host_async; returns its diagnostics."""
+    """Waits for the oldest pending dg_advance_host_async call (for that call only: a
+    second pending call keeps running); returns its diagnostics."""
     d = dg_diag()
     check(lib().dg_advance_host_wait(ctypes.c_void_p(ctx), ctypes.byref(d) if want_diag else None,
                                      stream_ptr(stream)))

@@ -399,6 +399,41 @@ def test_advance_host_async_on_two_streams_equals_device_path(dg):
         dg.dg_advance_host_async(ctxs[0].h, dev[0], 1e-3, 1)
 
 
+def test_advance_host_two_pending_calls_equal_the_device_path(dg):
+    """Step s + 1 queued before step s is collected: every wait returns the oldest call's
+    diagnostics (those of the device path after that many steps), the host state ends equal
+    to the device path's, and a third pending call or a second one on another stream is
+    refused."""
+    c = Ctx(dg, 3, 3, precision=1)
+    q, _ = c.tgv()
+    h = torch.empty(q.numel(), dtype=torch.float64, pin_memory=True)
+    h.copy_(q)
+    s = torch.cuda.Stream()
+    ref = []
+    dev = q.clone()
+    for _ in range(4):
+        dg.dg_rk3_step(c.h, dev, 1e-3, 1)
+        ref.append(dg.dg_diagnostics(c.h, dev))
+    got = []
+    dg.dg_advance_host_async(c.h, h, 1e-3, 1, None, s)
+    for step in range(1, 4):
+        dg.dg_advance_host_async(c.h, h, 1e-3, 1, None, s)   # queued behind the previous one
+        if step == 1:
+            with pytest.raises(dg.DGError) as e:               # a third pending call
+                dg.dg_advance_host_async(c.h, h, 1e-3, 1, None, s)
+            assert e.value.status == dg.DG_ERR_INVALID_ARG
+        got.append(dg.dg_advance_host_wait(c.h, s))
+    got.append(dg.dg_advance_host_wait(c.h, s))
+    for d, r in zip(got, ref):
+        assert d["mass"] == r["mass"] and d["ke"] == r["ke"] and d["energy"] == r["energy"]
+    np.testing.assert_array_equal(h.numpy(), dev.cpu().numpy())
+    dg.dg_advance_host_async(c.h, h, 1e-3, 1, None, s)
+    with pytest.raises(dg.DGError) as e:                       # a second pending call on another stream
+        dg.dg_advance_host_async(c.h, h, 1e-3, 1, None, torch.cuda.Stream())
+    assert e.value.status == dg.DG_ERR_INVALID_ARG
+    dg.dg_advance_host_wait(c.h, s)
+
+
 def test_bounded_waits_expire_and_leave_the_context_usable(dg):
     """Failure detection without a fault: waits on mbarriers that nothing completes give up
     after their limit (about a second), the kernel returns, and the next launches work."""
