@@ -400,6 +400,14 @@ __device__ __forceinline__ void gradient_block(int blk, const double* __restrict
       T acc = T(0);
       if (kLines && E == 1) {
         acc = sG[(4 * d + a) * np + node];
+      } else if (P == 3 && !CUBE && std::is_same<T, float>::value && d < 2) {
+        // P3 rows: an element's 64 nodes are two whole warps (node i + 4 j + 16 k), so its
+        // x- and y-lines lie within one warp: the line's values come by warp shuffles of
+        // the threads' own U (same products, same order: the same bits as from shared
+        // memory; measured -1 % per 32^3 RK3 step); z-lines span the two warps
+        const int l0 = (threadIdx.x & 31) - idx[d] * stride[d];
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc += Drow[m] * __shfl_sync(0xffffffffu, U[a], l0 + m * stride[d]);
       } else {
 #pragma unroll
         for (int m = 0; m < n; ++m) acc += Drow[m] * sU[a * tileN + base + m * stride[d]];
@@ -683,6 +691,11 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
 
   // RK operands of the update (loaded first with one node per thread, late with two)
   T gold[NPT][5], dold[NPT][5];
+  // P3 rows in FP32: the x- and y-direction volume fluxes stay in registers and the
+  // contraction takes a line's values by warp shuffles (an element is two whole warps, its
+  // x- and y-lines lie within one); the z-fluxes go through shared memory
+  constexpr bool kShfl = (P == 3) && !CUBE && !SPLIT && std::is_same<T, float>::value && !flux_early(P, sizeof(T));
+  T Fr[NPT][2][5];
   auto load_rk = [&](int j) {
     if (MODE == 3 || MODE == 4) {
 #pragma unroll
@@ -853,7 +866,11 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
       euler_flux(s[j], w, C.Hc, d, F);
       viscous_flux(vs[j], w.v, d, fv);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) sX[(5 * d + c) * tileN + tix[j]] = SPLIT ? -fv[c] : F[c] - fv[c];
+      for (int c = 0; c < 5; ++c) {
+        const T fd = SPLIT ? -fv[c] : F[c] - fv[c];
+        if (kShfl && d < 2) Fr[j][d][c] = fd;
+        else sX[(5 * d + c) * tileN + tix[j]] = fd;
+      }
     }
   }
   if (!kEarlyF) __syncthreads();
@@ -874,8 +891,14 @@ __device__ __forceinline__ void flux_block(int blk, double* __restrict__ q, cons
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         T acc = T(0);
+        if (kShfl && d < 2) {
+          const int l0 = (threadIdx.x & 31) - idx[d] * stride[d];
 #pragma unroll
-        for (int m = 0; m < n; ++m) acc += Drow[m] * sF[(5 * d + c) * tileN + base + m * stride[d]];
+          for (int m = 0; m < n; ++m) acc += Drow[m] * __shfl_sync(0xffffffffu, Fr[j][d][c], l0 + m * stride[d]);
+        } else {
+#pragma unroll
+          for (int m = 0; m < n; ++m) acc += Drow[m] * sF[(5 * d + c) * tileN + base + m * stride[d]];
+        }
         R[c] -= C.s2h * acc;
       }
     }
