@@ -302,6 +302,46 @@ def test_diagnostics_match_oracle(dg):
     assert d["nonfinite"] == 0
 
 
+def _max_wave_brute(q, N, gamma=1.4):
+    """|v| + c of every node in FP64 (torch, one node at a time in vector form)."""
+    r, mx, my, mz, e = q.view(5, N)
+    ir = 1.0 / r
+    vx, vy, vz = mx * ir, my * ir, mz * ir
+    v2 = vx * vx + vy * vy + vz * vz
+    p = (gamma - 1.0) * (e - 0.5 * r * v2)
+    return (v2.sqrt() + (gamma * p * ir).clamp_min(0.0).sqrt()).max().item()
+
+
+@pytest.mark.parametrize("case", ["tgv", "rough", "spike", "cancel"])
+def test_max_wave_screen_keeps_the_fp64_maximum(dg, case):
+    """The diagnostics screen the wave speed in FP32 and evaluate the FP64 expression only
+    near each thread's running maximum: the result is the FP64 maximum over every node.
+    Cases: Taylor-Green; a rough per-node state; a state where one node late in a thread's
+    walk exceeds the rest by 1e-6 relative (below FP32 resolution of the estimate's screen);
+    nodes whose pressure is nearly cancelled (the FP32 estimate is unreliable there, so
+    they go to FP64)."""
+    c = Ctx(dg, 6, 3)
+    q, _ = c.tgv()
+    N = c.N
+    g = torch.Generator(device="cpu").manual_seed(5)
+    if case == "rough":
+        q.view(5, N).mul_(1 + 0.05 * torch.rand(5, N, generator=g, dtype=torch.float64).cuda())
+    elif case == "spike":
+        q.view(5, N)[1:4] = 0.0
+        q.view(5, N)[4] = 2.5 / 0.4           # rho e = p / (gamma - 1), p = 2.5, rho = 1
+        q.view(5, N)[0] = 1.0
+        k = N - 7
+        q.view(5, N)[4, k] *= 1 + 2e-6        # c grows by ~1e-6 relative at one node
+    elif case == "cancel":
+        r = q.view(5, N)
+        for k in (11, N // 2, N - 3):          # kinetic energy takes all but 0.1 % of rho e
+            v2 = (r[1, k] ** 2 + r[2, k] ** 2 + r[3, k] ** 2) / r[0, k] ** 2
+            r[4, k] = 0.5 * r[0, k] * v2 * 1.001
+    d = dg.dg_diagnostics(c.h, q)
+    ref = _max_wave_brute(q, N)
+    assert d["max_wave"] == pytest.approx(ref, rel=1e-15, abs=0), (d["max_wave"], ref)
+
+
 def test_diagnostics_flag_nonfinite_state(dg):
     c = Ctx(dg, 2, 3)
     q, _ = c.tgv()
