@@ -6,7 +6,7 @@
 // through the network.  Each CTA loads the tile's features by TMA.  CTA j of the cluster
 // owns output columns [j N/C, (j+1) N/C) of every layer: it streams only that slice of
 // each weight matrix, writes its bf16 slice of each hidden layer's output into its own
-// activation panels, and copies that slice (whole 64-column panels, one bulk copy per
+// activation panels, and copies that slice (64-column panels, one bulk copy per panel and
 // peer on the asynchronous copy engine) into the same panels of every other CTA of the
 // cluster (distributed shared memory), so that each CTA holds the whole input of the next
 // layer.  With C = 4 a 4096-element mesh occupies 128 SMs, and every weight byte read from
@@ -15,8 +15,8 @@
 // Warps: 0 TMA producer (the feature tile, then weight tiles through a 5-stage ring),
 // 1 TMEM allocation and the MMA issuer, 2..9 epilogue: two warps per TMEM lane quarter
 // (one TMEM lane = one element per thread), taking alternate 16-column groups, one 64-column
-// panel of the CTA's slice after the other; 10 the exchange: the arrivals at the peers and
-// the slice copies, off the epilogue's path.  The layers' biases and the output scaling of
+// panel of the CTA's slice after the other; 10 the exchange (lane k talks to CTA k): the
+// arrivals at the peers, the slice copies and the receipts, off the epilogue's path.  The layers' biases and the output scaling of
 // this CTA's slices sit in shared memory.  Ordering uses mbarriers only:
 //   panel_ready[i] (one arrival per epilogue thread): panel i of this CTA's slice of the
 //       next input is written (a CTA's own panels are free once its own MMAs of the layer
@@ -30,9 +30,9 @@
 //       slice has landed everywhere, so the copy engine no longer reads the panels that
 //       the next slice overwrites.
 // A hidden layer's K loop starts on the CTA's own panels as each is written and then takes
-// the peers' slices in the order they are sent (CTA k copies each panel to k - 1 first,
-// then k - 2, ...), so the tensor core works while the other slices are still in flight;
-// the weight tiles stream in the same order.  Where a slice is at most 256 columns, layers
+// the peers' slices in rank order after its own (j + 1, j + 2, ...), each on its own
+// barrier, so the tensor core works while the other slices are still in flight; the
+// weight tiles stream in the same order.  Where a slice is at most 256 columns, layers
 // alternate between two TMEM accumulators, so the next layer's MMAs may start while the
 // epilogue still reads the last panels of this one.
 // Every wait is bounded (about a second): on expiry a thread sets the error flag and the
