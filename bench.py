@@ -116,6 +116,46 @@ def bf16_peak():
         return 1900.0, "fallback"
 
 
+# The FP64 operator (the parity path) against GB300's FP64 rate: not a performance
+# target, reported for context.  Arithmetic per DOF-stage estimated from the operator's
+# structure: ~30 (P+1) inviscid and ~48 (P+1) gradient/viscous contraction flops plus
+# ~300 pointwise flops; nominal FP64 peak 1.25 TFLOP/s (no measured FP64 peak exists).
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def fp64_measure(stream, steps=3):
+    import torch
+
+    from paper_2207_11571_gb300 import dg, inputs
+    per_mesh, tot_upd, tot_ms, tot_flop = {}, 0, 0.0, 0.0
+    for K, P in WORKLOAD:
+        c = dg.dg_create(K, P, RE, MACH, PR, 0, precision=dg.DG_PREC_FP64)
+        N = dg.dg_sizes(c)[0]
+        q = torch.empty(5 * N, dtype=torch.float64, device="cuda")
+        dg.dg_init_tgv(c, q, torch.from_numpy(inputs.perturbation((5, N), seed=inputs.TGV_SEED).ravel()).cuda())
+        dt = dg.dg_stable_dt(c, q, CFL)
+        dg.dg_rk3_step(c, q, dt, 1, None, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dg.dg_rk3_step(c, q, dt, steps, None, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        flop = (30 * (P + 1) + 48 * (P + 1) + 300) * 3 * N
+        per_mesh[f"{K}^3/P{P}"] = {"ms_per_step": round(ms, 3), "dof_stage_per_s": 3 * N / (ms / 1e3),
+                                   "tflops_estimate": flop / (ms / 1e3) / 1e12}
+        tot_upd += 3 * N
+        tot_ms += ms
+        tot_flop += flop
+        dg.dg_destroy(c)
+    achieved = tot_flop / (tot_ms / 1e3) / 1e12
+    return {"value": tot_upd / (tot_ms / 1e3), "unit": UNIT, "ms_per_step": round(tot_ms, 3), "per_mesh": per_mesh,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_NOMINAL_TFLOPS, "peak_source": "nominal (recipe table)",
+                         "flop_per_dof_stage": "estimate 78 (P+1) + 300"},
+            "note": "FP64 operator and FP64 RK3 (the parity path), same meshes, CUDA events; context only"}
+
+
 def nn_measure(stream, steps=100):
     """Forcing network of the corrected P=3 run (5 x 64 = 320 inputs and outputs, 4 hidden
     layers of 512, batch 4096): one training step (forward, MSE, backward, Adam) and one
@@ -597,6 +637,7 @@ def run_ours(args, rank, ws):
         cpu = cpu_baseline()
 
     nn_line = nn_measure(stream)
+    fp64_line = fp64_measure(stream)
     alg1 = None if args.no_algorithm1 else algorithm1_measure()
     batched = None
     if not args.no_batched:
@@ -628,7 +669,8 @@ def run_ours(args, rank, ws):
                            "parallelism": f"replicas x{ws}", "per_workload": per_workload},
                 "value_x5_variables": {"value": 5 * value, "unit": "variable-stage updates/s",
                                        "note": "the same rate counting each node's 5 conserved variables"},
-                "roofline": roofline, "kernels": per_kernel, "network": nn_line, "batched": batched,
+                "roofline": roofline, "kernels": per_kernel, "network": nn_line, "fp64_operator": fp64_line,
+                "batched": batched,
                 "algorithm1": alg1,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 6 * len(WORKLOAD) * args.steps, "clocks": clk}
