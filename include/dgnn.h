@@ -208,7 +208,8 @@ int dg_batch_autotune(dg_batch* batch, double* const* q, const double* dt, void*
 
 /* Same as dg_rk3_step but q_host is a HOST array (pageable or pinned, 5 N doubles):
  * copies it to the device, advances, copies it back, and fills *diag (host, may be
- * NULL) for the final state.  Synchronises the stream. */
+ * NULL) for the final state.  Synchronises the stream.  DG_ERR_INVALID_ARG while
+ * dg_advance_host_async calls of the context are pending. */
 int dg_advance_host(dg_ctx* ctx, double* q_host, double dt, int nsteps,
                     const nn_model* forcing, dg_diag* diag, void* stream);
 

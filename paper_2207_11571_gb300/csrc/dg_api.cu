@@ -707,6 +707,8 @@ int dg_advance_host(dg_ctx* c, double* q_host, double dt, int nsteps, const nn_m
                     void* stream) {
   if (!c || !q_host) return fail(DG_ERR_INVALID_ARG, "dg_advance_host: NULL argument");
   if (nsteps < 0 || !std::isfinite(dt)) return fail(DG_ERR_INVALID_ARG, "dg_advance_host: bad nsteps or dt");
+  // its wait must collect this call, not an older pending one
+  if (c->host_pending) return fail(DG_ERR_INVALID_ARG, "dg_advance_host: dg_advance_host_async calls are pending");
   int rc = dg_advance_host_async(c, q_host, dt, nsteps, forcing, diag != nullptr, stream);
   if (rc) return rc;
   return dg_advance_host_wait(c, diag, stream);

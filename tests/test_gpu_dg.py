@@ -471,6 +471,9 @@ def test_advance_host_two_pending_calls_equal_the_device_path(dg):
     with pytest.raises(dg.DGError) as e:                       # a second pending call on another stream
         dg.dg_advance_host_async(c.h, h, 1e-3, 1, None, torch.cuda.Stream())
     assert e.value.status == dg.DG_ERR_INVALID_ARG
+    with pytest.raises(dg.DGError) as e:                       # the synchronous form while one is pending
+        dg.dg_advance_host(c.h, h, 1e-3, 1, None, s)
+    assert e.value.status == dg.DG_ERR_INVALID_ARG
     dg.dg_advance_host_wait(c.h, s)
 
 
