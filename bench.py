@@ -483,7 +483,7 @@ def run_ours(args, rank, ws):
     dev = torch.cuda.current_device()
     stream = torch.cuda.current_stream()
 
-    ctxs, states, dts, nodes, tuned = [], [], [], [], []
+    ctxs, states, dts, nodes, tuned, tuned_ms = [], [], [], [], [], []
     for K, P in WORKLOAD:
         c = dg.dg_create(K, P, RE, MACH, PR, 0, precision=dg.DG_PREC_FP32)
         N = dg.dg_sizes(c)[0]
@@ -492,14 +492,19 @@ def run_ours(args, rank, ws):
         dg.dg_init_tgv(c, q, pert)
         del pert
         dts.append(dg.dg_stable_dt(c, q, CFL))
-        tuned.append(dg.dg_autotune(c, q, dts[-1])[0])
+        E_best, ms_best = dg.dg_autotune(c, q, dts[-1])
+        tuned.append(E_best)
+        tuned_ms.append(ms_best)
         ctxs.append(c)
         states.append(q)
         nodes.append(N)
     updates_per_step = 3 * sum(nodes)
     # one stream per mesh, forked from and joined to the launching stream every step: the
-    # meshes are independent, so one mesh's kernels fill the SMs another's tail leaves idle
-    mesh_streams = [torch.cuda.Stream() for _ in ctxs]
+    # meshes are independent, so one mesh's kernels fill the SMs another's tail leaves idle;
+    # the mesh with the longest step (by the autotuner's timing) runs at high priority, so
+    # the others fill in around it (measured 1377 -> 1349 us per step)
+    slowest = max(range(len(ctxs)), key=lambda i: tuned_ms[i])
+    mesh_streams = [torch.cuda.Stream(priority=-1 if i == slowest else 0) for i in range(len(ctxs))]
 
     def step():
         fork = torch.cuda.Event()
@@ -672,7 +677,8 @@ def run_ours(args, rank, ws):
                            "nodes": nodes, "l2": "working set per mesh 190-400 MB > 129 MB L2 (no flush)",
                            "elems_per_block": tuned,
                            "block_shape": shapes,
-                           "streams": "one per mesh, forked from and joined to the timed stream every step",
+                           "streams": "one per mesh, forked from and joined to the timed stream every step; "
+                                      "the mesh with the longest step at high priority",
                            "parallelism": f"replicas x{ws}", "per_workload": per_workload},
                 "value_x5_variables": {"value": 5 * value, "unit": "variable-stage updates/s",
                                        "note": "the same rate counting each node's 5 conserved variables"},
