@@ -138,3 +138,13 @@ def test_network_bindings_check_rows_dtype_and_device():
         nn._check_rows(OnDevice(torch.zeros(10, 320, dtype=torch.float64)), 320, "X")
     with pytest.raises(ValueError):
         nn._check_rows(torch.zeros(10, 320), 320, "X")          # host tensor
+
+
+def test_training_calls_reject_bad_arguments_before_touching_cuda(L):
+    """The data-parallel training calls check their handles and sizes before any CUDA call."""
+    from paper_2207_11571_gb300 import dg, nn
+    nn._register(L)
+    assert L.nn_backward(None, None, None, None, 1, 1, None, None) == dg.DG_ERR_INVALID_ARG
+    dW, db = ctypes.c_void_p(), ctypes.c_void_p()
+    assert L.nn_grad_buffers(None, 0, ctypes.byref(dW), ctypes.byref(db)) == dg.DG_ERR_INVALID_ARG
+    assert L.nn_adam_apply(None, None, None) == dg.DG_ERR_INVALID_ARG
